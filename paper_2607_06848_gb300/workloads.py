@@ -1,0 +1,79 @@
+"""Seeded synthetic inputs shared by the CUDA path, the tests and the benchmark.
+
+This module draws random numbers and builds geometries; it holds none of the
+method's arithmetic.  Everything here is a plain function of a seed.
+
+Workloads (shaped like the paper's Sec. IV systems; the paper's geometries and
+pseudopotentials are not available, so seeded stand-ins are used):
+  dimer      2 atoms 2.2 bohr apart at the centre of a 16-bohr cube, Z = 4,
+             8^3 cells of degree 4, 8 states, filter degree 20.
+  cluster64  64 atoms (Z = 4) placed uniformly at random in [6, 34]^3 with
+             pairwise distance >= 4.2 bohr, 40-bohr cube, 24^3 cells of
+             degree 6, 154 states, filter degree 30.
+  cluster512 512 atoms in an 80-bohr cube, 40^3 cells of degree 5, 1230 states.
+"""
+import numpy as np
+
+
+def place_atoms(n_atoms, lo, hi, min_dist, seed, max_tries=2_000_000):
+    """Rejection-sample n_atoms positions uniform in [lo, hi]^3, pairwise >= min_dist."""
+    rng = np.random.default_rng(seed)
+    pos = np.empty((0, 3))
+    tries = 0
+    while len(pos) < n_atoms:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place atoms")
+        p = rng.uniform(lo, hi, size=3)
+        if len(pos) == 0 or np.min(np.sum((pos - p) ** 2, axis=1)) >= min_dist ** 2:
+            pos = np.vstack([pos, p])
+    return pos
+
+
+def projector_strengths(n_atoms, seed):
+    """h_{I,l} for l = s, p drawn uniformly from [-2, 2] Ha: shape (n_atoms, 2)."""
+    return np.random.default_rng(seed).uniform(-2.0, 2.0, size=(n_atoms, 2))
+
+
+def random_block(rows, cols, seed):
+    """Seeded N(0, 1) block of shape (rows, cols), row-major float64."""
+    return np.random.default_rng(seed).standard_normal((rows, cols))
+
+
+def dimer(seed=0):
+    """The 2-atom workload (8^3 cells, degree 4)."""
+    L = 16.0
+    atoms = np.array([[L / 2 - 1.1, L / 2, L / 2], [L / 2 + 1.1, L / 2, L / 2]])
+    return dict(name="dimer", h=2.0, ncell=(8, 8, 8), p=4, atoms=atoms,
+                Z=np.full(2, 4.0), hproj=projector_strengths(2, seed), nstates=8,
+                cheb_degree=20)
+
+
+def cluster(n_atoms, side, ncell, p, nstates, cheb_degree, seed=0, margin=6.0,
+            min_dist=4.2, name=None):
+    atoms = place_atoms(n_atoms, margin, side - margin, min_dist, seed)
+    return dict(name=name or f"cluster{n_atoms}", h=side / ncell, ncell=(ncell,) * 3, p=p,
+                atoms=atoms, Z=np.full(n_atoms, 4.0),
+                hproj=projector_strengths(n_atoms, seed + 1), nstates=nstates,
+                cheb_degree=cheb_degree)
+
+
+def cluster64(seed=0):
+    return cluster(64, 40.0, 24, 6, 154, 30, seed=seed, name="cluster64")
+
+
+def cluster512(seed=0):
+    return cluster(512, 80.0, 40, 5, 1230, 30, seed=seed, name="cluster512")
+
+
+def small_cluster(n_atoms, seed, h=2.0, p=4, pad=7.0, min_dist=4.2):
+    """8-32 atom training clusters: box = extent + 2*pad rounded up to a multiple of h."""
+    side0 = 4.2 * (n_atoms ** (1.0 / 3.0)) * 1.3
+    rel = place_atoms(n_atoms, 0.0, side0, min_dist, seed)
+    ext = rel.max(axis=0) - rel.min(axis=0)
+    ncell = tuple(int(np.ceil((e + 2 * pad) / h)) for e in ext)
+    box = np.array(ncell) * h
+    atoms = rel - rel.min(axis=0) + (box - ext) / 2.0
+    return dict(name=f"small{n_atoms}_{seed}", h=h, ncell=ncell, p=p, atoms=atoms,
+                Z=np.full(n_atoms, 4.0), hproj=projector_strengths(n_atoms, seed + 1),
+                nstates=int(np.ceil(1.2 * 2 * n_atoms)), cheb_degree=20)
