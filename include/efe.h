@@ -1,0 +1,204 @@
+/*
+ * efe.h -- C ABI of libefe: the orthogonalized enriched finite element (EFE)
+ * Kohn-Sham eigensolver path on one GPU (sm_103a).
+ *
+ * The operations follow "Large-scale pseudopotential density functional
+ * theory calculations using orthogonalized enriched finite element basis":
+ *   Sec. II.A  Eq. (KS)                 the Kohn-Sham eigenproblem
+ *   Sec. II.B  Eqs. (cutoff), (N^E)     enrichment functions, orthogonalized
+ *   Sec. II.B  Eqs. (Discrete_Eig_Gen_H/M)  H^E psi = eps M^E psi, M^ec = 0
+ *   Sec. III.A Eq. (MEInvApprox)        (M~^E)^-1 = diag(M^cc)^-1 + atom blocks
+ *   Sec. III.B Eqs. (ChebyRecur), (residual), (residualapprox), (projectedKSEig)
+ *   Sec. II.A  Eqs. (rhocompute), (electronconstraint), (EellocReform), (poisson)
+ *
+ * Conventions shared by every call
+ *   - Every function returns efe_status; nothing throws across the ABI.
+ *   - Pointers documented "device" are CUDA device pointers owned by the
+ *     caller; the library never frees them.  "host" pointers are ordinary
+ *     memory.  All device work is issued on the stream given to efe_setup and
+ *     is finished when a call that returns host values returns; calls that
+ *     return nothing on the host may still be running on that stream.
+ *   - Arguments are validated before any launch; on EFE_ERR_ARG nothing ran.
+ *   - efe_last_error() gives a one-line description of the last failure.
+ *
+ * Block-vector layout ("rows")
+ *   A block of N vectors is a row-major (n_rows x ld) array of doubles, ld >= N
+ *   (ld = N unless stated), with
+ *     rows [0, n_nodes)           FE nodes of the full (Gx x Gy x Gz) GLL grid,
+ *                                 node n = (iz*Gy + iy)*Gx + ix, G* = ncell* p + 1;
+ *                                 Dirichlet boundary rows are kept and held at 0
+ *     rows [n_nodes, n_rows)      enrichment coefficients, 4 per atom
+ *                                 (s, px, py, pz), atom-major.
+ *   Fields at quadrature points are arrays of n_cells * nq^3 doubles, cell
+ *   c = (cz*ny + cy)*nx + cx, point q = (qz*nq + qy)*nq + qx, Gauss-Legendre
+ *   points per axis per cell.
+ */
+#ifndef EFE_H
+#define EFE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct efe_ctx efe_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    EFE_OK = 0,
+    EFE_ERR_ARG = 1,         /* invalid argument; nothing was launched */
+    EFE_ERR_CUDA = 2,        /* a CUDA runtime or library call failed */
+    EFE_ERR_NOT_SPD = 3,     /* an overlap block is not positive definite */
+    EFE_ERR_NO_CONVERGE = 4, /* iteration cap reached before the tolerance */
+    EFE_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+    EFE_ERR_OOM = 6,         /* device allocation failed */
+    EFE_ERR_STATE = 7        /* call order violated (e.g. no potential set) */
+} efe_status;
+
+typedef enum {
+    EFE_FP64 = 0, /* every filter operation in double precision */
+    EFE_FP32 = 1, /* filter cell products and recurrence in float (FP32 accumulate) */
+    EFE_BF16 = 2  /* filter cell products on tcgen05 tensor cores, bf16 operands,
+                     FP32 accumulate; recurrence stored in float */
+} efe_precision;
+
+/* Uniform mesh of cubic cells of side h over [0, nx h] x [0, ny h] x [0, nz h]
+ * (Sec. III.A spectral elements).  degree p in [1, 8]; nquad Gauss points per
+ * axis per cell for every integral except the GLL-lumped M^cc (0 -> p + 2). */
+typedef struct {
+    double h;
+    int ncell[3];
+    int degree;
+    int nquad;
+} efe_mesh;
+
+/* Atoms (Sec. II.A): positions in bohr (natoms x 3, host), valence charges. */
+typedef struct {
+    int natoms;
+    const double *xyz;
+    const double *zval;
+} efe_atoms;
+
+/* Enrichment (Sec. II.B): per atom a_s = Y00 g0 h, a_pm = r Y_1m g1 h with
+ * g_l(r) = r^l exp(-alpha r^2) and the smooth cutoff h(r, r0, t), r0 chosen so
+ * that the support ends at r_end: r0 = r_end t / (1 + t).  enabled = 0 gives
+ * the classical FE basis alone. */
+typedef struct {
+    int enabled;
+    double alpha;
+    double r_end;
+    double t;
+} efe_enrichment;
+
+/* Pseudopotential: local part v_loc = -Z erf(r / rloc) / r (enters only via
+ * the Gaussian smeared charge of the electrostatics) and a separable nonlocal
+ * part sum_I sum_lm |beta_Ilm> h_Il <beta_Ilm| with s and p Gaussian
+ * projectors exp(-r^2/(2 rc^2)) (unit norm), truncated at r_trunc.
+ * h: host, natoms x 2 (h_s, h_p) in Ha.  enabled = 0 drops the nonlocal part. */
+typedef struct {
+    int enabled;
+    double rc;
+    double r_trunc;
+    const double *h;
+    double rloc;
+} efe_psp;
+
+typedef struct {
+    long long n_nodes;   /* FE rows incl. boundary */
+    long long n_fe_dof;  /* interior FE nodes (true unknowns) */
+    long long n_rows;    /* n_nodes + n_enr */
+    long long n_quad;    /* n_cells * nq^3 */
+    int n_enr;
+    int n_proj;
+    int n_cells;
+    int ne;              /* (p+1)^3 nodes per cell */
+    int nq;              /* Gauss points per axis */
+    int grid[3];         /* Gx, Gy, Gz */
+} efe_dims;
+
+/* Timings of the last efe_chfsi / efe_filter call, from CUDA events on the
+ * library stream (milliseconds), and the number of kernels it launched. */
+typedef struct {
+    double ms_filter;
+    double ms_rr;
+    double ms_lanczos;
+    double ms_cell;      /* the cell-product kernels inside the filter */
+    long long launches;
+    int passes;
+} efe_stats;
+
+/* Build the discretisation, enrichment, orthogonalization (C = B^T (M^cc)^-1,
+ * M^ee = A_ee - B^T (M^cc)^-1 B, Sec. II.B), the atom blocks of M~^ee and their
+ * inverses (Eq. MEInvApprox), and the projector tables.  stream: a
+ * cudaStream_t (NULL = legacy default).  Fails with EFE_ERR_NOT_SPD if an atom
+ * block of M^ee is not positive definite, EFE_ERR_ARG if an enrichment or
+ * projector support leaves the box.  *out receives a new context. */
+efe_status efe_setup(const efe_mesh *mesh, const efe_atoms *atoms,
+                     const efe_enrichment *enrich, const efe_psp *psp,
+                     void *stream, efe_ctx **out);
+
+void efe_destroy(efe_ctx *ctx);
+const char *efe_last_error(const efe_ctx *ctx);
+efe_status efe_get_dims(const efe_ctx *ctx, efe_dims *dims);
+efe_status efe_get_stats(const efe_ctx *ctx, efe_stats *stats);
+
+/* Assemble the potential-dependent operator (Eq. KS with v_KS = veff):
+ * cell matrices H_e = 1/2 K_e + int veff N_i N_j, the raw coupling blocks
+ * H^ac, H^aa.  veff_q: device, n_quad doubles at the Gauss points.  Must be
+ * called before any H product. */
+efe_status efe_set_potential(efe_ctx *ctx, const double *veff_q);
+
+/* Y = H^E X = T^T H_raw T X (Eq. Discrete_Eig_Gen_H).  X, Y: device, rows x N,
+ * not aliased.  prec selects the arithmetic of the cell products (EFE_FP64:
+ * double; EFE_FP32 / EFE_BF16: inputs rounded, FP32 accumulate), used by the
+ * parity tests of the mixed filter. */
+efe_status efe_apply_h(efe_ctx *ctx, const double *X, double *Y, int N, efe_precision prec);
+
+/* Y = M^E X with the exact M^E (diagonal M^cc, full M^ee). device, rows x N. */
+efe_status efe_apply_m(efe_ctx *ctx, const double *X, double *Y, int N);
+
+/* Y = (M~^E)^-1 X (Eq. MEInvApprox).  device, rows x N. */
+efe_status efe_apply_minv(efe_ctx *ctx, const double *X, double *Y, int N);
+
+/* k-step Lanczos for M~^-1 H^E in the M~ inner product from the device vector
+ * u0 (rows doubles).  out (host): theta_min, theta_max, theta_max + |beta_k s_k|. */
+efe_status efe_lanczos(efe_ctx *ctx, const double *u0, int k, double out[3]);
+
+/* One residual Chebyshev filter of degree m (Eqs. residual, residualapprox
+ * with the recurrence re-derived from Eq. ChebyRecur):
+ *   G = HV - M^E V diag(lam);  Z_1 = (s1/e) G;
+ *   Z_k = (2 s_k/e)(H M~^-1 Z_{k-1} - c Z_{k-1}) - s_{k-1} s_k Z_{k-2}
+ *         + (2 s_k/e) G diag(C_{k-1}(lam));
+ *   Vout = M~^-1 Z_m + V diag(C_m(lam)).
+ * V, HV, Vout: device rows x N (HV = H^E V in double); lam: device N doubles;
+ * bounds (host): a0 <= lowest wanted, [a, b] the damped interval. */
+efe_status efe_filter(efe_ctx *ctx, const double *V, const double *HV, const double *lam,
+                      int N, int m, const double bounds[3], efe_precision prec, double *Vout);
+
+/* Rayleigh-Ritz with the exact M^E (Eq. projectedKSEig), in place:
+ * X <- X D, HX <- H^E X D with D^T (X^T M X) D = I, ascending eigenvalues.
+ * X, HX: device rows x N (HX is computed here); eig, resid: host N doubles
+ * (resid_i = ||H psi_i - eps_i M psi_i||_2).  EFE_ERR_NOT_SPD if X^T M X is
+ * not positive definite (dependent columns). */
+efe_status efe_rayleigh_ritz(efe_ctx *ctx, double *X, double *HX, int N,
+                             double *eig, double *resid);
+
+/* Multipass residual ChFSI (Sec. III.B): Rayleigh-Ritz on X, then passes of
+ * efe_filter + Rayleigh-Ritz until max(resid[0:nconv]) < tol or max_pass.
+ * bounds (host, a0, a, b) or NULL for a 10-step Lanczos from u0 (device)
+ * with a0 = theta_min, a = a0 + 0.3 (b - a0); later passes a = max Ritz value,
+ * a0 = min Ritz value.  X, HX: device rows x N, in/out (HX may be NULL).
+ * eig, resid: host N.  passes: host, may be NULL.  EFE_ERR_NO_CONVERGE when
+ * max_pass is reached (results are still written). */
+efe_status efe_chfsi(efe_ctx *ctx, double *X, double *HX, int N, int m, const double *bounds,
+                     const double *u0, int max_pass, double tol, int nconv,
+                     efe_precision prec, double *eig, double *resid, int *passes);
+
+/* Same filter with host buffers (V, HV, Vout: host rows x N; lam: host N):
+ * copies in, filters, copies out on the library stream, returns when done. */
+efe_status efe_filter_host(efe_ctx *ctx, const double *V, const double *HV, const double *lam,
+                           int N, int m, const double bounds[3], efe_precision prec,
+                           double *Vout);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EFE_H */

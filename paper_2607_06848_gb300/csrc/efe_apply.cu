@@ -1,0 +1,1241 @@
+// H^E, M^E, (M~^E)^-1 products, the residual Chebyshev filter, Rayleigh-Ritz,
+// Lanczos bounds and the C ABI entry points (paper Sec. II.B, III.A, III.B).
+#include "efe_internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <type_traits>
+
+namespace {
+
+inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+__device__ inline bool node_interior(const MeshDev &m, int ix, int iy, int iz) {
+    return ix > 0 && iy > 0 && iz > 0 && ix < m.Gx - 1 && iy < m.Gy - 1 && iz < m.Gz - 1;
+}
+
+// ---------------------------------------------------------------------------
+// Cell products of one colour: Y[nodes(c)] += H_c X[nodes(c)].  Cells of one
+// colour (parity of cx, cy, cz) share no node, so the read-modify-write of Y
+// needs no atomics.  Block = one cell x TN columns; the cell's X block is
+// gathered into shared memory by index arithmetic on the node grid.
+// ---------------------------------------------------------------------------
+template <typename T, int TN>
+__global__ void __launch_bounds__(256) k_cell_apply(MeshDev m, int colour, const T *He, long long he_stride,
+                                                    const T *X, T *Y, int N, int ld) {
+    extern __shared__ unsigned char smraw[];
+    T *sX = reinterpret_cast<T *>(smraw);
+    const int ox = colour & 1, oy = (colour >> 1) & 1, oz = (colour >> 2) & 1;
+    const int hx = (m.nx - ox + 1) / 2, hy = (m.ny - oy + 1) / 2;
+    const int b = blockIdx.x;
+    const int cx = 2 * (b % hx) + ox, cy = 2 * ((b / hx) % hy) + oy, cz = 2 * (b / (hx * hy)) + oz;
+    const int c = (cz * m.ny + cy) * m.nx + cx;
+    const int col0 = blockIdx.y * TN;
+    const int np1 = m.np1, ne = m.ne;
+    for (int i = threadIdx.x; i < ne * TN; i += blockDim.x) {
+        int l = i / TN, j = i % TN;
+        int lx = l % np1, ly = (l / np1) % np1, lz = l / (np1 * np1);
+        long long n = ((long long)(cz * m.p + lz) * m.Gy + (cy * m.p + ly)) * m.Gx + (cx * m.p + lx);
+        sX[i] = (col0 + j < N) ? X[n * ld + col0 + j] : T(0);
+    }
+    __syncthreads();
+    const T *H = He + (long long)c * he_stride;
+    for (int i = threadIdx.x; i < ne * TN; i += blockDim.x) {
+        int l = i / TN, j = i % TN;
+        if (col0 + j >= N) continue;
+        const T *Hr = H + (long long)l * ne;
+        T acc = T(0);
+        for (int k = 0; k < ne; ++k) acc += Hr[k] * sX[k * TN + j];
+        int lx = l % np1, ly = (l / np1) % np1, lz = l / (np1 * np1);
+        int ix = cx * m.p + lx, iy = cy * m.p + ly, iz = cz * m.p + lz;
+        if (!node_interior(m, ix, iy, iz)) continue;
+        long long n = ((long long)iz * m.Gy + iy) * m.Gx + ix;
+        Y[n * ld + col0 + j] += acc;
+    }
+}
+
+template <typename T>
+efe_status launch_cells(efe_ctx *ctx, const T *He, long long he_stride, const T *X, T *Y, int N, int ld) {
+    const MeshDev &m = ctx->m;
+    for (int colour = 0; colour < 8; ++colour) {
+        const int ox = colour & 1, oy = (colour >> 1) & 1, oz = (colour >> 2) & 1;
+        const int hx = (m.nx - ox + 1) / 2, hy = (m.ny - oy + 1) / 2, hz = (m.nz - oz + 1) / 2;
+        const int ncol = hx * hy * hz;
+        if (!ncol) continue;
+        if (N <= 8) {
+            dim3 g(ncol, nblk(N, 8));
+            size_t shm = sizeof(T) * m.ne * 8;
+            cudaFuncSetAttribute(k_cell_apply<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            k_cell_apply<T, 8><<<g, 256, shm, ctx->stream>>>(m, colour, He, he_stride, X, Y, N, ld);
+        } else if (N <= 16) {
+            dim3 g(ncol, nblk(N, 16));
+            size_t shm = sizeof(T) * m.ne * 16;
+            cudaFuncSetAttribute(k_cell_apply<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            k_cell_apply<T, 16><<<g, 256, shm, ctx->stream>>>(m, colour, He, he_stride, X, Y, N, ld);
+        } else {
+            dim3 g(ncol, nblk(N, 32));
+            size_t shm = sizeof(T) * m.ne * 32;
+            cudaFuncSetAttribute(k_cell_apply<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            k_cell_apply<T, 32><<<g, 256, shm, ctx->stream>>>(m, colour, He, he_stride, X, Y, N, ld);
+        }
+        ctx->launches++;
+        EFE_TRY(efe_check_launch(ctx, "k_cell_apply"));
+    }
+    return EFE_OK;
+}
+
+// X'_c = X_c - C^T X_e (first half of T), boundary rows forced to zero.
+template <typename T>
+__global__ void k_xprime(MeshDev m, long long n_nodes, const T *X, T *Xp, int N, int ld,
+                         const long long *node_ptr, const int *node_ent, const int *ent_atom,
+                         const double *C, int use_c) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= n_nodes * N) return;
+    long long n = idx / N;
+    int j = (int)(idx % N);
+    int ix = (int)(n % m.Gx), iy = (int)((n / m.Gx) % m.Gy), iz = (int)(n / ((long long)m.Gx * m.Gy));
+    if (!node_interior(m, ix, iy, iz)) { Xp[n * ld + j] = T(0); return; }
+    T v = X[n * ld + j];
+    if (use_c) {
+        const T *Xe = X + n_nodes * ld;
+        double acc = 0.0;
+        for (long long e = node_ptr[n]; e < node_ptr[n + 1]; ++e) {
+            int g = node_ent[e];
+            int I = ent_atom[g];
+            const double *c = C + 4 * (long long)g;
+            acc += c[0] * (double)Xe[(4 * I + 0) * (long long)ld + j] + c[1] * (double)Xe[(4 * I + 1) * (long long)ld + j] +
+                   c[2] * (double)Xe[(4 * I + 2) * (long long)ld + j] + c[3] * (double)Xe[(4 * I + 3) * (long long)ld + j];
+        }
+        v = (T)((double)v - acc);
+    }
+    Xp[n * ld + j] = v;
+}
+
+// Partial support reductions: for atom I (blockIdx.y) and chunk blockIdx.x,
+//   part[(I*nch + chunk)][r][j] = sum_{g in chunk} coef_r[g] * S[node(g)][j]
+// with up to 8 coefficient rows (two 4-wide tables A and B).
+template <typename T>
+__global__ void k_support_reduce(const long long *sup_off, const int *sup_node, const double *coefA,
+                                 const double *coefB, const T *S, int N, int ld, int chunk, int nch,
+                                 double *part) {
+    const int I = blockIdx.y;
+    const long long beg = sup_off[I] + (long long)blockIdx.x * chunk;
+    const long long end = min(sup_off[I + 1], beg + chunk);
+    const int nr = coefB ? 8 : 4;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (long long g = beg; g < end; ++g) {
+            double s = (double)S[(long long)sup_node[g] * ld + j];
+            const double *a = coefA + 4 * g;
+            acc[0] += a[0] * s; acc[1] += a[1] * s; acc[2] += a[2] * s; acc[3] += a[3] * s;
+            if (coefB) {
+                const double *b2 = coefB + 4 * g;
+                acc[4] += b2[0] * s; acc[5] += b2[1] * s; acc[6] += b2[2] * s; acc[7] += b2[3] * s;
+            }
+        }
+        double *o = part + ((long long)(I * nch + blockIdx.x) * 8) * N;
+        for (int r = 0; r < nr; ++r) o[(long long)r * N + j] = acc[r];
+    }
+}
+
+// Sum the chunk partials: outA[4I+f][j] (rows 0-3) and outB[4I+f][j] (rows 4-7).
+__global__ void k_support_sum(int natoms, int nch, int N, const double *part, double *outA, double *outB) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)natoms * 8 * N) return;
+    int j = (int)(idx % N);
+    int r = (int)((idx / N) % 8);
+    int I = (int)(idx / (8LL * N));
+    double s = 0.0;
+    for (int ch = 0; ch < nch; ++ch) s += part[((long long)(I * nch + ch) * 8 + r) * N + j];
+    if (r < 4) { if (outA) outA[(long long)(4 * I + r) * N + j] = s; }
+    else if (outB) outB[(long long)(4 * I + r - 4) * N + j] = s;
+}
+
+// W = D (Wc + Pa X_e)  (nonlocal strengths applied)
+template <typename T>
+__global__ void k_proj_w(int n_proj, int n_enr, const double *Wc, const double *Pa, const T *Xe, int ld,
+                         const double *D, int N, double *W) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)n_proj * N) return;
+    int p = (int)(idx / N), j = (int)(idx % N);
+    double s = Wc[idx];
+    if (Pa)
+        for (int k = 0; k < n_enr; ++k) s += Pa[(long long)p * n_enr + k] * (double)Xe[(long long)k * ld + j];
+    W[idx] = D[p] * s;
+}
+
+// Y_e,raw = R_hac + H_aa X_e + Pa^T W
+template <typename T>
+__global__ void k_enr_raw(int n_enr, int n_proj, const double *Rhac, const double *Haa, const double *Pa,
+                          const double *W, const T *Xe, int ld, int N, double *Ye) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)n_enr * N) return;
+    int k = (int)(idx / N), j = (int)(idx % N);
+    double s = Rhac[idx];
+    for (int k2 = 0; k2 < n_enr; ++k2) s += Haa[(long long)k * n_enr + k2] * (double)Xe[(long long)k2 * ld + j];
+    if (Pa)
+        for (int p = 0; p < n_proj; ++p) s += Pa[(long long)p * n_enr + k] * W[(long long)p * N + j];
+    Ye[idx] = s;
+}
+
+// Y_c[n] += sum_entries (Hca X_e + Pc W)
+template <typename T>
+__global__ void k_node_coupling(long long n_nodes, const long long *node_ptr, const int *node_ent,
+                                const int *ent_atom, const double *Hca, const double *Pc, const T *Xe,
+                                int ld, const double *W, int N, T *Y, int use_h, int use_p) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= n_nodes * N) return;
+    long long n = idx / N;
+    int j = (int)(idx % N);
+    long long e0 = node_ptr[n], e1 = node_ptr[n + 1];
+    if (e0 == e1) return;
+    double acc = 0.0;
+    for (long long e = e0; e < e1; ++e) {
+        int g = node_ent[e];
+        int I = ent_atom[g];
+        if (use_h) {
+            const double *h = Hca + 4 * (long long)g;
+            for (int f = 0; f < 4; ++f) acc += h[f] * (double)Xe[(long long)(4 * I + f) * ld + j];
+        }
+        if (use_p) {
+            const double *pc = Pc + 4 * (long long)g;
+            for (int f = 0; f < 4; ++f) acc += pc[f] * W[(long long)(4 * I + f) * N + j];
+        }
+    }
+    Y[n * ld + j] = (T)((double)Y[n * ld + j] + acc);
+}
+
+// Y_e = Y_e,raw - Q  written into the enriched rows of Y
+template <typename T>
+__global__ void k_enr_final(int n_enr, int N, const double *Yraw, const double *Q, T *Ye, int ld) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)n_enr * N) return;
+    int k = (int)(idx / N), j = (int)(idx % N);
+    Ye[(long long)k * ld + j] = (T)(Yraw[idx] - (Q ? Q[idx] : 0.0));
+}
+
+template <typename A, typename B>
+__global__ void k_cast(long long n, const A *x, B *y) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (B)x[i];
+}
+
+// ---- M^E, (M~^E)^-1 ------------------------------------------------------
+template <typename T>
+__global__ void k_diag_scale(long long n, int N, const double *d, const T *X, T *Y) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= n * N) return;
+    Y[idx] = (T)(d[idx / N] * (double)X[idx]);
+}
+// enriched rows: Y_e = A X_e with A dense (n_enr x n_enr) or atom blocks (4x4)
+template <typename T>
+__global__ void k_enr_mat(int n_enr, int N, const double *A, int blocks, const T *X, T *Y) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)n_enr * N) return;
+    int k = (int)(idx / N), j = (int)(idx % N);
+    double s = 0.0;
+    if (blocks) {
+        int I = k / 4, f = k % 4;
+        const double *b = A + 16 * I + 4 * f;
+        for (int g = 0; g < 4; ++g) s += b[g] * (double)X[(long long)(4 * I + g) * N + j];
+    } else {
+        for (int g = 0; g < n_enr; ++g) s += A[(long long)k * n_enr + g] * (double)X[(long long)g * N + j];
+    }
+    Y[idx] = (T)s;
+}
+
+// ---- residual Chebyshev recurrence ----------------------------------------
+// G = HV - MV diag(lam)
+__global__ void k_eig_residual(long long rows, int N, const double *HV, const double *MV, const double *lam,
+                               double *G) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= rows * N) return;
+    G[idx] = HV[idx] - MV[idx] * lam[idx % N];
+}
+// Z_k = a (HY - c Z1) - b Z0 + a G ck   (a = 2 s_k / e, b = s_{k-1} s_k)
+template <typename T>
+__global__ void k_recurrence(long long n, int N, double a, double c, double b, const T *HY, const T *Z1,
+                             const T *Z0, const double *G, const double *ck, T *Zn) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    double z0 = Z0 ? (double)Z0[idx] : 0.0;
+    double v = a * ((double)HY[idx] - c * (double)Z1[idx]) - b * z0 + a * G[idx] * ck[idx % N];
+    Zn[idx] = (T)v;
+}
+template <typename T>
+__global__ void k_scale_to(long long n, double s, const double *G, T *Z) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx < n) Z[idx] = (T)(s * G[idx]);
+}
+// Vout = Y + V diag(cm)   (Y = M~^-1 Z_m)
+template <typename T>
+__global__ void k_vout(long long n, int N, const T *Y, const double *V, const double *cm, double *Vout) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx < n) Vout[idx] = (double)Y[idx] + V[idx] * cm[idx % N];
+}
+
+// ---- Rayleigh-Ritz ----------------------------------------------------------
+// Partial Gram blocks: part[chunk][i][j] = sum_{r in chunk} A[r][i] B[r][j]
+__global__ void k_gram_partial(long long rows, int N, const double *A, const double *B, long long chunk,
+                               double *part) {
+    __shared__ double sA[32][33], sB[32][33];
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.z * 32;
+    const long long r0 = blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // 256 threads: ty 0..7
+    double acc[4] = {0, 0, 0, 0};
+    for (long long rb = r0; rb < r1; rb += 32) {
+        for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+            int rr = t / 32, cc = t % 32;
+            long long r = rb + rr;
+            sA[rr][cc] = (r < r1 && i0 + cc < N) ? A[r * N + i0 + cc] : 0.0;
+            sB[rr][cc] = (r < r1 && j0 + cc < N) ? B[r * N + j0 + cc] : 0.0;
+        }
+        __syncthreads();
+        for (int rr = 0; rr < 32; ++rr) {
+            double bv = sB[rr][tx];
+            for (int q = 0; q < 4; ++q) acc[q] += sA[rr][ty + 8 * q] * bv;
+        }
+        __syncthreads();
+    }
+    double *o = part + (long long)blockIdx.x * N * N;
+    for (int q = 0; q < 4; ++q) {
+        int i = i0 + ty + 8 * q, j = j0 + tx;
+        if (i < N && j < N) o[(long long)i * N + j] = acc[q];
+    }
+}
+__global__ void k_gram_sum(int N, int nch, const double *part, double *out) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)N * N) return;
+    double s = 0.0;
+    for (int c = 0; c < nch; ++c) s += part[(long long)c * N * N + idx];
+    out[idx] = s;
+}
+// symmetrise and scale (Jacobi): out_ij = (A_ij + A_ji)/2 / (d_i d_j), d_i = sqrt(S_ii)
+__global__ void k_rr_scale(int N, const double *S0, const double *H0, double *Ss, double *Hs, double *d) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)N * N) return;
+    int i = (int)(idx / N), j = (int)(idx % N);
+    double di = sqrt(S0[(long long)i * N + i]), dj = sqrt(S0[(long long)j * N + j]);
+    if (i == j) d[i] = di;
+    Hs[idx] = 0.5 * (H0[(long long)i * N + j] + H0[(long long)j * N + i]) / (di * dj);
+    Ss[idx] = 0.5 * (S0[(long long)i * N + j] + S0[(long long)j * N + i]) / (di * dj);
+}
+// Q (row-major) = D^-1 Qcol  : Qr[i][j] = Qc[i + j N] / d_i
+__global__ void k_rr_unscale(int N, const double *Qc, const double *d, double *Qr) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)N * N) return;
+    int i = (int)(idx / N), j = (int)(idx % N);
+    Qr[idx] = Qc[i + (long long)j * N] / d[i];
+}
+// out = in Q (rows x N) with Q row-major N x N
+__global__ void k_rotate(long long rows, int N, const double *in, const double *Q, double *out) {
+    extern __shared__ double sR[];   // 16 rows x N
+    const long long r0 = blockIdx.x * 16LL;
+    for (int t = threadIdx.x; t < 16 * N; t += blockDim.x) {
+        long long r = r0 + t / N;
+        sR[t] = r < rows ? in[r * N + (t % N)] : 0.0;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 16 * N; t += blockDim.x) {
+        int rr = t / N, j = t % N;
+        long long r = r0 + rr;
+        if (r >= rows) continue;
+        double s = 0.0;
+        for (int i = 0; i < N; ++i) s += sR[rr * N + i] * Q[(long long)i * N + j];
+        out[r * N + j] = s;
+    }
+}
+// column sums of squares of R = HX - MX diag(lam), partial per block
+__global__ void k_resid_partial(long long rows, int N, const double *HX, const double *MX, const double *lam,
+                                long long chunk, double *part) {
+    const long long r0 = blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double s = 0.0;
+        for (long long r = r0; r < r1; ++r) {
+            double v = HX[r * N + j] - MX[r * N + j] * lam[j];
+            s += v * v;
+        }
+        part[(long long)blockIdx.x * N + j] = s;
+    }
+}
+__global__ void k_colsum(int N, int nch, const double *part, double *out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    double s = 0.0;
+    for (int c = 0; c < nch; ++c) s += part[(long long)c * N + j];
+    out[j] = s;
+}
+// dot products of single vectors: partial sums
+__global__ void k_dot_partial(long long n, const double *a, const double *b, double *part) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += a[i] * b[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+__global__ void k_axpby3(long long n, double a, const double *x, double b, const double *y, double c,
+                         const double *z, double *out) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a * x[i] + b * y[i] + (z ? c * z[i] : 0.0);
+}
+
+// host: eigenvalues/vectors of a small symmetric matrix by cyclic Jacobi
+void jacobi_eig(int n, std::vector<double> A, std::vector<double> &w, std::vector<double> &V) {
+    V.assign(n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
+        if (off < 1e-30) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[p * n + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                double th = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * akq;
+                    A[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * aqk;
+                    A[q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - s * vkq;
+                    V[k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    w.resize(n);
+    for (int i = 0; i < n; ++i) w[i] = A[i * n + i];
+}
+
+// Chebyshev scalars C_k(lam_j), k = 0..m (Eq. ChebyRecur), table (m+1) x N
+void cheb_table(int m, int N, const double *lam, double a, double b, double a0, std::vector<double> &ck,
+                std::vector<double> &sig) {
+    const double e = 0.5 * (b - a), c = 0.5 * (b + a), s1 = e / (a0 - c);
+    ck.assign((size_t)(m + 1) * N, 0.0);
+    sig.assign(m + 1, 0.0);
+    sig[1] = s1;
+    for (int j = 0; j < N; ++j) {
+        ck[j] = 1.0;
+        if (m >= 1) ck[N + j] = s1 * (lam[j] - c) / e;
+    }
+    double sp = s1;
+    for (int k = 2; k <= m; ++k) {
+        double s = 1.0 / (2.0 / s1 - sp);
+        sig[k] = s;
+        for (int j = 0; j < N; ++j)
+            ck[(size_t)k * N + j] = (2.0 * s / e) * (lam[j] - c) * ck[(size_t)(k - 1) * N + j] -
+                                    sp * s * ck[(size_t)(k - 2) * N + j];
+        sp = s;
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// infrastructure
+// ===========================================================================
+efe_status efe_check_launch(efe_ctx *ctx, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+        return EFE_ERR_CUDA;
+    }
+    return EFE_OK;
+}
+efe_status efe_alloc(efe_ctx *ctx, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 8);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e);
+        return EFE_ERR_OOM;
+    }
+    return EFE_OK;
+}
+efe_status efe_workspace(efe_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->ws_bytes) return EFE_OK;
+    EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->d_ws) cudaFree(ctx->d_ws);
+    ctx->d_ws = nullptr;
+    ctx->ws_bytes = 0;
+    EFE_TRY(efe_alloc(ctx, &ctx->d_ws, bytes));
+    ctx->ws_bytes = bytes;
+    return EFE_OK;
+}
+efe_status efe_partials(efe_ctx *ctx, size_t doubles) {
+    if (doubles * 8 <= ctx->part_bytes) return EFE_OK;
+    EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->d_part) cudaFree(ctx->d_part);
+    ctx->d_part = nullptr;
+    ctx->part_bytes = 0;
+    EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_part, doubles * 8));
+    ctx->part_bytes = doubles * 8;
+    return EFE_OK;
+}
+efe_status efe_pinned(efe_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->pinned_bytes) return EFE_OK;
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    ctx->h_pinned = nullptr;
+    ctx->pinned_bytes = 0;
+    EFE_CUDA(ctx, cudaMallocHost((void **)&ctx->h_pinned, bytes));
+    ctx->pinned_bytes = bytes;
+    return EFE_OK;
+}
+
+namespace {
+
+// Scratch layout for one H^E product on N columns (doubles):
+//   Xp  n_nodes*N | part 64*natoms*8*N | Rh n_enr*N | Wc n_proj*N | W n_proj*N | Yraw n_enr*N | Q n_enr*N
+struct HxScratch {
+    double *part, *Rh, *Wc, *W, *Yraw, *Q;
+    int nch, chunk;
+};
+
+efe_status hx_scratch(efe_ctx *ctx, int N, HxScratch &s) {
+    long long maxsup = 0;
+    for (int I = 0; I < ctx->natoms; ++I) maxsup = std::max(maxsup, ctx->sup_off[I + 1] - ctx->sup_off[I]);
+    s.chunk = 1024;
+    s.nch = (int)std::max<long long>(1, (maxsup + s.chunk - 1) / s.chunk);
+    size_t need = (size_t)s.nch * std::max(ctx->natoms, 1) * 8 * N + (size_t)(3 * ctx->n_enr + 2 * ctx->n_proj) * N + 64;
+    EFE_TRY(efe_partials(ctx, need));
+    double *p = ctx->d_part;
+    s.part = p;
+    p += (size_t)s.nch * std::max(ctx->natoms, 1) * 8 * N;
+    s.Rh = p; p += (size_t)ctx->n_enr * N;
+    s.Wc = p; p += (size_t)ctx->n_proj * N;
+    s.W = p; p += (size_t)ctx->n_proj * N;
+    s.Yraw = p; p += (size_t)ctx->n_enr * N;
+    s.Q = p;
+    return EFE_OK;
+}
+
+}  // namespace
+
+// Generic H^E product for storage type T (double or float).  Xp: n_nodes x N scratch.
+template <typename T>
+static efe_status hx_generic(efe_ctx *ctx, const T *X, T *Y, int N, const T *He, T *Xp) {
+    const MeshDev &m = ctx->m;
+    const long long nn = ctx->n_nodes;
+    const int ld = N;
+    const bool cpl = (ctx->enrich || ctx->nonlocal) && ctx->natoms > 0;
+    HxScratch s{};
+    if (cpl) EFE_TRY(hx_scratch(ctx, N, s));
+    // (1) X' = T X (FE part)
+    k_xprime<T><<<nblk(nn * N, 256), 256, 0, ctx->stream>>>(m, nn, X, Xp, N, ld, ctx->d_node_ptr, ctx->d_node_ent,
+                                                            ctx->d_ent_atom, ctx->d_C, ctx->enrich ? 1 : 0);
+    ctx->launches++;
+    EFE_TRY(efe_check_launch(ctx, "k_xprime"));
+    // (2) cell products
+    EFE_CUDA(ctx, cudaMemsetAsync(Y, 0, sizeof(T) * ctx->n_rows * N, ctx->stream));
+    EFE_TRY(launch_cells<T>(ctx, He, (long long)m.ne * m.ne, Xp, Y, N, ld));
+    if (!cpl) return EFE_OK;
+    const T *Xe = X + nn * ld;
+    const long long *d_so = ctx->d_sup_off;
+    dim3 gr(s.nch, ctx->natoms);
+    // (3) R = [Hca; Pc] X'  (support reductions)
+    k_support_reduce<T><<<gr, 128, 0, ctx->stream>>>(d_so, ctx->d_sup_node, ctx->enrich ? ctx->d_Hca : ctx->d_Pc,
+                                                     (ctx->enrich && ctx->nonlocal) ? ctx->d_Pc : nullptr, Xp, N, ld,
+                                                     s.chunk, s.nch, s.part);
+    ctx->launches++;
+    EFE_TRY(efe_check_launch(ctx, "k_support_reduce"));
+    {
+        long long n = (long long)ctx->natoms * 8 * N;
+        double *oA = ctx->enrich ? s.Rh : s.Wc;
+        double *oB = (ctx->enrich && ctx->nonlocal) ? s.Wc : nullptr;
+        k_support_sum<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->natoms, s.nch, N, s.part, oA, oB);
+        ctx->launches++;
+    }
+    // (4) W and the raw enriched rows
+    if (ctx->nonlocal) {
+        k_proj_w<T><<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
+            ctx->n_proj, ctx->n_enr, s.Wc, ctx->enrich ? ctx->d_Pa : nullptr, Xe, ld, ctx->d_hproj, N, s.W);
+        ctx->launches++;
+    }
+    if (ctx->enrich) {
+        k_enr_raw<T><<<nblk((long long)ctx->n_enr * N, 256), 256, 0, ctx->stream>>>(
+            ctx->n_enr, ctx->n_proj, s.Rh, ctx->d_Haa, ctx->nonlocal ? ctx->d_Pa : nullptr, s.W, Xe, ld, N, s.Yraw);
+        ctx->launches++;
+    }
+    // (5) node-side coupling into Y_c
+    k_node_coupling<T><<<nblk(nn * N, 256), 256, 0, ctx->stream>>>(nn, ctx->d_node_ptr, ctx->d_node_ent,
+                                                                   ctx->d_ent_atom, ctx->d_Hca, ctx->d_Pc, Xe, ld, s.W,
+                                                                   N, Y, ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0);
+    ctx->launches++;
+    EFE_TRY(efe_check_launch(ctx, "k_node_coupling"));
+    if (!ctx->enrich) return EFE_OK;
+    // (6) Q = C Y_c and (7) Y_e = Y_e,raw - Q
+    k_support_reduce<T><<<gr, 128, 0, ctx->stream>>>(d_so, ctx->d_sup_node, ctx->d_C, nullptr, Y, N, ld, s.chunk,
+                                                     s.nch, s.part);
+    {
+        long long n = (long long)ctx->natoms * 8 * N;
+        k_support_sum<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->natoms, s.nch, N, s.part, s.Q, nullptr);
+    }
+    k_enr_final<T><<<nblk((long long)ctx->n_enr * N, 256), 256, 0, ctx->stream>>>(ctx->n_enr, N, s.Yraw, s.Q,
+                                                                                   Y + nn * ld, ld);
+    ctx->launches += 3;
+    return efe_check_launch(ctx, "k_enr_final");
+}
+
+
+// ===========================================================================
+// products used by the drivers
+// ===========================================================================
+template <typename T>
+static efe_status mtilde_inv(efe_ctx *ctx, const T *X, T *Y, int N) {
+    const long long nn = ctx->n_nodes;
+    k_diag_scale<T><<<nblk(nn * N, 256), 256, 0, ctx->stream>>>(nn, N, ctx->d_minv, X, Y);
+    ctx->launches++;
+    if (ctx->n_enr) {
+        k_enr_mat<T><<<nblk((long long)ctx->n_enr * N, 256), 256, 0, ctx->stream>>>(ctx->n_enr, N, ctx->d_Mblk_inv, 1,
+                                                                                    X + nn * N, Y + nn * N);
+        ctx->launches++;
+    }
+    return efe_check_launch(ctx, "mtilde_inv");
+}
+
+// M~ (the block-diagonal approximation itself) or exact M^E (full M^ee)
+static efe_status m_apply(efe_ctx *ctx, const double *X, double *Y, int N, bool exact) {
+    const long long nn = ctx->n_nodes;
+    k_diag_scale<double><<<nblk(nn * N, 256), 256, 0, ctx->stream>>>(nn, N, ctx->d_mcc, X, Y);
+    ctx->launches++;
+    if (ctx->n_enr) {
+        if (exact)
+            k_enr_mat<double><<<nblk((long long)ctx->n_enr * N, 256), 256, 0, ctx->stream>>>(
+                ctx->n_enr, N, ctx->d_Mee, 0, X + nn * N, Y + nn * N);
+        else
+            k_enr_mat<double><<<nblk((long long)ctx->n_enr * N, 256), 256, 0, ctx->stream>>>(
+                ctx->n_enr, N, ctx->d_Mblk, 1, X + nn * N, Y + nn * N);
+        ctx->launches++;
+    }
+    return efe_check_launch(ctx, "m_apply");
+}
+
+efe_status efe_hx(efe_ctx *ctx, const double *X, double *Y, int N, efe_precision prec, double *wsXp) {
+    (void)prec;
+    return hx_generic<double>(ctx, X, Y, N, ctx->d_He, wsXp);
+}
+efe_status efe_mx(efe_ctx *ctx, const double *X, double *Y, int N) { return m_apply(ctx, X, Y, N, true); }
+efe_status efe_minvx(efe_ctx *ctx, const double *X, double *Y, int N) { return mtilde_inv<double>(ctx, X, Y, N); }
+
+namespace {
+
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaStream_t s;
+    explicit Timer(cudaStream_t st) : s(st) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+    }
+    double stop() {
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        return ms;
+    }
+    ~Timer() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+// scratch carving from the big workspace
+struct Carver {
+    char *p;
+    size_t left;
+    template <typename T>
+    T *take(size_t n) {
+        size_t bytes = ((n * sizeof(T)) + 255) & ~size_t(255);
+        T *r = reinterpret_cast<T *>(p);
+        p += bytes;
+        left -= bytes;
+        return r;
+    }
+};
+
+template <typename T>
+efe_status filter_impl(efe_ctx *ctx, const double *V, const double *HV, const double *lam_dev, int N, int m,
+                       const double bounds[3], double *Vout) {
+    const long long rows = ctx->n_rows, nn = ctx->n_nodes;
+    const long long n = rows * N;
+    const double a0 = bounds[0], a = bounds[1], b = bounds[2];
+    if (!(b > a) || !(a0 < a)) {
+        ctx->err = "filter bounds must satisfy a0 < a < b";
+        return EFE_ERR_ARG;
+    }
+    std::vector<double> lam(N);
+    EFE_CUDA(ctx, cudaMemcpyAsync(lam.data(), lam_dev, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
+    EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<double> ck, sig;
+    cheb_table(m, N, lam.data(), a, b, a0, ck, sig);
+    const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+    size_t need = 256 * 16 + sizeof(double) * (2 * n + (size_t)(m + 1) * N) + sizeof(T) * (5 * n + nn * N);
+    EFE_TRY(efe_workspace(ctx, need));
+    Carver cv{(char *)ctx->d_ws, ctx->ws_bytes};
+    double *G = cv.take<double>(n), *MV = cv.take<double>(n), *dck = cv.take<double>((size_t)(m + 1) * N);
+    T *Z0 = cv.take<T>(n), *Z1 = cv.take<T>(n), *Z2 = cv.take<T>(n), *Y = cv.take<T>(n), *HY = cv.take<T>(n);
+    T *Xp = cv.take<T>((size_t)nn * N);
+    EFE_CUDA(ctx, cudaMemcpyAsync(dck, ck.data(), sizeof(double) * ck.size(), cudaMemcpyHostToDevice, ctx->stream));
+    Timer tm(ctx->stream);
+    const long long l0 = ctx->launches;
+    EFE_TRY(m_apply(ctx, V, MV, N, true));
+    k_eig_residual<<<nblk(n, 256), 256, 0, ctx->stream>>>(rows, N, HV, MV, lam_dev, G);
+    k_scale_to<T><<<nblk(n, 256), 256, 0, ctx->stream>>>(n, sig[1] / e, G, Z1);
+    ctx->launches += 2;
+    T *Zprev = nullptr, *Zcur = Z1, *Znext = Z2, *Zspare = Z0;
+    const T *He = std::is_same<T, double>::value ? (const T *)ctx->d_He : (const T *)ctx->d_He32;
+    for (int k = 2; k <= m; ++k) {
+        EFE_TRY(mtilde_inv<T>(ctx, Zcur, Y, N));
+        EFE_TRY(hx_generic<T>(ctx, Y, HY, N, He, Xp));
+        const double ak = 2.0 * sig[k] / e, bk = sig[k - 1] * sig[k];
+        k_recurrence<T><<<nblk(n, 256), 256, 0, ctx->stream>>>(n, N, ak, c, bk, HY, Zcur, Zprev, G,
+                                                               dck + (size_t)(k - 1) * N, Znext);
+        ctx->launches++;
+        EFE_TRY(efe_check_launch(ctx, "k_recurrence"));
+        T *old_prev = Zprev ? Zprev : Zspare;
+        Zprev = Zcur;
+        Zcur = Znext;
+        Znext = old_prev;
+    }
+    EFE_TRY(mtilde_inv<T>(ctx, Zcur, Y, N));
+    k_vout<T><<<nblk(n, 256), 256, 0, ctx->stream>>>(n, N, Y, V, dck + (size_t)m * N, Vout);
+    ctx->launches++;
+    EFE_TRY(efe_check_launch(ctx, "k_vout"));
+    ctx->stats.ms_filter = tm.stop();
+    ctx->stats.launches = ctx->launches - l0;
+    return EFE_OK;
+}
+
+}  // namespace
+
+efe_status efe_filter_dispatch(efe_ctx *ctx, const double *V, const double *HV, const double *lam, int N, int m,
+                               const double bounds[3], efe_precision prec, double *Vout) {
+    if (prec == EFE_FP64) return filter_impl<double>(ctx, V, HV, lam, N, m, bounds, Vout);
+    if (prec == EFE_FP32) return filter_impl<float>(ctx, V, HV, lam, N, m, bounds, Vout);
+    ctx->err = "EFE_BF16 filter is not available in this build";
+    return EFE_ERR_ARG;
+}
+
+// Rayleigh-Ritz (Eq. projectedKSEig), FP64.
+efe_status efe_rr_impl(efe_ctx *ctx, double *X, double *HX, int N, double *eig, double *resid) {
+    const long long rows = ctx->n_rows, nn = ctx->n_nodes;
+    const long long n = rows * N;
+    size_t need = 256 * 8 + sizeof(double) * (2 * n + nn * N);
+    EFE_TRY(efe_workspace(ctx, need));
+    Carver cv{(char *)ctx->d_ws, ctx->ws_bytes};
+    double *MX = cv.take<double>(n), *T1 = cv.take<double>(n), *Xp = cv.take<double>((size_t)nn * N);
+    Timer tm(ctx->stream);
+    EFE_TRY(hx_generic<double>(ctx, X, HX, N, ctx->d_He, Xp));
+    EFE_TRY(m_apply(ctx, X, MX, N, true));
+    const long long chunk = 4096;
+    const int nch = (int)((rows + chunk - 1) / chunk);
+    const size_t N2 = (size_t)N * N;
+    EFE_TRY(efe_partials(ctx, (size_t)nch * N2 + 6 * N2 + 4 * N + (size_t)nch * N));
+    double *part = ctx->d_part, *S0 = part + (size_t)nch * N2, *H0 = S0 + N2, *Ss = H0 + N2, *Hs = Ss + N2,
+           *Qr = Hs + N2, *d = Qr + N2, *W = d + N, *rs = W + N, *rpart = rs + N + N2;
+    dim3 g(nch, nblk(N, 32), nblk(N, 32));
+    k_gram_partial<<<g, 256, 0, ctx->stream>>>(rows, N, X, MX, chunk, part);
+    k_gram_sum<<<nblk(N2, 256), 256, 0, ctx->stream>>>(N, nch, part, S0);
+    k_gram_partial<<<g, 256, 0, ctx->stream>>>(rows, N, X, HX, chunk, part);
+    k_gram_sum<<<nblk(N2, 256), 256, 0, ctx->stream>>>(N, nch, part, H0);
+    ctx->launches += 4;
+    EFE_TRY(efe_check_launch(ctx, "gram"));
+    k_rr_scale<<<nblk(N2, 256), 256, 0, ctx->stream>>>(N, S0, H0, Ss, Hs, d);
+    ctx->launches++;
+    EFE_TRY(efe_check_launch(ctx, "k_rr_scale"));
+    if (cusolverDnSetStream(ctx->solver, ctx->stream) != CUSOLVER_STATUS_SUCCESS) {
+        ctx->err = "cusolverDnSetStream failed";
+        return EFE_ERR_CUDA;
+    }
+    int lwork = 0;
+    if (cusolverDnDsygvd_bufferSize(ctx->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                                    CUBLAS_FILL_MODE_UPPER, N, Hs, N, Ss, N, W, &lwork) != CUSOLVER_STATUS_SUCCESS) {
+        ctx->err = "cusolverDnDsygvd_bufferSize failed";
+        return EFE_ERR_CUDA;
+    }
+    if ((size_t)lwork * 8 > ctx->solver_ws_bytes) {
+        EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (ctx->d_solver_ws) cudaFree(ctx->d_solver_ws);
+        ctx->d_solver_ws = nullptr;
+        ctx->solver_ws_bytes = 0;
+        EFE_TRY(efe_alloc(ctx, &ctx->d_solver_ws, (size_t)lwork * 8));
+        ctx->solver_ws_bytes = (size_t)lwork * 8;
+    }
+    if (cusolverDnDsygvd(ctx->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, N, Hs,
+                         N, Ss, N, W, (double *)ctx->d_solver_ws, lwork, ctx->d_info) != CUSOLVER_STATUS_SUCCESS) {
+        ctx->err = "cusolverDnDsygvd failed";
+        return EFE_ERR_CUDA;
+    }
+    int info = 0;
+    EFE_CUDA(ctx, cudaMemcpyAsync(&info, ctx->d_info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (info != 0) {
+        ctx->err = "Rayleigh-Ritz: X^T M X is not positive definite (sygvd info " + std::to_string(info) + ")";
+        return info > N ? EFE_ERR_NOT_SPD : EFE_ERR_NO_CONVERGE;
+    }
+    k_rr_unscale<<<nblk(N2, 256), 256, 0, ctx->stream>>>(N, Hs, d, Qr);
+    const size_t shm = sizeof(double) * 16 * N;
+    cudaFuncSetAttribute(k_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    const unsigned rb = (unsigned)((rows + 15) / 16);
+    k_rotate<<<rb, 256, shm, ctx->stream>>>(rows, N, X, Qr, T1);
+    EFE_CUDA(ctx, cudaMemcpyAsync(X, T1, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    k_rotate<<<rb, 256, shm, ctx->stream>>>(rows, N, HX, Qr, T1);
+    EFE_CUDA(ctx, cudaMemcpyAsync(HX, T1, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    k_rotate<<<rb, 256, shm, ctx->stream>>>(rows, N, MX, Qr, T1);
+    EFE_CUDA(ctx, cudaMemcpyAsync(MX, T1, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    k_resid_partial<<<nch, 128, 0, ctx->stream>>>(rows, N, HX, MX, W, chunk, rpart);
+    k_colsum<<<nblk(N, 128), 128, 0, ctx->stream>>>(N, nch, rpart, rs);
+    ctx->launches += 6;
+    EFE_TRY(efe_check_launch(ctx, "rr rotate"));
+    std::vector<double> r2(N);
+    EFE_CUDA(ctx, cudaMemcpyAsync(eig, W, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
+    EFE_CUDA(ctx, cudaMemcpyAsync(r2.data(), rs, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
+    EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (resid)
+        for (int j = 0; j < N; ++j) resid[j] = std::sqrt(std::max(r2[j], 0.0));
+    ctx->stats.ms_rr = tm.stop();
+    return EFE_OK;
+}
+
+// k-step Lanczos for M~^-1 H in the M~ inner product.
+static efe_status lanczos_impl(efe_ctx *ctx, const double *u0, int k, double out[3]) {
+    const long long rows = ctx->n_rows, nn = ctx->n_nodes;
+    size_t need = 256 * 8 + sizeof(double) * (5 * rows + nn);
+    EFE_TRY(efe_workspace(ctx, need));
+    Carver cv{(char *)ctx->d_ws, ctx->ws_bytes};
+    double *q = cv.take<double>(rows), *qp = cv.take<double>(rows), *w = cv.take<double>(rows),
+           *r = cv.take<double>(rows), *t = cv.take<double>(rows), *Xp = cv.take<double>(nn);
+    const int nb = 256;
+    EFE_TRY(efe_partials(ctx, nb));
+    Timer tm(ctx->stream);
+    std::vector<double> hp(nb);
+    auto dot = [&](const double *a, const double *b, double &res) -> efe_status {
+        k_dot_partial<<<nb, 256, 0, ctx->stream>>>(rows, a, b, ctx->d_part);
+        ctx->launches++;
+        EFE_CUDA(ctx, cudaMemcpyAsync(hp.data(), ctx->d_part, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+        EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        res = 0.0;
+        for (int i = 0; i < nb; ++i) res += hp[i];
+        return EFE_OK;
+    };
+    EFE_TRY(m_apply(ctx, u0, t, 1, false));
+    double nrm2;
+    EFE_TRY(dot(u0, t, nrm2));
+    if (!(nrm2 > 0.0)) {
+        ctx->err = "Lanczos start vector has zero norm";
+        return EFE_ERR_ARG;
+    }
+    k_axpby3<<<nblk(rows, 256), 256, 0, ctx->stream>>>(rows, 1.0 / std::sqrt(nrm2), u0, 0.0, u0, 0.0, nullptr, q);
+    EFE_CUDA(ctx, cudaMemsetAsync(qp, 0, sizeof(double) * rows, ctx->stream));
+    std::vector<double> al, be;
+    double beta = 0.0;
+    for (int j = 0; j < k; ++j) {
+        EFE_TRY(hx_generic<double>(ctx, q, w, 1, ctx->d_He, Xp));
+        double alpha;
+        EFE_TRY(dot(q, w, alpha));
+        EFE_TRY(mtilde_inv<double>(ctx, w, r, 1));
+        k_axpby3<<<nblk(rows, 256), 256, 0, ctx->stream>>>(rows, 1.0, r, -alpha, q, -beta, qp, r);
+        EFE_TRY(m_apply(ctx, r, t, 1, false));
+        double b2;
+        EFE_TRY(dot(r, t, b2));
+        beta = std::sqrt(std::max(b2, 0.0));
+        al.push_back(alpha);
+        be.push_back(beta);
+        if (beta == 0.0) break;
+        std::swap(qp, q);
+        k_axpby3<<<nblk(rows, 256), 256, 0, ctx->stream>>>(rows, 1.0 / beta, r, 0.0, r, 0.0, nullptr, q);
+        ctx->launches += 2;
+    }
+    const int kk = (int)al.size();
+    std::vector<double> Tm(kk * kk, 0.0), wv, Vv;
+    for (int i = 0; i < kk; ++i) {
+        Tm[i * kk + i] = al[i];
+        if (i + 1 < kk) Tm[i * kk + i + 1] = Tm[(i + 1) * kk + i] = be[i];
+    }
+    jacobi_eig(kk, Tm, wv, Vv);
+    int imin = 0, imax = 0;
+    for (int i = 1; i < kk; ++i) {
+        if (wv[i] < wv[imin]) imin = i;
+        if (wv[i] > wv[imax]) imax = i;
+    }
+    out[0] = wv[imin];
+    out[1] = wv[imax];
+    out[2] = wv[imax] + std::fabs(be[kk - 1] * Vv[(kk - 1) * kk + imax]);
+    ctx->stats.ms_lanczos = tm.stop();
+    return EFE_OK;
+}
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+static thread_local std::string g_setup_err;
+
+#define EFE_CHECK_CTX(ctx)                                  \
+    do {                                                    \
+        if (!(ctx)) return EFE_ERR_ARG;                     \
+    } while (0)
+#define EFE_ARG(ctx, cond, msg)                             \
+    do {                                                    \
+        if (!(cond)) {                                      \
+            (ctx)->err = (msg);                             \
+            return EFE_ERR_ARG;                             \
+        }                                                   \
+    } while (0)
+
+extern "C" {
+
+const char *efe_last_error(const efe_ctx *ctx) { return ctx ? ctx->err.c_str() : g_setup_err.c_str(); }
+
+void efe_destroy(efe_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    void *ptrs[] = {ctx->d_B1, ctx->d_D1, ctx->d_wq, ctx->d_Khat, ctx->d_mcc, ctx->d_minv, ctx->d_He, ctx->d_He32,
+                    ctx->d_He16, ctx->d_atoms, ctx->d_hproj, ctx->d_sup_off, ctx->d_sup_node, ctx->d_C, ctx->d_B,
+                    ctx->d_Kca, ctx->d_Hca, ctx->d_Pc, ctx->d_node_ptr, ctx->d_node_ent, ctx->d_ent_atom,
+                    ctx->d_pairs, ctx->d_pair_pos, ctx->d_cell_atom_ptr, ctx->d_cell_atoms, ctx->d_Aee, ctx->d_Kaa,
+                    ctx->d_Haa, ctx->d_Mee, ctx->d_Pa, ctx->d_Mblk_inv, ctx->d_Mblk, ctx->d_ws, ctx->d_part,
+                    ctx->d_info, ctx->d_solver_ws};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->solver) cusolverDnDestroy(ctx->solver);
+    delete ctx;
+}
+
+efe_status efe_setup(const efe_mesh *mesh, const efe_atoms *atoms, const efe_enrichment *enrich,
+                     const efe_psp *psp, void *stream, efe_ctx **out) {
+    g_setup_err.clear();
+    if (!out || !mesh || !atoms) {
+        g_setup_err = "efe_setup: null argument";
+        return EFE_ERR_ARG;
+    }
+    *out = nullptr;
+    auto fail = [&](const char *msg) {
+        g_setup_err = msg;
+        return EFE_ERR_ARG;
+    };
+    if (!(mesh->h > 0.0)) return fail("mesh h must be > 0");
+    if (mesh->degree < 1 || mesh->degree > EFE_MAXP) return fail("degree must be in [1, 8]");
+    for (int d = 0; d < 3; ++d)
+        if (mesh->ncell[d] < 1) return fail("ncell must be >= 1");
+    const int nq = mesh->nquad > 0 ? mesh->nquad : mesh->degree + 2;
+    if (nq > EFE_MAXNQ || nq < mesh->degree + 1) return fail("nquad must be in [p+1, 12]");
+    if (atoms->natoms < 0 || (atoms->natoms > 0 && (!atoms->xyz || !atoms->zval))) return fail("bad atoms");
+    const bool en = enrich && enrich->enabled;
+    const bool nl = psp && psp->enabled;
+    if (en && !(enrich->alpha > 0.0 && enrich->r_end > 0.0 && enrich->t > 0.0)) return fail("bad enrichment");
+    if (nl && (!(psp->rc > 0.0) || !(psp->r_trunc > 0.0) || (atoms->natoms > 0 && !psp->h)))
+        return fail("bad pseudopotential");
+    efe_ctx *ctx = new efe_ctx();
+    ctx->stream = (cudaStream_t)stream;
+    MeshDev &m = ctx->m;
+    m.nx = mesh->ncell[0];
+    m.ny = mesh->ncell[1];
+    m.nz = mesh->ncell[2];
+    m.p = mesh->degree;
+    m.np1 = m.p + 1;
+    m.ne = m.np1 * m.np1 * m.np1;
+    m.nq = nq;
+    m.nq3 = nq * nq * nq;
+    m.h = mesh->h;
+    m.Gx = m.nx * m.p + 1;
+    m.Gy = m.ny * m.p + 1;
+    m.Gz = m.nz * m.p + 1;
+    ctx->natoms = atoms->natoms;
+    ctx->enrich = en && atoms->natoms > 0;
+    ctx->nonlocal = nl && atoms->natoms > 0;
+    ctx->n_enr = ctx->enrich ? 4 * ctx->natoms : 0;
+    ctx->n_proj = ctx->nonlocal ? 4 * ctx->natoms : 0;
+    ctx->n_nodes = (long long)m.Gx * m.Gy * m.Gz;
+    ctx->n_rows = ctx->n_nodes + ctx->n_enr;
+    ctx->n_fe_dof = (long long)(m.Gx - 2) * (m.Gy - 2) * (m.Gz - 2);
+    ctx->n_quad = (long long)m.nx * m.ny * m.nz * m.nq3;
+    if (ctx->enrich) {
+        ctx->alpha = enrich->alpha;
+        ctx->t = enrich->t;
+        ctx->r0 = enrich->r_end * enrich->t / (1.0 + enrich->t);
+    }
+    if (ctx->nonlocal) {
+        ctx->rc = psp->rc;
+        ctx->rtrunc = psp->r_trunc;
+    }
+    if (psp) ctx->rloc = psp->rloc > 0 ? psp->rloc : 0.8;
+    ctx->xyz.assign(atoms->xyz, atoms->xyz + 3 * atoms->natoms);
+    ctx->zval.assign(atoms->zval, atoms->zval + atoms->natoms);
+    const double L[3] = {m.nx * m.h, m.ny * m.h, m.nz * m.h};
+    for (int I = 0; I < ctx->natoms; ++I)
+        for (int d = 0; d < 3; ++d) {
+            double x = ctx->xyz[3 * I + d];
+            if (x < 0.0 || x > L[d]) { delete ctx; return fail("atom outside the box"); }
+            if (ctx->enrich && (x - enrich->r_end < -1e-12 || x + enrich->r_end > L[d] + 1e-12)) {
+                delete ctx;
+                return fail("enrichment support leaves the box (Dirichlet boundary)");
+            }
+        }
+    auto bail = [&](efe_status st) {
+        g_setup_err = ctx->err;
+        efe_destroy(ctx);
+        return st;
+    };
+    efe_status st;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        ctx->err = "invalid CUDA stream or no device";
+        return bail(EFE_ERR_CUDA);
+    }
+    if (cusolverDnCreate(&ctx->solver) != CUSOLVER_STATUS_SUCCESS) {
+        ctx->err = "cusolverDnCreate failed";
+        return bail(EFE_ERR_CUDA);
+    }
+    if ((st = efe_alloc(ctx, (void **)&ctx->d_info, sizeof(int))) != EFE_OK) return bail(st);
+    if ((st = efe_alloc(ctx, (void **)&ctx->d_atoms, sizeof(double) * 3 * std::max(1, ctx->natoms))) != EFE_OK)
+        return bail(st);
+    if (ctx->natoms && cudaMemcpy(ctx->d_atoms, ctx->xyz.data(), sizeof(double) * 3 * ctx->natoms,
+                                  cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(EFE_ERR_CUDA);
+    if (ctx->nonlocal) {
+        ctx->hproj.assign(psp->h, psp->h + 2 * ctx->natoms);
+        std::vector<double> D(ctx->n_proj);
+        for (int I = 0; I < ctx->natoms; ++I) {
+            D[4 * I] = ctx->hproj[2 * I];
+            for (int mm = 1; mm < 4; ++mm) D[4 * I + mm] = ctx->hproj[2 * I + 1];
+        }
+        if ((st = efe_alloc(ctx, (void **)&ctx->d_hproj, sizeof(double) * ctx->n_proj)) != EFE_OK) return bail(st);
+        if (cudaMemcpy(ctx->d_hproj, D.data(), sizeof(double) * ctx->n_proj, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(EFE_ERR_CUDA);
+    }
+    if ((st = efe_build_tables(ctx)) != EFE_OK) return bail(st);
+    if ((st = efe_static_integrals(ctx)) != EFE_OK) return bail(st);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        ctx->err = std::string("setup: ") + cudaGetErrorString(cudaGetLastError());
+        return bail(EFE_ERR_CUDA);
+    }
+    *out = ctx;
+    return EFE_OK;
+}
+
+efe_status efe_get_dims(const efe_ctx *ctx, efe_dims *d) {
+    if (!ctx || !d) return EFE_ERR_ARG;
+    d->n_nodes = ctx->n_nodes;
+    d->n_fe_dof = ctx->n_fe_dof;
+    d->n_rows = ctx->n_rows;
+    d->n_quad = ctx->n_quad;
+    d->n_enr = ctx->n_enr;
+    d->n_proj = ctx->n_proj;
+    d->n_cells = ctx->m.nx * ctx->m.ny * ctx->m.nz;
+    d->ne = ctx->m.ne;
+    d->nq = ctx->m.nq;
+    d->grid[0] = ctx->m.Gx;
+    d->grid[1] = ctx->m.Gy;
+    d->grid[2] = ctx->m.Gz;
+    return EFE_OK;
+}
+
+efe_status efe_get_stats(const efe_ctx *ctx, efe_stats *s) {
+    if (!ctx || !s) return EFE_ERR_ARG;
+    *s = ctx->stats;
+    return EFE_OK;
+}
+
+efe_status efe_set_potential(efe_ctx *ctx, const double *veff_q) {
+    EFE_CHECK_CTX(ctx);
+    EFE_ARG(ctx, veff_q, "veff_q is null");
+    EFE_TRY(efe_potential_assembly(ctx, veff_q));
+    EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return EFE_OK;
+}
+
+efe_status efe_apply_h(efe_ctx *ctx, const double *X, double *Y, int N, efe_precision prec) {
+    EFE_CHECK_CTX(ctx);
+    EFE_ARG(ctx, X && Y && X != Y && N > 0, "efe_apply_h: bad arguments");
+    if (!ctx->have_potential) {
+        ctx->err = "efe_apply_h: no potential set";
+        return EFE_ERR_STATE;
+    }
+    const long long n = ctx->n_rows * N;
+    if (prec == EFE_FP64) {
+        EFE_TRY(efe_workspace(ctx, sizeof(double) * ctx->n_nodes * N + 256));
+        return hx_generic<double>(ctx, X, Y, N, ctx->d_He, (double *)ctx->d_ws);
+    }
+    if (prec == EFE_FP32) {
+        EFE_TRY(efe_workspace(ctx, sizeof(float) * (2 * n + ctx->n_nodes * N) + 1024));
+        Carver cv{(char *)ctx->d_ws, ctx->ws_bytes};
+        float *Xf = cv.take<float>(n), *Yf = cv.take<float>(n), *Xp = cv.take<float>((size_t)ctx->n_nodes * N);
+        k_cast<double, float><<<nblk(n, 256), 256, 0, ctx->stream>>>(n, X, Xf);
+        EFE_TRY(hx_generic<float>(ctx, Xf, Yf, N, ctx->d_He32, Xp));
+        k_cast<float, double><<<nblk(n, 256), 256, 0, ctx->stream>>>(n, Yf, Y);
+        return efe_check_launch(ctx, "apply_h fp32");
+    }
+    ctx->err = "efe_apply_h: precision not available";
+    return EFE_ERR_ARG;
+}
+
+efe_status efe_apply_m(efe_ctx *ctx, const double *X, double *Y, int N) {
+    EFE_CHECK_CTX(ctx);
+    EFE_ARG(ctx, X && Y && X != Y && N > 0, "efe_apply_m: bad arguments");
+    return m_apply(ctx, X, Y, N, true);
+}
+
+efe_status efe_apply_minv(efe_ctx *ctx, const double *X, double *Y, int N) {
+    EFE_CHECK_CTX(ctx);
+    EFE_ARG(ctx, X && Y && X != Y && N > 0, "efe_apply_minv: bad arguments");
+    return mtilde_inv<double>(ctx, X, Y, N);
+}
+
+efe_status efe_lanczos(efe_ctx *ctx, const double *u0, int k, double out[3]) {
+    EFE_CHECK_CTX(ctx);
+    EFE_ARG(ctx, u0 && out && k >= 1 && k <= 100, "efe_lanczos: bad arguments");
+    if (!ctx->have_potential) {
+        ctx->err = "efe_lanczos: no potential set";
+        return EFE_ERR_STATE;
+    }
+    return lanczos_impl(ctx, u0, k, out);
+}
+
+efe_status efe_filter(efe_ctx *ctx, const double *V, const double *HV, const double *lam, int N, int m,
+                      const double bounds[3], efe_precision prec, double *Vout) {
+    EFE_CHECK_CTX(ctx);
+    EFE_ARG(ctx, V && HV && lam && bounds && Vout && N > 0 && m >= 1 && Vout != V && Vout != HV,
+            "efe_filter: bad arguments");
+    if (!ctx->have_potential) {
+        ctx->err = "efe_filter: no potential set";
+        return EFE_ERR_STATE;
+    }
+    return efe_filter_dispatch(ctx, V, HV, lam, N, m, bounds, prec, Vout);
+}
+
+efe_status efe_rayleigh_ritz(efe_ctx *ctx, double *X, double *HX, int N, double *eig, double *resid) {
+    EFE_CHECK_CTX(ctx);
+    EFE_ARG(ctx, X && HX && eig && N > 0 && X != HX, "efe_rayleigh_ritz: bad arguments");
+    if (!ctx->have_potential) {
+        ctx->err = "efe_rayleigh_ritz: no potential set";
+        return EFE_ERR_STATE;
+    }
+    return efe_rr_impl(ctx, X, HX, N, eig, resid);
+}
+
+efe_status efe_chfsi(efe_ctx *ctx, double *X, double *HX, int N, int m, const double *bounds, const double *u0,
+                     int max_pass, double tol, int nconv, efe_precision prec, double *eig, double *resid,
+                     int *passes) {
+    EFE_CHECK_CTX(ctx);
+    EFE_ARG(ctx, X && eig && resid && N > 0 && m >= 1 && max_pass >= 0 && (bounds || u0),
+            "efe_chfsi: bad arguments");
+    if (!ctx->have_potential) {
+        ctx->err = "efe_chfsi: no potential set";
+        return EFE_ERR_STATE;
+    }
+    if (nconv <= 0 || nconv > N) nconv = N;
+    const long long n = ctx->n_rows * N;
+    // persistent buffers for HX (if not given), Vout and lam
+    double *dHX = HX, *dVout = nullptr, *dlam = nullptr;
+    std::vector<void *> owned;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(ctx->stream);
+        for (void *p : owned) cudaFree(p);
+    };
+    if (!dHX) {
+        if (efe_alloc(ctx, (void **)&dHX, sizeof(double) * n) != EFE_OK) return EFE_ERR_OOM;
+        owned.push_back(dHX);
+    }
+    if (efe_alloc(ctx, (void **)&dVout, sizeof(double) * n) != EFE_OK) { cleanup(); return EFE_ERR_OOM; }
+    owned.push_back(dVout);
+    if (efe_alloc(ctx, (void **)&dlam, sizeof(double) * N) != EFE_OK) { cleanup(); return EFE_ERR_OOM; }
+    owned.push_back(dlam);
+    double bd[3];
+    efe_status st = EFE_OK;
+    if (bounds) {
+        bd[0] = bounds[0];
+        bd[1] = bounds[1];
+        bd[2] = bounds[2];
+    } else {
+        double lz[3];
+        if ((st = lanczos_impl(ctx, u0, 10, lz)) != EFE_OK) { cleanup(); return st; }
+        bd[0] = lz[0];
+        bd[1] = lz[0] + 0.3 * (lz[2] - lz[0]);
+        bd[2] = lz[2];
+    }
+    if ((st = efe_rr_impl(ctx, X, dHX, N, eig, resid)) != EFE_OK) { cleanup(); return st; }
+    double ms_filter = 0.0, ms_rr = 0.0;
+    int pass = 0;
+    bool conv = false;
+    while (pass < max_pass) {
+        if (cudaMemcpyAsync(dlam, eig, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+            cleanup();
+            return EFE_ERR_CUDA;
+        }
+        if ((st = efe_filter_dispatch(ctx, X, dHX, dlam, N, m, bd, prec, dVout)) != EFE_OK) { cleanup(); return st; }
+        ms_filter += ctx->stats.ms_filter;
+        if ((st = efe_rr_impl(ctx, dVout, dHX, N, eig, resid)) != EFE_OK) { cleanup(); return st; }
+        ms_rr += ctx->stats.ms_rr;
+        if (cudaMemcpyAsync(X, dVout, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) {
+            cleanup();
+            return EFE_ERR_CUDA;
+        }
+        ++pass;
+        double mx = 0.0;
+        for (int j = 0; j < nconv; ++j) mx = std::max(mx, resid[j]);
+        bd[0] = eig[0];
+        bd[1] = eig[N - 1];
+        if (mx < tol) { conv = true; break; }
+    }
+    cleanup();
+    ctx->stats.ms_filter = ms_filter;
+    ctx->stats.ms_rr = ms_rr;
+    ctx->stats.passes = pass;
+    if (passes) *passes = pass;
+    return (conv || max_pass == 0) ? EFE_OK : EFE_ERR_NO_CONVERGE;
+}
+
+efe_status efe_filter_host(efe_ctx *ctx, const double *V, const double *HV, const double *lam, int N, int m,
+                           const double bounds[3], efe_precision prec, double *Vout) {
+    EFE_CHECK_CTX(ctx);
+    EFE_ARG(ctx, V && HV && lam && bounds && Vout && N > 0 && m >= 1, "efe_filter_host: bad arguments");
+    const long long n = ctx->n_rows * N;
+    double *dV = nullptr, *dHV = nullptr, *dO = nullptr, *dl = nullptr;
+    std::vector<void *> owned;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(ctx->stream);
+        for (void *p : owned) cudaFree(p);
+    };
+    for (double **p : {&dV, &dHV, &dO}) {
+        if (efe_alloc(ctx, (void **)p, sizeof(double) * n) != EFE_OK) { cleanup(); return EFE_ERR_OOM; }
+        owned.push_back(*p);
+    }
+    if (efe_alloc(ctx, (void **)&dl, sizeof(double) * N) != EFE_OK) { cleanup(); return EFE_ERR_OOM; }
+    owned.push_back(dl);
+    efe_status st = EFE_OK;
+    if (cudaMemcpyAsync(dV, V, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(dHV, HV, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(dl, lam, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+        ctx->err = "efe_filter_host: host-to-device copy failed";
+        cleanup();
+        return EFE_ERR_CUDA;
+    }
+    st = efe_filter(ctx, dV, dHV, dl, N, m, bounds, prec, dO);
+    if (st == EFE_OK && cudaMemcpyAsync(Vout, dO, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) {
+        ctx->err = "efe_filter_host: device-to-host copy failed";
+        st = EFE_ERR_CUDA;
+    }
+    cleanup();
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+"""Thin ctypes binding of libefe (include/efe.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module only converts Python
+and torch arguments into the C structs and raw pointers the ABI expects.  It
+raises if the compiled library is missing -- there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libefe.so")
+
+EFE_FP64, EFE_FP32, EFE_BF16 = 0, 1, 2
+PRECISIONS = {"fp64": EFE_FP64, "fp32": EFE_FP32, "bf16": EFE_BF16}
+STATUS = {0: "EFE_OK", 1: "EFE_ERR_ARG", 2: "EFE_ERR_CUDA", 3: "EFE_ERR_NOT_SPD",
+          4: "EFE_ERR_NO_CONVERGE", 5: "EFE_ERR_TIMEOUT", 6: "EFE_ERR_OOM", 7: "EFE_ERR_STATE"}
+
+
+class efe_mesh(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_double), ("ncell", ctypes.c_int * 3), ("degree", ctypes.c_int),
+                ("nquad", ctypes.c_int)]
+
+
+class efe_atoms(ctypes.Structure):
+    _fields_ = [("natoms", ctypes.c_int), ("xyz", ctypes.POINTER(ctypes.c_double)),
+                ("zval", ctypes.POINTER(ctypes.c_double))]
+
+
+class efe_enrichment(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int), ("alpha", ctypes.c_double), ("r_end", ctypes.c_double),
+                ("t", ctypes.c_double)]
+
+
+class efe_psp(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int), ("rc", ctypes.c_double), ("r_trunc", ctypes.c_double),
+                ("h", ctypes.POINTER(ctypes.c_double)), ("rloc", ctypes.c_double)]
+
+
+class efe_dims(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_longlong), ("n_fe_dof", ctypes.c_longlong),
+                ("n_rows", ctypes.c_longlong), ("n_quad", ctypes.c_longlong), ("n_enr", ctypes.c_int),
+                ("n_proj", ctypes.c_int), ("n_cells", ctypes.c_int), ("ne", ctypes.c_int),
+                ("nq", ctypes.c_int), ("grid", ctypes.c_int * 3)]
+
+
+class efe_stats(ctypes.Structure):
+    _fields_ = [("ms_filter", ctypes.c_double), ("ms_rr", ctypes.c_double), ("ms_lanczos", ctypes.c_double),
+                ("ms_cell", ctypes.c_double), ("launches", ctypes.c_longlong), ("passes", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.c_int
+SIGNATURES = {
+    "efe_setup": [ctypes.POINTER(efe_mesh), ctypes.POINTER(efe_atoms), ctypes.POINTER(efe_enrichment),
+                  ctypes.POINTER(efe_psp), _P, ctypes.POINTER(_P)],
+    "efe_destroy": [_P],
+    "efe_last_error": [_P],
+    "efe_get_dims": [_P, ctypes.POINTER(efe_dims)],
+    "efe_get_stats": [_P, ctypes.POINTER(efe_stats)],
+    "efe_set_potential": [_P, _P],
+    "efe_apply_h": [_P, _P, _P, _I, _I],
+    "efe_apply_m": [_P, _P, _P, _I],
+    "efe_apply_minv": [_P, _P, _P, _I],
+    "efe_lanczos": [_P, _P, _I, _D],
+    "efe_filter": [_P, _P, _P, _P, _I, _I, _D, _I, _P],
+    "efe_rayleigh_ritz": [_P, _P, _P, _I, _D, _D],
+    "efe_chfsi": [_P, _P, _P, _I, _I, _D, _P, _I, ctypes.c_double, _I, _I, _D, _D, ctypes.POINTER(_I)],
+    "efe_filter_host": [_P, _D, _D, _D, _I, _I, _D, _I, _D],
+}
+
+_lib = None
+
+
+def load():
+    """Load libefe.so (built in-tree by paper_2607_06848_gb300.build).  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libefe.so is not built: run `python -m paper_2607_06848_gb300.build` "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, args in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name == "efe_last_error" else (None if name == "efe_destroy" else ctypes.c_int)
+    _lib = lib
+    return lib
+
+
+class EFEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def _ptr(t):
+    """Raw device pointer of a contiguous CUDA tensor."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _darr(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_D)
+
+
+class EFE:
+    """One EFE discretisation on the current CUDA device (wraps an efe_ctx)."""
+
+    def __init__(self, h, ncell, degree, atoms, zval, enrich=None, psp=None, nquad=0, stream=None):
+        import torch
+        self.lib = load()
+        self._keep = []
+        mesh = efe_mesh(float(h), (ctypes.c_int * 3)(*[int(v) for v in ncell]), int(degree), int(nquad))
+        xyz, pxyz = _darr(np.asarray(atoms, float).reshape(-1, 3))
+        z, pz = _darr(zval)
+        self._keep += [xyz, z]
+        at = efe_atoms(len(z), pxyz, pz)
+        en = efe_enrichment(0, 0.0, 0.0, 0.0)
+        if enrich is not None:
+            en = efe_enrichment(1, float(enrich["alpha"]), float(enrich["r_end"]), float(enrich["t"]))
+        ps = efe_psp(0, 0.0, 0.0, None, 0.8)
+        if psp is not None:
+            hh, ph = _darr(np.asarray(psp["h"], float).reshape(-1, 2))
+            self._keep.append(hh)
+            ps = efe_psp(1, float(psp["rc"]), float(psp["r_trunc"]), ph, float(psp.get("rloc", 0.8)))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        ctx = ctypes.c_void_p()
+        st = self.lib.efe_setup(ctypes.byref(mesh), ctypes.byref(at), ctypes.byref(en), ctypes.byref(ps),
+                                ctypes.c_void_p(stream.cuda_stream), ctypes.byref(ctx))
+        if st != 0:
+            raise EFEError(st, self.lib.efe_last_error(None).decode())
+        self.ctx = ctx
+        d = efe_dims()
+        self._check(self.lib.efe_get_dims(self.ctx, ctypes.byref(d)))
+        self.dims = {k: (list(getattr(d, k)) if k == "grid" else getattr(d, k)) for k, _ in efe_dims._fields_}
+
+    def _check(self, st):
+        if st != 0:
+            raise EFEError(st, self.lib.efe_last_error(self.ctx).decode())
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.efe_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- marshalling wrappers with the ABI names -------------------------
+    def stats(self):
+        s = efe_stats()
+        self._check(self.lib.efe_get_stats(self.ctx, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in efe_stats._fields_}
+
+    def efe_set_potential(self, veff_q):
+        self._check(self.lib.efe_set_potential(self.ctx, _ptr(veff_q)))
+
+    def efe_apply_h(self, X, Y, prec=EFE_FP64):
+        self._check(self.lib.efe_apply_h(self.ctx, _ptr(X), _ptr(Y), X.shape[1], prec))
+
+    def efe_apply_m(self, X, Y):
+        self._check(self.lib.efe_apply_m(self.ctx, _ptr(X), _ptr(Y), X.shape[1]))
+
+    def efe_apply_minv(self, X, Y):
+        self._check(self.lib.efe_apply_minv(self.ctx, _ptr(X), _ptr(Y), X.shape[1]))
+
+    def efe_lanczos(self, u0, k=10):
+        out = (ctypes.c_double * 3)()
+        self._check(self.lib.efe_lanczos(self.ctx, _ptr(u0), int(k), out))
+        return tuple(out)
+
+    def efe_filter(self, V, HV, lam, m, bounds, Vout, prec=EFE_FP64):
+        b = (ctypes.c_double * 3)(*[float(x) for x in bounds])
+        self._check(self.lib.efe_filter(self.ctx, _ptr(V), _ptr(HV), _ptr(lam), V.shape[1], int(m), b,
+                                        int(prec), _ptr(Vout)))
+
+    def efe_rayleigh_ritz(self, X, HX):
+        N = X.shape[1]
+        eig = (ctypes.c_double * N)()
+        res = (ctypes.c_double * N)()
+        self._check(self.lib.efe_rayleigh_ritz(self.ctx, _ptr(X), _ptr(HX), N, eig, res))
+        return np.array(eig[:]), np.array(res[:])
+
+    def efe_chfsi(self, X, m, bounds=None, u0=None, max_pass=20, tol=1e-8, nconv=0, prec=EFE_FP64, HX=None):
+        N = X.shape[1]
+        eig = (ctypes.c_double * N)()
+        res = (ctypes.c_double * N)()
+        passes = ctypes.c_int(0)
+        b = None if bounds is None else (ctypes.c_double * 3)(*[float(x) for x in bounds])
+        st = self.lib.efe_chfsi(self.ctx, _ptr(X), _ptr(HX), N, int(m), b, _ptr(u0), int(max_pass),
+                                float(tol), int(nconv), int(prec), eig, res, ctypes.byref(passes))
+        if st not in (0, 4):
+            self._check(st)
+        return np.array(eig[:]), np.array(res[:]), passes.value, st == 0
+
+    def efe_filter_host(self, V, HV, lam, m, bounds, prec=EFE_FP64):
+        """Host arrays in and out (the library copies on its stream)."""
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        HV = np.ascontiguousarray(HV, dtype=np.float64)
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        out = np.empty_like(V)
+        b = (ctypes.c_double * 3)(*[float(x) for x in bounds])
+        self._check(self.lib.efe_filter_host(self.ctx, V.ctypes.data_as(_D), HV.ctypes.data_as(_D),
+                                             lam.ctypes.data_as(_D), V.shape[1], int(m), b, int(prec),
+                                             out.ctypes.data_as(_D)))
+        return out
