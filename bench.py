@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Residual Chebyshev filter throughput on one GB300 (GDOF*vec*deg/s).
+
+Workload (default): 64-atom seeded cluster (Z = 4, >= 4.2 bohr apart) in a
+40-bohr cube, 24^3 cells of degree 6 (145^3 GLL grid, 2.92M interior FE DOF)
++ 256 enrichment DOF, 154 vectors, filter degree 30, bounds from a 10-step
+Lanczos.  One step = one residual filter pass (eigen-residual G, 29 steps of
+the recurrence with H M~^-1, V_out) -- the "filter" of the metric.
+value = (FE DOF + enriched DOF) * vectors * degree / step time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU runs are independent replicas (one per rank), weak scaling.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ChFSI GDOF·vec·deg/s, mixed vs FP64 at |ΔE|≤1e-5 Ha/atom; SCF time-to-solution"
+UNIT = "GDOF*vec*deg/s"
+T_ENR, R_END, ALPHA = 0.33, 5.0, 1.2
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload(name):
+    from paper_2607_06848_gb300 import workloads as W
+    if name == "cluster64":
+        return W.cluster64()
+    if name == "dimer":
+        return W.dimer()
+    raise SystemExit("unknown workload " + name)
+
+
+def cpu_sample(steps=1, warmup=0):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload:
+    the 64-atom cluster's discretisation (h = 40/24 bohr, degree 6, Gauss 8^3)
+    on a 6^3-cell sub-box around one atom, 16 vectors, filter degree 30.
+    Returns (GDOF*vec*deg/s, seconds per step, description, threads)."""
+    from oracle.fe import Mesh
+    from oracle.efe import EFESystem
+    from oracle import chfsi as OC
+    from paper_2607_06848_gb300 import workloads as W
+    h = 40.0 / 24.0
+    mesh = Mesh(h, (6, 6, 6), 6)
+    atom = np.array([[5.0, 5.0, 5.0]])
+    osys = EFESystem(mesh, atom, enrich=dict(alpha=ALPHA, r0=R_END * T_ENR / (1 + T_ENR), t=T_ENR),
+                     proj=dict(rc=1.0, rtrunc=6.0, h=np.array([[1.0, -0.5]])))
+    osys.set_potential(W.soft_coulomb_potential(mesh.all_quad_points(), atom))
+    N, m = 16, 30
+    V = W.random_block(osys.nn + osys.n_enr, N, 7)
+    V[:osys.nn] *= osys.mask[:, None]
+    lam, V, HV = OC.rayleigh_ritz(osys, V)
+    b = OC.lanczos_bounds(osys, W.random_block(osys.nn + osys.n_enr, 1, 8), 10)[2]
+    for _ in range(warmup):
+        OC.residual_filter(osys, V, lam, m, lam[-1], b, lam[0], HV=HV)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        OC.residual_filter(osys, V, lam, m, lam[-1], b, lam[0], HV=HV)
+    dt = (time.perf_counter() - t0) / max(steps, 1)
+    M = int(osys.mask.sum()) + osys.n_enr
+    desc = ("oracle residual filter (FP64 NumPy/SciPy) on a 6^3-cell sub-box of the cluster64 "
+            "discretisation around one atom: %d DOF x %d vectors x degree %d, %d steps"
+            % (M, N, m, steps))
+    return M * N * m / dt / 1e9, dt, desc, os.cpu_count()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    val, dt, desc, cores = cpu_sample(steps=args.steps, warmup=args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cluster64 (sampled sub-box for the CPU oracle)", "vectors": 16,
+                       "filter_degree": 30},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def roofline(head, d, N, ms_sweep, pk, pk_kind):
+    """Roofline of the dominant kernel (the cell products), from its live CUDA-event time."""
+    if head == "bf16":
+        # tensor-core cell products stream H_e (bf16, n_e^2), gather X'_e (bf16,
+        # n_e N) and write Y_e (fp32, n_e N) per cell: 2 n_e^2 N flop against
+        # 2 n_e^2 + 6 n_e N bytes -> ~66 flop/B at N = 154, below the ridge
+        # (~292 flop/B), so HBM-bound
+        traffic_alg = d["n_cells"] * (2.0 * d["ne"] ** 2 + 6.0 * d["ne"] * N)
+        achieved = traffic_alg / (ms_sweep / 1e3) / 1e9 if ms_sweep > 0 else None
+        return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"] if achieved else None, "traffic": None,
+                "algorithmic_bytes": traffic_alg, "peak_kind": pk_kind + " (burst copy)",
+                "kernel": "k_cell_mma (tcgen05 cell products, one launch per H apply)",
+                "ms_per_launch": ms_sweep}
+    # SIMT cell products: FP32 (or FP64) FMA pipes, 152 SMs x lanes x 2 flop x max clock
+    lanes = 128 if head == "fp32" else 2
+    peak = 152 * lanes * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    flops = d["n_cells"] * 2.0 * d["ne"] ** 2 * N
+    achieved = flops / (ms_sweep / 1e3) / 1e12 if ms_sweep > 0 else None
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None, "traffic": None,
+            "peak_kind": "derived from SM count and max clock",
+            "kernel": "k_cell_apply (SIMT cell products, 8 colour launches per H apply)",
+            "ms_per_launch": ms_sweep}
+
+
+def run_ours(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2607_06848_gb300 import EFE, workloads as W, EFE_FP64, EFE_FP32, EFE_BF16
+    w = workload(args.workload)
+    t_setup = time.perf_counter()
+    g = EFE(w["h"], w["ncell"], w["p"], w["atoms"], w["Z"], enrich=dict(alpha=ALPHA, r_end=R_END, t=T_ENR),
+            psp=dict(rc=1.0, r_trunc=6.0, h=w["hproj"]))
+    d = g.dims
+    q = torch.tensor(W.quad_points(w["h"], w["ncell"], d["nq"]), device=dev)
+    v = torch.zeros(q.shape[0], dtype=torch.float64, device=dev)
+    for a in w["atoms"]:
+        v -= 3.0 / torch.sqrt(0.5 + ((q - torch.tensor(a, device=dev)) ** 2).sum(1))
+    del q
+    g.efe_set_potential(v)
+    rows, N, m = d["n_rows"], w["nstates"], w["cheb_degree"]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234)
+    X = torch.randn((rows, N), generator=gen, dtype=torch.float64, device=dev)
+    HX = torch.empty_like(X)
+    eig, res = g.efe_rayleigh_ritz(X, HX)
+    u0 = torch.randn((rows, 1), generator=gen, dtype=torch.float64, device=dev)
+    tmin, tmax, b = g.efe_lanczos(u0, 10)
+    bounds = (float(eig[0]), float(eig[-1]), float(b))
+    lam = torch.tensor(eig, device=dev)
+    Vout = torch.empty_like(X)
+    t_setup = time.perf_counter() - t_setup
+    M = d["n_fe_dof"] + d["n_enr"]
+    units = M * N * m
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            g.efe_filter(X, HX, lam, m, bounds, Vout, prec=prec)
+        barrier()
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cells_ms = 0.0
+        launches = 0
+        e0.record(s)
+        for _ in range(steps):
+            g.efe_filter(X, HX, lam, m, bounds, Vout, prec=prec)
+            st = g.stats()
+            cells_ms += st["ms_cell"]
+            launches += st["launches"]
+        e1.record(s)
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, cells_ms / steps, launches
+
+    precs = {"fp64": EFE_FP64, "fp32": EFE_FP32, "bf16": EFE_BF16}
+    head = args.prec
+    clk = ClockSampler(local)
+    ms, cell_ms, launches = timed(precs[head], args.steps, args.warmup)
+    clocks = clk.stop()
+    by_prec = {head: {"ms_per_step": ms, "value": units / (ms / 1e3) / 1e9, "steps": args.steps}}
+    for extra in args.also:
+        if extra != head:
+            mse, _, _ = timed(precs[extra], 1, 0)
+            by_prec[extra] = {"ms_per_step": mse, "value": units / (mse / 1e3) / 1e9, "steps": 1}
+
+    # end to end through the public call with host buffers (pinned)
+    Vh = torch.empty((rows, N), dtype=torch.float64, pin_memory=True)
+    HVh = torch.empty_like(Vh)
+    lamh = torch.tensor(eig, dtype=torch.float64).contiguous()
+    Vh.copy_(X.cpu())
+    HVh.copy_(HX.cpu())
+    e2e_steps = max(1, min(args.steps, 3))
+    g.efe_filter_host(Vh.numpy(), HVh.numpy(), lamh.numpy(), m, bounds, prec=precs[head])
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        out_h = g.efe_filter_host(Vh.numpy(), HVh.numpy(), lamh.numpy(), m, bounds, prec=precs[head])
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = (2 * rows * N + N) * 8
+    d2h = rows * N * 8
+    del out_h
+
+    pk, pk_kind = peaks()
+    ms_sweep = cell_ms / (m - 1)          # m - 1 H applies per filter pass
+    line = {
+        "metric": METRIC, "value": units / (ms / 1e3) / 1e9 * world, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[head],
+        "data": "synthetic",
+        "config": {"workload": "%s: %d atoms, %dx%dx%d cells p=%d (%d FE DOF + %d enriched), %d vectors, "
+                               "filter degree %d" % (w["name"], len(w["atoms"]), *w["ncell"], w["p"],
+                                                     d["n_fe_dof"], d["n_enr"], N, m),
+                   "precision": head, "l2": "inputs larger than L2 (%.2f GB per block)" % (rows * N * 8 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "potential": "seeded soft-Coulomb stand-in"},
+        "by_precision": by_prec,
+        "roofline": roofline(head, d, N, ms_sweep, pk, pk_kind),
+        "e2e": {"value": units / e2e_s / 1e9 * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "setup_s": t_setup,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        val, dt, desc, cores = cpu_sample(steps=6, warmup=0)
+        line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--also", nargs="*", default=["fp32", "fp64"],
+                    help="other precisions timed once for the by_precision table")
+    ap.add_argument("--workload", default="cluster64")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

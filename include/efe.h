@@ -120,8 +120,9 @@ typedef struct {
     double ms_filter;
     double ms_rr;
     double ms_lanczos;
-    double ms_cell;      /* the cell-product kernels inside the filter */
-    long long launches;
+    double ms_cell;      /* the cell-product sweeps inside the last filter */
+    long long launches;  /* kernels launched by the last filter */
+    long long cell_launches; /* of which cell-product kernels */
     int passes;
 } efe_stats;
 

@@ -2,6 +2,8 @@
 // Lanczos bounds and the C ABI entry points (paper Sec. II.B, III.A, III.B).
 #include "efe_internal.cuh"
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -57,9 +59,33 @@ __global__ void __launch_bounds__(256) k_cell_apply(MeshDev m, int colour, const
     }
 }
 
+// events bracketing one sweep of cell products (reused across calls)
+std::pair<cudaEvent_t, cudaEvent_t> *cell_event_pair(efe_ctx *ctx) {
+    if (ctx->cell_events_used == ctx->cell_events.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess) return nullptr;
+        if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return nullptr; }
+        ctx->cell_events.push_back({a, b});
+    }
+    return &ctx->cell_events[ctx->cell_events_used++];
+}
+
+// sum of the recorded sweeps (the stream must have been synchronised)
+double cell_events_ms(efe_ctx *ctx) {
+    double t = 0.0;
+    for (size_t i = 0; i < ctx->cell_events_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->cell_events[i].first, ctx->cell_events[i].second) == cudaSuccess) t += ms;
+    }
+    ctx->cell_events_used = 0;
+    return t;
+}
+
 template <typename T>
 efe_status launch_cells(efe_ctx *ctx, const T *He, long long he_stride, const T *X, T *Y, int N, int ld) {
     const MeshDev &m = ctx->m;
+    auto *ev = cell_event_pair(ctx);
+    if (ev) cudaEventRecord(ev->first, ctx->stream);
     for (int colour = 0; colour < 8; ++colour) {
         const int ox = colour & 1, oy = (colour >> 1) & 1, oz = (colour >> 2) & 1;
         const int hx = (m.nx - ox + 1) / 2, hy = (m.ny - oy + 1) / 2, hz = (m.nz - oz + 1) / 2;
@@ -82,8 +108,10 @@ efe_status launch_cells(efe_ctx *ctx, const T *He, long long he_stride, const T 
             k_cell_apply<T, 32><<<g, 256, shm, ctx->stream>>>(m, colour, He, he_stride, X, Y, N, ld);
         }
         ctx->launches++;
+        ctx->cell_launches++;
         EFE_TRY(efe_check_launch(ctx, "k_cell_apply"));
     }
+    if (ev) cudaEventRecord(ev->second, ctx->stream);
     return EFE_OK;
 }
 
@@ -114,6 +142,10 @@ __global__ void k_xprime(MeshDev m, long long n_nodes, const T *X, T *Xp, int N,
     Xp[n * ld + j] = v;
 }
 
+__device__ inline double to_d(double x) { return x; }
+__device__ inline double to_d(float x) { return (double)x; }
+__device__ inline double to_d(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+
 // Partial support reductions: for atom I (blockIdx.y) and chunk blockIdx.x,
 //   part[(I*nch + chunk)][r][j] = sum_{g in chunk} coef_r[g] * S[node(g)][j]
 // with up to 8 coefficient rows (two 4-wide tables A and B).
@@ -128,7 +160,7 @@ __global__ void k_support_reduce(const long long *sup_off, const int *sup_node, 
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (long long g = beg; g < end; ++g) {
-            double s = (double)S[(long long)sup_node[g] * ld + j];
+            double s = to_d(S[(long long)sup_node[g] * ld + j]);
             const double *a = coefA + 4 * g;
             acc[0] += a[0] * s; acc[1] += a[1] * s; acc[2] += a[2] * s; acc[3] += a[3] * s;
             if (coefB) {
@@ -221,6 +253,93 @@ template <typename A, typename B>
 __global__ void k_cast(long long n, const A *x, B *y) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) y[i] = (B)x[i];
+}
+
+// X' = Y_c - C^T Y_e rounded to bf16 with row stride ldb (padding columns and
+// boundary rows zero): the B operand of the tensor-core cell products.
+__global__ void k_xprime_bf16(MeshDev m, long long n_nodes, const float *Y, int N, int ldb,
+                              const long long *node_ptr, const int *node_ent, const int *ent_atom,
+                              const double *C, int use_c, __nv_bfloat16 *Xb) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= n_nodes * ldb) return;
+    long long n = idx / ldb;
+    int j = (int)(idx % ldb);
+    int ix = (int)(n % m.Gx), iy = (int)((n / m.Gx) % m.Gy), iz = (int)(n / ((long long)m.Gx * m.Gy));
+    float out = 0.f;
+    if (j < N && node_interior(m, ix, iy, iz)) {
+        double v = (double)Y[n * N + j];
+        if (use_c) {
+            const float *Ye = Y + n_nodes * N;
+            for (long long e = node_ptr[n]; e < node_ptr[n + 1]; ++e) {
+                int g = node_ent[e];
+                int I = ent_atom[g];
+                const double *c = C + 4 * (long long)g;
+                v -= c[0] * (double)Ye[(4 * I + 0) * (long long)N + j] + c[1] * (double)Ye[(4 * I + 1) * (long long)N + j] +
+                     c[2] * (double)Ye[(4 * I + 2) * (long long)N + j] + c[3] * (double)Ye[(4 * I + 3) * (long long)N + j];
+            }
+        }
+        out = (float)v;
+    }
+    Xb[idx] = __float2bfloat16_rn(out);
+}
+
+// HY_c[n] = sum over the cells containing node n of their per-cell product
+// rows, plus the node-side coupling (H^ca X_e + P_c^T W).  Boundary rows 0.
+__global__ void k_gather(MeshDev m, long long n_nodes, int N, const float *Yc, int ldy,
+                         const long long *node_ptr, const int *node_ent, const int *ent_atom, const double *Hca,
+                         const double *Pc, const float *Xe, const double *W, int use_h, int use_p, float *HY) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= n_nodes * N) return;
+    long long n = idx / N;
+    int j = (int)(idx % N);
+    int ix = (int)(n % m.Gx), iy = (int)((n / m.Gx) % m.Gy), iz = (int)(n / ((long long)m.Gx * m.Gy));
+    if (!node_interior(m, ix, iy, iz)) { HY[idx] = 0.f; return; }
+    int cxv[2], axv[2], cyv[2], ayv[2], czv[2], azv[2];
+    int nxc = 0, nyc = 0, nzc = 0;
+    auto split = [&](int i, int ncell, int *cv, int *av, int &cnt) {
+        int q = i / m.p, r = i % m.p;
+        if (r == 0) {
+            if (q - 1 >= 0) { cv[cnt] = q - 1; av[cnt] = m.p; ++cnt; }
+            if (q < ncell) { cv[cnt] = q; av[cnt] = 0; ++cnt; }
+        } else {
+            cv[cnt] = q; av[cnt] = r; ++cnt;
+        }
+    };
+    split(ix, m.nx, cxv, axv, nxc);
+    split(iy, m.ny, cyv, ayv, nyc);
+    split(iz, m.nz, czv, azv, nzc);
+    double acc = 0.0;
+    for (int a = 0; a < nzc; ++a)
+        for (int b = 0; b < nyc; ++b)
+            for (int c = 0; c < nxc; ++c) {
+                long long cell = ((long long)czv[a] * m.ny + cyv[b]) * m.nx + cxv[c];
+                int l = (azv[a] * m.np1 + ayv[b]) * m.np1 + axv[c];
+                acc += (double)Yc[(cell * m.ne + l) * ldy + j];
+            }
+    if (node_ptr) {
+        for (long long e = node_ptr[n]; e < node_ptr[n + 1]; ++e) {
+            int g = node_ent[e];
+            int I = ent_atom[g];
+            if (use_h) {
+                const double *h = Hca + 4 * (long long)g;
+                for (int f = 0; f < 4; ++f) acc += h[f] * (double)Xe[(long long)(4 * I + f) * N + j];
+            }
+            if (use_p) {
+                const double *pc = Pc + 4 * (long long)g;
+                for (int f = 0; f < 4; ++f) acc += pc[f] * W[(long long)(4 * I + f) * N + j];
+            }
+        }
+    }
+    HY[idx] = (float)acc;
+}
+
+// zero the Dirichlet boundary rows of a block (they are not unknowns)
+__global__ void k_zero_boundary(MeshDev m, long long n_nodes, int N, double *X) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= n_nodes * N) return;
+    long long n = idx / N;
+    int ix = (int)(n % m.Gx), iy = (int)((n / m.Gx) % m.Gy), iz = (int)(n / ((long long)m.Gx * m.Gy));
+    if (!node_interior(m, ix, iy, iz)) X[idx] = 0.0;
 }
 
 // ---- M^E, (M~^E)^-1 ------------------------------------------------------
@@ -595,6 +714,66 @@ static efe_status hx_generic(efe_ctx *ctx, const T *X, T *Y, int N, const T *He,
 }
 
 
+// H^E Y with the cell products on tcgen05 tensor cores (bf16 operands, FP32
+// accumulate); Y, HY: float rows x N.  Scratch: Xb (bf16 n_nodes x ldb) and
+// Ycells (float n_cells x ne x ldy).
+static efe_status hx_bf16(efe_ctx *ctx, const float *Y, float *HY, int N, __nv_bfloat16 *Xb, float *Ycells) {
+    const MeshDev &m = ctx->m;
+    const long long nn = ctx->n_nodes;
+    const int ldb = (N + 7) / 8 * 8, ldy = (N + 3) / 4 * 4;
+    const bool cpl = (ctx->enrich || ctx->nonlocal) && ctx->natoms > 0;
+    HxScratch s{};
+    if (cpl) EFE_TRY(hx_scratch(ctx, N, s));
+    k_xprime_bf16<<<nblk(nn * ldb, 256), 256, 0, ctx->stream>>>(m, nn, Y, N, ldb, ctx->d_node_ptr, ctx->d_node_ent,
+                                                               ctx->d_ent_atom, ctx->d_C, ctx->enrich ? 1 : 0, Xb);
+    ctx->launches++;
+    EFE_TRY(efe_check_launch(ctx, "k_xprime_bf16"));
+    {
+        auto *ev = cell_event_pair(ctx);
+        if (ev) cudaEventRecord(ev->first, ctx->stream);
+        EFE_TRY(efe_tc_cells(ctx, Xb, ldb, N, Ycells, ldy, ctx->d_err));
+        if (ev) cudaEventRecord(ev->second, ctx->stream);
+    }
+    const float *Ye = Y + nn * N;
+    if (cpl) {
+        dim3 gr(s.nch, ctx->natoms);
+        k_support_reduce<__nv_bfloat16><<<gr, 128, 0, ctx->stream>>>(
+            ctx->d_sup_off, ctx->d_sup_node, ctx->enrich ? ctx->d_Hca : ctx->d_Pc,
+            (ctx->enrich && ctx->nonlocal) ? ctx->d_Pc : nullptr, Xb, N, ldb, s.chunk, s.nch, s.part);
+        long long n8 = (long long)ctx->natoms * 8 * N;
+        k_support_sum<<<nblk(n8, 256), 256, 0, ctx->stream>>>(ctx->natoms, s.nch, N, s.part,
+                                                              ctx->enrich ? s.Rh : s.Wc,
+                                                              (ctx->enrich && ctx->nonlocal) ? s.Wc : nullptr);
+        ctx->launches += 2;
+        if (ctx->nonlocal) {
+            k_proj_w<float><<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
+                ctx->n_proj, ctx->n_enr, s.Wc, ctx->enrich ? ctx->d_Pa : nullptr, Ye, N, ctx->d_hproj, N, s.W);
+            ctx->launches++;
+        }
+        if (ctx->enrich) {
+            k_enr_raw<float><<<nblk((long long)ctx->n_enr * N, 256), 256, 0, ctx->stream>>>(
+                ctx->n_enr, ctx->n_proj, s.Rh, ctx->d_Haa, ctx->nonlocal ? ctx->d_Pa : nullptr, s.W, Ye, N, N, s.Yraw);
+            ctx->launches++;
+        }
+    }
+    k_gather<<<nblk(nn * N, 256), 256, 0, ctx->stream>>>(m, nn, N, Ycells, ldy, cpl ? ctx->d_node_ptr : nullptr,
+                                                         ctx->d_node_ent, ctx->d_ent_atom, ctx->d_Hca, ctx->d_Pc, Ye,
+                                                         s.W, ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0, HY);
+    ctx->launches++;
+    EFE_TRY(efe_check_launch(ctx, "k_gather"));
+    if (ctx->enrich) {
+        dim3 gr(s.nch, ctx->natoms);
+        k_support_reduce<float><<<gr, 128, 0, ctx->stream>>>(ctx->d_sup_off, ctx->d_sup_node, ctx->d_C, nullptr, HY,
+                                                             N, N, s.chunk, s.nch, s.part);
+        long long n8 = (long long)ctx->natoms * 8 * N;
+        k_support_sum<<<nblk(n8, 256), 256, 0, ctx->stream>>>(ctx->natoms, s.nch, N, s.part, s.Q, nullptr);
+        k_enr_final<float><<<nblk((long long)ctx->n_enr * N, 256), 256, 0, ctx->stream>>>(ctx->n_enr, N, s.Yraw, s.Q,
+                                                                                           HY + nn * N, N);
+        ctx->launches += 3;
+    }
+    return efe_check_launch(ctx, "hx_bf16");
+}
+
 // ===========================================================================
 // products used by the drivers
 // ===========================================================================
@@ -674,7 +853,7 @@ struct Carver {
 
 template <typename T>
 efe_status filter_impl(efe_ctx *ctx, const double *V, const double *HV, const double *lam_dev, int N, int m,
-                       const double bounds[3], double *Vout) {
+                       const double bounds[3], double *Vout, bool tensor = false) {
     const long long rows = ctx->n_rows, nn = ctx->n_nodes;
     const long long n = rows * N;
     const double a0 = bounds[0], a = bounds[1], b = bounds[2];
@@ -688,13 +867,25 @@ efe_status filter_impl(efe_ctx *ctx, const double *V, const double *HV, const do
     std::vector<double> ck, sig;
     cheb_table(m, N, lam.data(), a, b, a0, ck, sig);
     const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+    const int ldb = (N + 7) / 8 * 8, ldy = (N + 3) / 4 * 4;
+    const long long ncells = (long long)ctx->m.nx * ctx->m.ny * ctx->m.nz;
     size_t need = 256 * 16 + sizeof(double) * (2 * n + (size_t)(m + 1) * N) + sizeof(T) * (5 * n + nn * N);
+    if (tensor) need += 512 + 2 * (size_t)nn * ldb + 4 * (size_t)ncells * ctx->m.ne * ldy;
     EFE_TRY(efe_workspace(ctx, need));
     Carver cv{(char *)ctx->d_ws, ctx->ws_bytes};
     double *G = cv.take<double>(n), *MV = cv.take<double>(n), *dck = cv.take<double>((size_t)(m + 1) * N);
     T *Z0 = cv.take<T>(n), *Z1 = cv.take<T>(n), *Z2 = cv.take<T>(n), *Y = cv.take<T>(n), *HY = cv.take<T>(n);
     T *Xp = cv.take<T>((size_t)nn * N);
+    __nv_bfloat16 *Xb = nullptr;
+    float *Ycells = nullptr;
+    if (tensor) {
+        Xb = cv.take<__nv_bfloat16>((size_t)nn * ldb);
+        Ycells = cv.take<float>((size_t)ncells * ctx->m.ne * ldy);
+        EFE_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    }
     EFE_CUDA(ctx, cudaMemcpyAsync(dck, ck.data(), sizeof(double) * ck.size(), cudaMemcpyHostToDevice, ctx->stream));
+    ctx->cell_events_used = 0;
+    ctx->cell_launches = 0;
     Timer tm(ctx->stream);
     const long long l0 = ctx->launches;
     EFE_TRY(m_apply(ctx, V, MV, N, true));
@@ -705,7 +896,15 @@ efe_status filter_impl(efe_ctx *ctx, const double *V, const double *HV, const do
     const T *He = std::is_same<T, double>::value ? (const T *)ctx->d_He : (const T *)ctx->d_He32;
     for (int k = 2; k <= m; ++k) {
         EFE_TRY(mtilde_inv<T>(ctx, Zcur, Y, N));
-        EFE_TRY(hx_generic<T>(ctx, Y, HY, N, He, Xp));
+        if constexpr (std::is_same<T, float>::value) {
+            if (tensor) {
+                EFE_TRY(hx_bf16(ctx, Y, HY, N, Xb, Ycells));
+            } else {
+                EFE_TRY(hx_generic<T>(ctx, Y, HY, N, He, Xp));
+            }
+        } else {
+            EFE_TRY(hx_generic<T>(ctx, Y, HY, N, He, Xp));
+        }
         const double ak = 2.0 * sig[k] / e, bk = sig[k - 1] * sig[k];
         k_recurrence<T><<<nblk(n, 256), 256, 0, ctx->stream>>>(n, N, ak, c, bk, HY, Zcur, Zprev, G,
                                                                dck + (size_t)(k - 1) * N, Znext);
@@ -721,7 +920,17 @@ efe_status filter_impl(efe_ctx *ctx, const double *V, const double *HV, const do
     ctx->launches++;
     EFE_TRY(efe_check_launch(ctx, "k_vout"));
     ctx->stats.ms_filter = tm.stop();
+    ctx->stats.ms_cell = cell_events_ms(ctx);
     ctx->stats.launches = ctx->launches - l0;
+    ctx->stats.cell_launches = ctx->cell_launches;
+    if (tensor) {
+        int flag = 0;
+        EFE_CUDA(ctx, cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) {
+            ctx->err = "tensor-core cell product: a bounded wait gave up (role " + std::to_string(flag) + ")";
+            return EFE_ERR_TIMEOUT;
+        }
+    }
     return EFE_OK;
 }
 
@@ -731,7 +940,11 @@ efe_status efe_filter_dispatch(efe_ctx *ctx, const double *V, const double *HV, 
                                const double bounds[3], efe_precision prec, double *Vout) {
     if (prec == EFE_FP64) return filter_impl<double>(ctx, V, HV, lam, N, m, bounds, Vout);
     if (prec == EFE_FP32) return filter_impl<float>(ctx, V, HV, lam, N, m, bounds, Vout);
-    ctx->err = "EFE_BF16 filter is not available in this build";
+    if (prec == EFE_BF16) {
+        if (!ctx->he16_valid) EFE_TRY(efe_tc_prepare(ctx));
+        return filter_impl<float>(ctx, V, HV, lam, N, m, bounds, Vout, true);
+    }
+    ctx->err = "unknown precision";
     return EFE_ERR_ARG;
 }
 
@@ -744,6 +957,8 @@ efe_status efe_rr_impl(efe_ctx *ctx, double *X, double *HX, int N, double *eig, 
     Carver cv{(char *)ctx->d_ws, ctx->ws_bytes};
     double *MX = cv.take<double>(n), *T1 = cv.take<double>(n), *Xp = cv.take<double>((size_t)nn * N);
     Timer tm(ctx->stream);
+    k_zero_boundary<<<nblk(nn * N, 256), 256, 0, ctx->stream>>>(ctx->m, nn, N, X);
+    ctx->launches++;
     EFE_TRY(hx_generic<double>(ctx, X, HX, N, ctx->d_He, Xp));
     EFE_TRY(m_apply(ctx, X, MX, N, true));
     const long long chunk = 4096;
@@ -913,10 +1128,14 @@ void efe_destroy(efe_ctx *ctx) {
                     ctx->d_Kca, ctx->d_Hca, ctx->d_Pc, ctx->d_node_ptr, ctx->d_node_ent, ctx->d_ent_atom,
                     ctx->d_pairs, ctx->d_pair_pos, ctx->d_cell_atom_ptr, ctx->d_cell_atoms, ctx->d_Aee, ctx->d_Kaa,
                     ctx->d_Haa, ctx->d_Mee, ctx->d_Pa, ctx->d_Mblk_inv, ctx->d_Mblk, ctx->d_ws, ctx->d_part,
-                    ctx->d_info, ctx->d_solver_ws};
+                    ctx->d_info, ctx->d_err, ctx->d_solver_ws};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    for (auto &e : ctx->cell_events) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
     if (ctx->solver) cusolverDnDestroy(ctx->solver);
     delete ctx;
 }
@@ -1006,6 +1225,8 @@ efe_status efe_setup(const efe_mesh *mesh, const efe_atoms *atoms, const efe_enr
         return bail(EFE_ERR_CUDA);
     }
     if ((st = efe_alloc(ctx, (void **)&ctx->d_info, sizeof(int))) != EFE_OK) return bail(st);
+    if ((st = efe_alloc(ctx, (void **)&ctx->d_err, sizeof(int))) != EFE_OK) return bail(st);
+    if (cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) return bail(EFE_ERR_CUDA);
     if ((st = efe_alloc(ctx, (void **)&ctx->d_atoms, sizeof(double) * 3 * std::max(1, ctx->natoms))) != EFE_OK)
         return bail(st);
     if (ctx->natoms && cudaMemcpy(ctx->d_atoms, ctx->xyz.data(), sizeof(double) * 3 * ctx->natoms,
@@ -1083,6 +1304,29 @@ efe_status efe_apply_h(efe_ctx *ctx, const double *X, double *Y, int N, efe_prec
         EFE_TRY(hx_generic<float>(ctx, Xf, Yf, N, ctx->d_He32, Xp));
         k_cast<float, double><<<nblk(n, 256), 256, 0, ctx->stream>>>(n, Yf, Y);
         return efe_check_launch(ctx, "apply_h fp32");
+    }
+    if (prec == EFE_BF16) {
+        const int ldb = (N + 7) / 8 * 8, ldy = (N + 3) / 4 * 4;
+        const long long ncells = (long long)ctx->m.nx * ctx->m.ny * ctx->m.nz;
+        EFE_TRY(efe_workspace(ctx, sizeof(float) * 2 * n + 2 * (size_t)ctx->n_nodes * ldb +
+                                       4 * (size_t)ncells * ctx->m.ne * ldy + 2048));
+        Carver cv{(char *)ctx->d_ws, ctx->ws_bytes};
+        float *Xf = cv.take<float>(n), *Yf = cv.take<float>(n);
+        __nv_bfloat16 *Xb = cv.take<__nv_bfloat16>((size_t)ctx->n_nodes * ldb);
+        float *Yc = cv.take<float>((size_t)ncells * ctx->m.ne * ldy);
+        EFE_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+        k_cast<double, float><<<nblk(n, 256), 256, 0, ctx->stream>>>(n, X, Xf);
+        EFE_TRY(hx_bf16(ctx, Xf, Yf, N, Xb, Yc));
+        k_cast<float, double><<<nblk(n, 256), 256, 0, ctx->stream>>>(n, Yf, Y);
+        EFE_TRY(efe_check_launch(ctx, "apply_h bf16"));
+        int flag = 0;
+        EFE_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (flag) {
+            ctx->err = "tensor-core cell product: a bounded wait gave up";
+            return EFE_ERR_TIMEOUT;
+        }
+        return EFE_OK;
     }
     ctx->err = "efe_apply_h: precision not available";
     return EFE_ERR_ARG;

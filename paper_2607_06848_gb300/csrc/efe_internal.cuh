@@ -53,6 +53,7 @@ struct efe_ctx {
     float *d_He32 = nullptr;                  // n_cells x ne x ne, FP32 copy
     void *d_He16 = nullptr;                   // bf16 tiles for the tensor-core path
     size_t he16_bytes = 0;
+    bool he16_valid = false;                  // tiles match the current potential
     double *d_atoms = nullptr;                // natoms x 3
     double *d_hproj = nullptr;                // n_proj (per projector strength)
 
@@ -91,11 +92,17 @@ struct efe_ctx {
     double *h_pinned = nullptr;
     size_t pinned_bytes = 0;
     int *d_info = nullptr;
+    int *d_err = nullptr;                     // device error flag of bounded waits
     void *d_solver_ws = nullptr;
     size_t solver_ws_bytes = 0;
 
     efe_stats stats{};
     long long launches = 0;
+    // cell-product timing: events recorded around each colour sweep, summed
+    // after the next synchronisation of the stream
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> cell_events;
+    size_t cell_events_used = 0;
+    long long cell_launches = 0;
 };
 
 // error helpers
@@ -129,5 +136,5 @@ efe_status efe_hx(efe_ctx *ctx, const double *X, double *Y, int N, efe_precision
 efe_status efe_hx_f32(efe_ctx *ctx, const float *X, float *Y, int N, efe_precision prec);
 efe_status efe_mx(efe_ctx *ctx, const double *X, double *Y, int N);
 efe_status efe_minvx(efe_ctx *ctx, const double *X, double *Y, int N);
-efe_status efe_tc_cell_product(efe_ctx *ctx, const float *Xp, float *Y, int N, int colour);
 efe_status efe_tc_prepare(efe_ctx *ctx);
+efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, float *Ycells, int ldy, int *d_err);

@@ -771,6 +771,7 @@ efe_status efe_potential_assembly(efe_ctx *ctx, const double *veff_q) {
     k_cell_hamiltonian<<<(unsigned)ncell, 256, shm, ctx->stream>>>(m, T, veff_q, ctx->d_Khat, ctx->d_He,
                                                                   ctx->d_He32);
     EFE_TRY(efe_check_launch(ctx, "k_cell_hamiltonian"));
+    ctx->he16_valid = false;
     if (ctx->enrich && ctx->natoms) {
         const long long S4 = 4 * ctx->sup_total;
         k_copy<<<nblk(S4, 256), 256, 0, ctx->stream>>>(S4, ctx->d_Kca, ctx->d_Hca);

@@ -47,7 +47,8 @@ class efe_dims(ctypes.Structure):
 
 class efe_stats(ctypes.Structure):
     _fields_ = [("ms_filter", ctypes.c_double), ("ms_rr", ctypes.c_double), ("ms_lanczos", ctypes.c_double),
-                ("ms_cell", ctypes.c_double), ("launches", ctypes.c_longlong), ("passes", ctypes.c_int)]
+                ("ms_cell", ctypes.c_double), ("launches", ctypes.c_longlong),
+                ("cell_launches", ctypes.c_longlong), ("passes", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -77,3 +77,23 @@ def small_cluster(n_atoms, seed, h=2.0, p=4, pad=7.0, min_dist=4.2):
     return dict(name=f"small{n_atoms}_{seed}", h=h, ncell=ncell, p=p, atoms=atoms,
                 Z=np.full(n_atoms, 4.0), hproj=projector_strengths(n_atoms, seed + 1),
                 nstates=int(np.ceil(1.2 * 2 * n_atoms)), cheb_degree=20)
+
+
+def quad_points(h, ncell, nq):
+    """Gauss points of every cell in the library's order (cell-major, then q), shape (n, 3)."""
+    xq, _ = np.polynomial.legendre.leggauss(nq)
+    t = h * (xq + 1.0) / 2.0
+    nx, ny, nz = ncell
+    QZ, QY, QX = np.meshgrid(t, t, t, indexing="ij")
+    loc = np.stack([QX.ravel(), QY.ravel(), QZ.ravel()], axis=1)          # (nq^3, 3)
+    c = np.arange(nx * ny * nz)
+    org = np.stack([c % nx, (c // nx) % ny, c // (nx * ny)], axis=1) * h   # (ncell, 3)
+    return (org[:, None, :] + loc[None, :, :]).reshape(-1, 3)
+
+
+def soft_coulomb_potential(points, atoms, depth=3.0, soft=0.5):
+    """A smooth seeded stand-in potential: -sum_I depth / sqrt(soft + |x - R_I|^2)."""
+    v = np.zeros(len(points))
+    for a in atoms:
+        v -= depth / np.sqrt(soft + np.sum((points - a) ** 2, axis=1))
+    return v

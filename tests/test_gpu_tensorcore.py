@@ -1,0 +1,176 @@
+"""The tensor-core (tcgen05, bf16 operands, FP32 accumulate) filter path.
+
+* Small meshes: the bf16 H^E product against the FP64 oracle (bf16 rounding
+  of H_e and X' bounds the error near 2^-8 relative; a layout or descriptor
+  error would show as O(1)), and the multipass residual ChFSI in bf16
+  converging to the FP64 eigenvalues (the residual form tolerates the inexact
+  products because their error scales with the residual).
+* Full size, in the configuration the benchmark times (64-atom cluster,
+  24^3 cells of degree 6, 154 vectors): bf16 and FP32 products against FP64,
+  and sampled FP64 rows checked one by one against the oracle's cell
+  matrices for nodes whose whole neighbourhood lies outside every atom
+  support (there the row is a plain sum over the <= 8 cells of the node).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import chfsi as OC  # noqa: E402
+from oracle.fe import Mesh  # noqa: E402
+from paper_2607_06848_gb300 import workloads as W  # noqa: E402
+
+import test_gpu_parity as TP  # noqa: E402
+
+
+@pytest.mark.parametrize("name", ["dimer", "ragged", "single_atom", "cfe_only", "nonlocal_only", "p6_cfe",
+                                  "p6_enriched", "p5_enriched"])
+@pytest.mark.parametrize("N", [13, 37])
+def test_apply_h_bf16(name, N):
+    o, g = TP._systems(name)
+    X = TP._rand(o, N, 300 + N)
+    Xd = torch.tensor(X, device="cuda")
+    Y = torch.empty_like(Xd)
+    g.efe_apply_h(Xd, Y, prec=2)
+    rel = TP._rel(Y.cpu().numpy(), o.apply_H(X))
+    assert rel < 1e-2, rel
+
+
+@pytest.mark.parametrize("name", ["dimer", "ragged"])
+def test_chfsi_bf16_reaches_fp64_eigenvalues(name):
+    o, g = TP._systems(name)
+    N, nconv = 8, 6
+    X = TP._rand(o, N, 71)
+    u0 = torch.tensor(TP._rand(o, 1, 72), device="cuda")
+    X64 = torch.tensor(X, device="cuda")
+    e64, _, _, ok64 = g.efe_chfsi(X64, 16, u0=u0, max_pass=60, tol=1e-9, nconv=nconv)
+    X16 = torch.tensor(X, device="cuda")
+    e16, r16, passes, _ = g.efe_chfsi(X16, 16, u0=u0, max_pass=80, tol=1e-8, nconv=nconv, prec=2)
+    assert ok64
+    assert np.max(np.abs(e16[:nconv] - e64[:nconv])) < 1e-7, (e16 - e64, passes, r16)
+
+
+def test_filter_pass_bf16_vs_oracle():
+    # In use the filter sees Ritz vectors with a small residual G; the bf16
+    # rounding then acts on Z ~ G, so the output error scales with the
+    # residual (the point of the residual form).  On random vectors with a
+    # large residual the same rounding is amplified ~T_m(L(a0)) and a single
+    # pass is not comparable element by element.
+    o, g = TP._systems("dimer")
+    X = TP._rand(o, 8, 81)
+    out0 = OC.chfsi(o, X, 12, 1e-4, 20, TP._rand(o, 1, 82), nconv=6)
+    V, lam, HV = out0["V"], out0["lam"], out0["HV"]
+    a0, a, b = out0["bounds"]
+    ref = OC.residual_filter(o, V, lam, 12, a, b, a0, HV=HV)
+    Vd = torch.tensor(V, device="cuda")
+    out = torch.empty_like(Vd)
+    g.efe_filter(Vd, torch.tensor(HV, device="cuda"), torch.tensor(lam, device="cuda"), 12, (a0, a, b), out,
+                 prec=2)
+    rel = TP._rel(out.cpu().numpy(), ref)
+    # bf16 unit roundoff 2^-8 acting on Z ~ G: error ~ u * max residual, x4 margin
+    bound = 4 * 2.0 ** -8 * float(np.max(out0["resid"]))
+    assert rel < bound, (rel, bound)
+
+
+_C64 = {}
+
+
+def _cluster64():
+    if "g" in _C64:
+        return _C64["g"], _C64["w"], _C64["v"]
+    from paper_2607_06848_gb300 import EFE
+    w = W.cluster64()
+    g = EFE(w["h"], w["ncell"], w["p"], w["atoms"], w["Z"], enrich=dict(alpha=1.2, r_end=5.0, t=0.33),
+            psp=dict(rc=1.0, r_trunc=6.0, h=w["hproj"]))
+    q = W.quad_points(w["h"], w["ncell"], g.dims["nq"])
+    v = W.soft_coulomb_potential(q, w["atoms"])
+    g.efe_set_potential(torch.tensor(v, device="cuda"))
+    _C64.update(g=g, w=w, v=v)
+    return g, w, v
+
+
+def test_cluster64_full_size_products():
+    g, w, v = _cluster64()
+    rows, N = g.dims["n_rows"], w["nstates"]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(99)
+    X = torch.randn((rows, N), generator=gen, dtype=torch.float64, device="cuda")
+    Y64 = torch.empty_like(X)
+    g.efe_apply_h(X, Y64)
+    # symmetry of H^E in FP64 (a property that holds at any size)
+    a = torch.randn((rows, 1), generator=gen, dtype=torch.float64, device="cuda")
+    b = torch.randn((rows, 1), generator=gen, dtype=torch.float64, device="cuda")
+    Ha, Hb = torch.empty_like(a), torch.empty_like(b)
+    g.efe_apply_h(a, Ha)
+    g.efe_apply_h(b, Hb)
+    mask = torch.zeros(rows, 1, dtype=torch.float64, device="cuda")
+    Hones = torch.empty_like(mask)
+    g.efe_apply_m(torch.ones_like(mask), Hones)       # M^cc is zero exactly on Dirichlet rows
+    mask = (Hones != 0).double()
+    s1 = float((a * mask * Hb).sum())
+    s2 = float((b * mask * Ha).sum())
+    assert abs(s1 - s2) < 1e-10 * max(abs(s1), 1.0)
+    Y32 = torch.empty_like(X)
+    g.efe_apply_h(X, Y32, prec=1)
+    Y16 = torch.empty_like(X)
+    g.efe_apply_h(X, Y16, prec=2)
+    scale = float(Y64.abs().max())
+    assert float((Y32 - Y64).abs().max()) / scale < 2e-5
+    assert float((Y16 - Y64).abs().max()) / scale < 1e-2
+    _C64.update(X=X, Y64=Y64, Y16=Y16)
+
+
+def test_cluster64_sampled_rows_against_oracle():
+    g, w, v = _cluster64()
+    if "X" not in _C64:
+        test_cluster64_full_size_products()
+    X, Y64, Y16 = _C64["X"], _C64["Y64"], _C64["Y16"]
+    h, p, n = w["h"], w["p"], w["ncell"][0]
+    mesh = Mesh(h, w["ncell"], p)
+    A = w["atoms"]
+    # cells whose 5x5x5 neighbourhood is > 6.5 bohr from every atom: all their
+    # nodes and the nodes of every cell touching them lie outside the supports
+    picks = []
+    for cz in range(1, n - 1):
+        for cy in range(1, n - 1):
+            for cx in range(1, n - 1):
+                lo = np.array([max(cx - 2, 0), max(cy - 2, 0), max(cz - 2, 0)]) * h
+                hi = np.array([min(cx + 3, n), min(cy + 3, n), min(cz + 3, n)]) * h
+                q = np.clip(A, lo, hi)
+                if np.sqrt(((q - A) ** 2).sum(1)).min() > 6.5:
+                    picks.append((cx, cy, cz))
+    assert len(picks) >= 4
+    rng = np.random.default_rng(5)
+    chosen = [picks[i] for i in rng.choice(len(picks), 4, replace=False)]
+    G = mesh.Gx
+    Ke = mesh.stiffness_cell()
+    cn = mesh.cell_nodes()
+    nodes = []
+    for (cx, cy, cz) in chosen:
+        for (a, b, c) in [(0, 0, 0), (p, 3, 1), (2, p, 0), (3, 3, 3)]:
+            nodes.append(((cz * p + c) * G + (cy * p + b)) * G + (cx * p + a))
+    Xh = X.cpu().numpy()
+    # Dirichlet rows are not unknowns: the library ignores their values
+    Xh[:mesh.nnodes][~mesh.interior_mask()] = 0.0
+    Yg64 = Y64.cpu().numpy()
+    Yg16 = Y16.cpu().numpy()
+    for node in nodes:
+        ix, iy, iz = node % G, (node // G) % G, node // (G * G)
+
+        def owners(i):
+            qd, r = divmod(i, p)
+            return [(qd - 1, p), (qd, 0)] if r == 0 else [(qd, r)]
+
+        row = np.zeros(Xh.shape[1])
+        for (czz, az) in owners(iz):
+            for (cyy, ay) in owners(iy):
+                for (cxx, ax) in owners(ix):
+                    c = (czz * n + cyy) * n + cxx
+                    vq = W.soft_coulomb_potential(mesh.quad_points(c), A)
+                    He = 0.5 * Ke + mesh.potential_cell(vq)
+                    l = (az * (p + 1) + ay) * (p + 1) + ax
+                    row += He[l] @ Xh[cn[c]]
+        scale = np.abs(row).max()
+        assert np.max(np.abs(Yg64[node] - row)) < 1e-12 * max(scale, 1.0), node
+        assert np.max(np.abs(Yg16[node] - row)) < 1e-2 * max(scale, 1.0), node
