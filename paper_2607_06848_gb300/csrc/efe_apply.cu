@@ -333,6 +333,206 @@ __global__ void k_gather(MeshDev m, long long n_nodes, int N, const float *Yc, i
     HY[idx] = (float)acc;
 }
 
+// ---------------------------------------------------------------------------
+// Row kernels of the tensor-core filter: one warp per FE node row (node
+// coordinates and coupling lists are read once per row, lanes run over the
+// columns).  All arithmetic is FP32; the values feed bf16 products.
+// ---------------------------------------------------------------------------
+__device__ inline void node_xyz(const MeshDev &m, int n, int &ix, int &iy, int &iz) {
+    ix = n % m.Gx;
+    const int t = n / m.Gx;
+    iy = t % m.Gy;
+    iz = t / m.Gy;
+}
+
+// Xb[n][j] = bf16( minv[n] Z[n][j] - sum_e C_e . Ye[atom(e)][j] ): the first
+// half of T applied to M~^-1 Z (FE rows), padded to ldb columns.
+__global__ void __launch_bounds__(256) k_pre_bf16(MeshDev m, int nn, const float *Z, const float *Ye, int N,
+                                                  int ldb, const double *minv, const long long *node_ptr,
+                                                  const int *node_ent, const int *ent_atom, const double *C,
+                                                  int use_c, __nv_bfloat16 *Xb) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = blockIdx.x * 8 + warp;
+    if (n >= nn) return;
+    int ix, iy, iz;
+    node_xyz(m, n, ix, iy, iz);
+    const bool inter = node_interior(m, ix, iy, iz);
+    const float mi = inter ? (float)minv[n] : 0.f;
+    long long e0 = 0, e1 = 0;
+    if (inter && use_c) { e0 = node_ptr[n]; e1 = node_ptr[n + 1]; }
+    const float *zr = Z + (size_t)n * N;
+    __nv_bfloat16 *out = Xb + (size_t)n * ldb;
+    for (int j = 2 * lane; j < ldb; j += 64) {
+        float v0 = 0.f, v1 = 0.f;
+        if (inter) {
+            if (j < N) v0 = mi * zr[j];
+            if (j + 1 < N) v1 = mi * zr[j + 1];
+            for (long long e = e0; e < e1; ++e) {
+                const int g = node_ent[e];
+                const int I = ent_atom[g];
+                const double *c = C + 4 * (long long)g;
+                for (int f = 0; f < 4; ++f) {
+                    const float cf = (float)c[f];
+                    const float *yr = Ye + (size_t)(4 * I + f) * N;
+                    if (j < N) v0 -= cf * yr[j];
+                    if (j + 1 < N) v1 -= cf * yr[j + 1];
+                }
+            }
+        }
+        *reinterpret_cast<__nv_bfloat162 *>(out + j) = __floats2bfloat162_rn(v0, v1);
+    }
+}
+
+// Fused: HY_c[n] = sum over the node's cells of their product rows + the
+// node-side coupling, then the recurrence for the FE rows
+//   Zn = a (HY - c Z1) - b Z0 + a G ck,
+// and HY kept (HYs) only on nodes that carry coupling entries.
+__global__ void __launch_bounds__(256) k_gather_rec(MeshDev m, int nn, int N, const float *Yc, int ldy,
+                                                    const long long *node_ptr, const int *node_ent,
+                                                    const int *ent_atom, const double *Hca, const double *Pc,
+                                                    const float *Ye, const double *W, int use_h, int use_p,
+                                                    const float *Z1, const float *Z0, const float *G,
+                                                    const float *ck, float a, float c, float b, float *Zn,
+                                                    float *HYs) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = blockIdx.x * 8 + warp;
+    if (n >= nn) return;
+    int ix, iy, iz;
+    node_xyz(m, n, ix, iy, iz);
+    float *zn = Zn + (size_t)n * N;
+    if (!node_interior(m, ix, iy, iz)) {
+        for (int j = lane; j < N; j += 32) zn[j] = 0.f;
+        return;
+    }
+    int cv[3][2], av[3][2], cnt[3];
+    const int ii[3] = {ix, iy, iz}, nc[3] = {m.nx, m.ny, m.nz};
+    for (int d = 0; d < 3; ++d) {
+        const int q = ii[d] / m.p, r = ii[d] - q * m.p;
+        cnt[d] = 0;
+        if (r == 0) {
+            if (q - 1 >= 0) { cv[d][cnt[d]] = q - 1; av[d][cnt[d]] = m.p; ++cnt[d]; }
+            if (q < nc[d]) { cv[d][cnt[d]] = q; av[d][cnt[d]] = 0; ++cnt[d]; }
+        } else {
+            cv[d][0] = q; av[d][0] = r; cnt[d] = 1;
+        }
+    }
+    long long base[8];
+    int nb = 0;
+    for (int a2 = 0; a2 < cnt[2]; ++a2)
+        for (int b2 = 0; b2 < cnt[1]; ++b2)
+            for (int c2 = 0; c2 < cnt[0]; ++c2) {
+                const long long cell = ((long long)cv[2][a2] * m.ny + cv[1][b2]) * m.nx + cv[0][c2];
+                const int l = (av[2][a2] * m.np1 + av[1][b2]) * m.np1 + av[0][c2];
+                base[nb++] = (cell * m.ne + l) * ldy;
+            }
+    long long e0 = 0, e1 = 0;
+    if (node_ptr) { e0 = node_ptr[n]; e1 = node_ptr[n + 1]; }
+    const size_t row = (size_t)n * N;
+    for (int j = lane; j < N; j += 32) {
+        float acc = 0.f;
+        for (int t = 0; t < nb; ++t) acc += Yc[base[t] + j];
+        for (long long e = e0; e < e1; ++e) {
+            const int g = node_ent[e];
+            const int I = ent_atom[g];
+            if (use_h) {
+                const double *h = Hca + 4 * (long long)g;
+                for (int f = 0; f < 4; ++f) acc += (float)h[f] * Ye[(size_t)(4 * I + f) * N + j];
+            }
+            if (use_p) {
+                const double *pc = Pc + 4 * (long long)g;
+                for (int f = 0; f < 4; ++f) acc += (float)(pc[f] * W[(size_t)(4 * I + f) * N + j]);
+            }
+        }
+        const float z0 = Z0 ? Z0[row + j] : 0.f;
+        zn[j] = a * (acc - c * Z1[row + j]) - b * z0 + a * G[row + j] * ck[j];
+        if (e1 > e0) HYs[row + j] = acc;
+    }
+}
+
+// Support reductions with warps over positions and lanes over a 128-column
+// group (blockIdx.z): part[(I*nch + chunk)*8 + r][j] = sum_g coef_r[g] S[node(g)][j].
+template <typename T>
+__global__ void __launch_bounds__(256) k_support_reduce2(const long long *sup_off, const int *sup_node,
+                                                         const double *coefA, const double *coefB, const T *S,
+                                                         int N, int ld, int chunk, int nch, double *part) {
+    __shared__ float acc[8][128];
+    const int I = blockIdx.y, colg = blockIdx.z * 128;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < 8 * 128; i += blockDim.x) acc[i / 128][i % 128] = 0.f;
+    __syncthreads();
+    const long long beg = sup_off[I] + (long long)blockIdx.x * chunk;
+    const long long end = min(sup_off[I + 1], beg + chunk);
+    const int nr = coefB ? 8 : 4;
+    float r[8][4];
+    for (int i = 0; i < 8; ++i)
+        for (int t = 0; t < 4; ++t) r[i][t] = 0.f;
+    for (long long g = beg + warp; g < end; g += 8) {
+        const T *srow = S + (long long)sup_node[g] * ld + colg;
+        float ca[4], cb[4];
+        for (int f = 0; f < 4; ++f) {
+            ca[f] = (float)coefA[4 * g + f];
+            cb[f] = coefB ? (float)coefB[4 * g + f] : 0.f;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int j = lane + 32 * t;
+            if (colg + j < N) {
+                const float sv = (float)to_d(srow[j]);
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    r[f][t] += ca[f] * sv;
+                    r[4 + f][t] += cb[f] * sv;
+                }
+            }
+        }
+    }
+    for (int i = 0; i < nr; ++i)
+        for (int t = 0; t < 4; ++t) atomicAdd(&acc[i][lane + 32 * t], r[i][t]);
+    __syncthreads();
+    double *o = part + ((long long)(I * nch + blockIdx.x) * 8) * N;
+    for (int i = threadIdx.x; i < nr * 128; i += blockDim.x) {
+        const int rr = i / 128, j = i % 128;
+        if (colg + j < N) o[(long long)rr * N + colg + j] = acc[rr][j];
+    }
+}
+
+// Enriched rows of the recurrence: HY_e = Yraw - Q, Zn_e = a (HY_e - c Z1_e) - b Z0_e + a G_e ck.
+__global__ void k_enr_rec(int n_enr, int N, const double *Yraw, const double *Q, const float *Z1, const float *Z0,
+                          const float *G, const float *ck, float a, float c, float b, float *Zn) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_enr * N) return;
+    const int j = idx % N;
+    const float hy = (float)(Yraw[idx] - (Q ? Q[idx] : 0.0));
+    const float z0 = Z0 ? Z0[idx] : 0.f;
+    Zn[idx] = a * (hy - c * Z1[idx]) - b * z0 + a * G[idx] * ck[j];
+}
+
+__global__ void k_cast_scale(long long n, float s, const float *x, float *y) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = s * x[i];
+}
+
+// Row-parallel elementwise helpers (warp per row, no 64-bit division)
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_residual(long long rows, int N, const double *HV, const double *MV,
+                                                       const double *lam, T *G) {
+    const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    for (int j = threadIdx.x & 31; j < N; j += 32) G[r * N + j] = (T)(HV[r * N + j] - MV[r * N + j] * lam[j]);
+}
+__global__ void __launch_bounds__(256) k_rows_vout(long long rows, int N, const float *Y, const double *V,
+                                                   const double *cm, double *Vout) {
+    const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    for (int j = threadIdx.x & 31; j < N; j += 32) Vout[r * N + j] = (double)Y[r * N + j] + V[r * N + j] * cm[j];
+}
+__global__ void __launch_bounds__(256) k_rows_minv(long long nn, int N, const double *minv, const float *X, float *Y) {
+    const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= nn) return;
+    const float mi = (float)minv[r];
+    for (int j = threadIdx.x & 31; j < N; j += 32) Y[r * N + j] = mi * X[r * N + j];
+}
+
 // zero the Dirichlet boundary rows of a block (they are not unknowns)
 __global__ void k_zero_boundary(MeshDev m, long long n_nodes, int N, double *X) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -936,14 +1136,156 @@ efe_status filter_impl(efe_ctx *ctx, const double *V, const double *HV, const do
 
 }  // namespace
 
+// Residual filter with tcgen05 cell products (bf16 operands, FP32 accumulate)
+// and FP32 recurrence storage; G, V_out and the Chebyshev scalars as in
+// filter_impl.  Per recurrence step: M~^-1 on the enriched rows, the fused
+// bf16 producer of T M~^-1 Z, the tensor-core cell products, the coupling
+// reductions, and the fused gather + recurrence.
+static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV, const double *lam_dev, int N,
+                                int m, const double bounds[3], double *Vout) {
+    const MeshDev &mh = ctx->m;
+    const long long rows = ctx->n_rows, nn = ctx->n_nodes;
+    const long long n = rows * N;
+    const int ne_ = ctx->n_enr;
+    const double a0 = bounds[0], a = bounds[1], b = bounds[2];
+    if (!(b > a) || !(a0 < a)) {
+        ctx->err = "filter bounds must satisfy a0 < a < b";
+        return EFE_ERR_ARG;
+    }
+    if (nn > 2147483647LL) {
+        ctx->err = "mesh too large for 32-bit node indices";
+        return EFE_ERR_ARG;
+    }
+    if (!ctx->he16_valid) EFE_TRY(efe_tc_prepare(ctx));
+    std::vector<double> lam(N);
+    EFE_CUDA(ctx, cudaMemcpyAsync(lam.data(), lam_dev, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
+    EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<double> ck, sig;
+    cheb_table(m, N, lam.data(), a, b, a0, ck, sig);
+    std::vector<float> ckf(ck.begin(), ck.end());
+    const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+    const int ldb = (N + 7) / 8 * 8, ldy = (N + 3) / 4 * 4;
+    const long long ncells = (long long)mh.nx * mh.ny * mh.nz;
+    size_t need = 4096 + sizeof(double) * n + sizeof(double) * (size_t)(m + 1) * N + sizeof(float) * (size_t)(m + 1) * N +
+                  sizeof(float) * (4 * n + (size_t)nn * N + (size_t)ne_ * N) + 2 * (size_t)nn * ldb +
+                  4 * (size_t)ncells * mh.ne * ldy;
+    EFE_TRY(efe_workspace(ctx, need));
+    Carver cv{(char *)ctx->d_ws, ctx->ws_bytes};
+    double *MV = cv.take<double>(n), *dck = cv.take<double>((size_t)(m + 1) * N);
+    float *fck = cv.take<float>((size_t)(m + 1) * N);
+    float *G = cv.take<float>(n), *Z0 = cv.take<float>(n), *Z1 = cv.take<float>(n), *Z2 = cv.take<float>(n);
+    float *HYs = cv.take<float>((size_t)nn * N), *Ye = cv.take<float>((size_t)ne_ * N + 1);
+    __nv_bfloat16 *Xb = cv.take<__nv_bfloat16>((size_t)nn * ldb);
+    float *Ycells = cv.take<float>((size_t)ncells * mh.ne * ldy);
+    EFE_CUDA(ctx, cudaMemcpyAsync(dck, ck.data(), sizeof(double) * ck.size(), cudaMemcpyHostToDevice, ctx->stream));
+    EFE_CUDA(ctx, cudaMemcpyAsync(fck, ckf.data(), sizeof(float) * ckf.size(), cudaMemcpyHostToDevice, ctx->stream));
+    EFE_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    const bool cpl = (ctx->enrich || ctx->nonlocal) && ctx->natoms > 0;
+    HxScratch s{};
+    if (cpl) EFE_TRY(hx_scratch(ctx, N, s));
+    const unsigned rb_all = (unsigned)((rows + 7) / 8), rb_fe = (unsigned)((nn + 7) / 8);
+    ctx->cell_events_used = 0;
+    ctx->cell_launches = 0;
+    Timer tm(ctx->stream);
+    const long long l0 = ctx->launches;
+    EFE_TRY(m_apply(ctx, V, MV, N, true));
+    k_rows_residual<float><<<rb_all, 256, 0, ctx->stream>>>(rows, N, HV, MV, lam_dev, G);
+    ctx->launches += 1;
+    // Z_1 = (s1/e) G
+    {
+        const float s1e = (float)(sig[1] / e);
+        k_cast_scale<<<nblk(n, 256), 256, 0, ctx->stream>>>(n, s1e, G, Z1);
+        ctx->launches++;
+    }
+    float *Zprev = nullptr, *Zcur = Z1, *Znext = Z2, *Zspare = Z0;
+    const dim3 gred(s.nch, std::max(ctx->natoms, 1), (N + 127) / 128);
+    for (int k = 2; k <= m; ++k) {
+        const float ak = (float)(2.0 * sig[k] / e), bk = (float)(sig[k - 1] * sig[k]), cf = (float)c;
+        // enriched rows of M~^-1 Z
+        if (ne_) {
+            k_enr_mat<float><<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(ne_, N, ctx->d_Mblk_inv, 1,
+                                                                                     Zcur + nn * N, Ye);
+            ctx->launches++;
+        }
+        k_pre_bf16<<<rb_fe, 256, 0, ctx->stream>>>(mh, (int)nn, Zcur, Ye, N, ldb, ctx->d_minv, ctx->d_node_ptr,
+                                                   ctx->d_node_ent, ctx->d_ent_atom, ctx->d_C, ctx->enrich ? 1 : 0,
+                                                   Xb);
+        ctx->launches++;
+        EFE_TRY(efe_check_launch(ctx, "k_pre_bf16"));
+        {
+            auto *ev = cell_event_pair(ctx);
+            if (ev) cudaEventRecord(ev->first, ctx->stream);
+            EFE_TRY(efe_tc_cells(ctx, Xb, ldb, N, Ycells, ldy, ctx->d_err));
+            if (ev) cudaEventRecord(ev->second, ctx->stream);
+        }
+        if (cpl) {
+            k_support_reduce2<__nv_bfloat16><<<gred, 256, 0, ctx->stream>>>(
+                ctx->d_sup_off, ctx->d_sup_node, ctx->enrich ? ctx->d_Hca : ctx->d_Pc,
+                (ctx->enrich && ctx->nonlocal) ? ctx->d_Pc : nullptr, Xb, N, ldb, s.chunk, s.nch, s.part);
+            const long long n8 = (long long)ctx->natoms * 8 * N;
+            k_support_sum<<<nblk(n8, 256), 256, 0, ctx->stream>>>(ctx->natoms, s.nch, N, s.part,
+                                                                  ctx->enrich ? s.Rh : s.Wc,
+                                                                  (ctx->enrich && ctx->nonlocal) ? s.Wc : nullptr);
+            ctx->launches += 2;
+            if (ctx->nonlocal) {
+                k_proj_w<float><<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
+                    ctx->n_proj, ne_, s.Wc, ctx->enrich ? ctx->d_Pa : nullptr, Ye, N, ctx->d_hproj, N, s.W);
+                ctx->launches++;
+            }
+            if (ctx->enrich) {
+                k_enr_raw<float><<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(
+                    ne_, ctx->n_proj, s.Rh, ctx->d_Haa, ctx->nonlocal ? ctx->d_Pa : nullptr, s.W, Ye, N, N, s.Yraw);
+                ctx->launches++;
+            }
+        }
+        k_gather_rec<<<rb_fe, 256, 0, ctx->stream>>>(mh, (int)nn, N, Ycells, ldy, cpl ? ctx->d_node_ptr : nullptr,
+                                                     ctx->d_node_ent, ctx->d_ent_atom, ctx->d_Hca, ctx->d_Pc, Ye, s.W,
+                                                     ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0, Zcur, Zprev, G,
+                                                     fck + (size_t)(k - 1) * N, ak, cf, bk, Znext, HYs);
+        ctx->launches++;
+        EFE_TRY(efe_check_launch(ctx, "k_gather_rec"));
+        if (ne_) {
+            k_support_reduce2<float><<<gred, 256, 0, ctx->stream>>>(ctx->d_sup_off, ctx->d_sup_node, ctx->d_C, nullptr,
+                                                                    HYs, N, N, s.chunk, s.nch, s.part);
+            const long long n8 = (long long)ctx->natoms * 8 * N;
+            k_support_sum<<<nblk(n8, 256), 256, 0, ctx->stream>>>(ctx->natoms, s.nch, N, s.part, s.Q, nullptr);
+            k_enr_rec<<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(
+                ne_, N, s.Yraw, s.Q, Zcur + nn * N, Zprev ? Zprev + nn * N : nullptr, G + nn * N,
+                fck + (size_t)(k - 1) * N, ak, cf, bk, Znext + nn * N);
+            ctx->launches += 3;
+        }
+        float *old_prev = Zprev ? Zprev : Zspare;
+        Zprev = Zcur;
+        Zcur = Znext;
+        Znext = old_prev;
+    }
+    // V_out = M~^-1 Z_m + V diag(C_m(lam))
+    float *Y = Znext;
+    k_rows_minv<<<rb_fe, 256, 0, ctx->stream>>>(nn, N, ctx->d_minv, Zcur, Y);
+    if (ne_)
+        k_enr_mat<float><<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(ne_, N, ctx->d_Mblk_inv, 1,
+                                                                                 Zcur + nn * N, Y + nn * N);
+    k_rows_vout<<<rb_all, 256, 0, ctx->stream>>>(rows, N, Y, V, dck + (size_t)m * N, Vout);
+    ctx->launches += 3;
+    EFE_TRY(efe_check_launch(ctx, "filter_tensor"));
+    ctx->stats.ms_filter = tm.stop();
+    ctx->stats.ms_cell = cell_events_ms(ctx);
+    ctx->stats.launches = ctx->launches - l0;
+    ctx->stats.cell_launches = ctx->cell_launches;
+    int flag = 0;
+    EFE_CUDA(ctx, cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        ctx->err = "tensor-core cell product: a bounded wait gave up (role " + std::to_string(flag) + ")";
+        return EFE_ERR_TIMEOUT;
+    }
+    return EFE_OK;
+}
+
 efe_status efe_filter_dispatch(efe_ctx *ctx, const double *V, const double *HV, const double *lam, int N, int m,
                                const double bounds[3], efe_precision prec, double *Vout) {
     if (prec == EFE_FP64) return filter_impl<double>(ctx, V, HV, lam, N, m, bounds, Vout);
     if (prec == EFE_FP32) return filter_impl<float>(ctx, V, HV, lam, N, m, bounds, Vout);
-    if (prec == EFE_BF16) {
-        if (!ctx->he16_valid) EFE_TRY(efe_tc_prepare(ctx));
-        return filter_impl<float>(ctx, V, HV, lam, N, m, bounds, Vout, true);
-    }
+    if (prec == EFE_BF16) return filter_tensor(ctx, V, HV, lam, N, m, bounds, Vout);
     ctx->err = "unknown precision";
     return EFE_ERR_ARG;
 }
