@@ -87,6 +87,8 @@ def workload(name):
         return W.cluster64()
     if name == "dimer":
         return W.dimer()
+    if name == "cluster8":
+        return W.cluster8()
     raise SystemExit("unknown workload " + name)
 
 

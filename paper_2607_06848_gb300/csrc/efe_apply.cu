@@ -145,6 +145,8 @@ __global__ void k_xprime(MeshDev m, long long n_nodes, const T *X, T *Xp, int N,
 __device__ inline double to_d(double x) { return x; }
 __device__ inline double to_d(float x) { return (double)x; }
 __device__ inline double to_d(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+__device__ inline float to_f(float x) { return x; }
+__device__ inline float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
 
 // Partial support reductions: for atom I (blockIdx.y) and chunk blockIdx.x,
 //   part[(I*nch + chunk)][r][j] = sum_{g in chunk} coef_r[g] * S[node(g)][j]
@@ -349,7 +351,7 @@ __device__ inline void node_xyz(const MeshDev &m, int n, int &ix, int &iy, int &
 // half of T applied to M~^-1 Z (FE rows), padded to ldb columns.
 __global__ void __launch_bounds__(256) k_pre_bf16(MeshDev m, int nn, const float *Z, const float *Ye, int N,
                                                   int ldb, const double *minv, const long long *node_ptr,
-                                                  const int *node_ent, const int *ent_atom, const double *C,
+                                                  const int *node_ent, const int *ent_atom, const float *C,
                                                   int use_c, __nv_bfloat16 *Xb) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = blockIdx.x * 8 + warp;
@@ -370,9 +372,9 @@ __global__ void __launch_bounds__(256) k_pre_bf16(MeshDev m, int nn, const float
             for (long long e = e0; e < e1; ++e) {
                 const int g = node_ent[e];
                 const int I = ent_atom[g];
-                const double *c = C + 4 * (long long)g;
+                const float *c = C + 4 * (long long)g;
                 for (int f = 0; f < 4; ++f) {
-                    const float cf = (float)c[f];
+                    const float cf = c[f];
                     const float *yr = Ye + (size_t)(4 * I + f) * N;
                     if (j < N) v0 -= cf * yr[j];
                     if (j + 1 < N) v1 -= cf * yr[j + 1];
@@ -389,8 +391,8 @@ __global__ void __launch_bounds__(256) k_pre_bf16(MeshDev m, int nn, const float
 // and HY kept (HYs) only on nodes that carry coupling entries.
 __global__ void __launch_bounds__(256) k_gather_rec(MeshDev m, int nn, int N, const float *Yc, int ldy,
                                                     const long long *node_ptr, const int *node_ent,
-                                                    const int *ent_atom, const double *Hca, const double *Pc,
-                                                    const float *Ye, const double *W, int use_h, int use_p,
+                                                    const int *ent_atom, const float *Hca, const float *Pc,
+                                                    const float *Ye, const float *W, int use_h, int use_p,
                                                     const float *Z1, const float *Z0, const float *G,
                                                     const float *ck, float a, float c, float b, float *Zn,
                                                     float *HYs) {
@@ -435,12 +437,12 @@ __global__ void __launch_bounds__(256) k_gather_rec(MeshDev m, int nn, int N, co
             const int g = node_ent[e];
             const int I = ent_atom[g];
             if (use_h) {
-                const double *h = Hca + 4 * (long long)g;
-                for (int f = 0; f < 4; ++f) acc += (float)h[f] * Ye[(size_t)(4 * I + f) * N + j];
+                const float *h = Hca + 4 * (long long)g;
+                for (int f = 0; f < 4; ++f) acc += h[f] * Ye[(size_t)(4 * I + f) * N + j];
             }
             if (use_p) {
-                const double *pc = Pc + 4 * (long long)g;
-                for (int f = 0; f < 4; ++f) acc += (float)(pc[f] * W[(size_t)(4 * I + f) * N + j]);
+                const float *pc = Pc + 4 * (long long)g;
+                for (int f = 0; f < 4; ++f) acc += pc[f] * W[(size_t)(4 * I + f) * N + j];
             }
         }
         const float z0 = Z0 ? Z0[row + j] : 0.f;
@@ -453,7 +455,7 @@ __global__ void __launch_bounds__(256) k_gather_rec(MeshDev m, int nn, int N, co
 // group (blockIdx.z): part[(I*nch + chunk)*8 + r][j] = sum_g coef_r[g] S[node(g)][j].
 template <typename T>
 __global__ void __launch_bounds__(256) k_support_reduce2(const long long *sup_off, const int *sup_node,
-                                                         const double *coefA, const double *coefB, const T *S,
+                                                         const float *coefA, const float *coefB, const T *S,
                                                          int N, int ld, int chunk, int nch, double *part) {
     __shared__ float acc[8][128];
     const int I = blockIdx.y, colg = blockIdx.z * 128;
@@ -469,15 +471,19 @@ __global__ void __launch_bounds__(256) k_support_reduce2(const long long *sup_of
     for (long long g = beg + warp; g < end; g += 8) {
         const T *srow = S + (long long)sup_node[g] * ld + colg;
         float ca[4], cb[4];
-        for (int f = 0; f < 4; ++f) {
-            ca[f] = (float)coefA[4 * g + f];
-            cb[f] = coefB ? (float)coefB[4 * g + f] : 0.f;
+        const float4 qa = *reinterpret_cast<const float4 *>(coefA + 4 * g);
+        ca[0] = qa.x; ca[1] = qa.y; ca[2] = qa.z; ca[3] = qa.w;
+        if (coefB) {
+            const float4 qb = *reinterpret_cast<const float4 *>(coefB + 4 * g);
+            cb[0] = qb.x; cb[1] = qb.y; cb[2] = qb.z; cb[3] = qb.w;
+        } else {
+            cb[0] = cb[1] = cb[2] = cb[3] = 0.f;
         }
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int j = lane + 32 * t;
             if (colg + j < N) {
-                const float sv = (float)to_d(srow[j]);
+                const float sv = to_f(srow[j]);
 #pragma unroll
                 for (int f = 0; f < 4; ++f) {
                     r[f][t] += ca[f] * sv;
@@ -507,6 +513,10 @@ __global__ void k_enr_rec(int n_enr, int N, const double *Yraw, const double *Q,
     Zn[idx] = a * (hy - c * Z1[idx]) - b * z0 + a * G[idx] * ck[j];
 }
 
+__global__ void k_to_float_d(long long n, const double *x, float *y) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (float)x[i];
+}
 __global__ void k_cast_scale(long long n, float s, const float *x, float *y) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) y[i] = s * x[i];
@@ -1166,7 +1176,8 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     const double e = 0.5 * (b - a), c = 0.5 * (b + a);
     const int ldb = (N + 7) / 8 * 8, ldy = (N + 3) / 4 * 4;
     const long long ncells = (long long)mh.nx * mh.ny * mh.nz;
-    size_t need = 4096 + sizeof(double) * n + sizeof(double) * (size_t)(m + 1) * N + sizeof(float) * (size_t)(m + 1) * N +
+    size_t need = 8192 + sizeof(float) * ((size_t)ctx->n_proj * N + 1) + sizeof(double) * n +
+                  sizeof(double) * (size_t)(m + 1) * N + sizeof(float) * (size_t)(m + 1) * N +
                   sizeof(float) * (4 * n + (size_t)nn * N + (size_t)ne_ * N) + 2 * (size_t)nn * ldb +
                   4 * (size_t)ncells * mh.ne * ldy;
     EFE_TRY(efe_workspace(ctx, need));
@@ -1175,6 +1186,7 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     float *fck = cv.take<float>((size_t)(m + 1) * N);
     float *G = cv.take<float>(n), *Z0 = cv.take<float>(n), *Z1 = cv.take<float>(n), *Z2 = cv.take<float>(n);
     float *HYs = cv.take<float>((size_t)nn * N), *Ye = cv.take<float>((size_t)ne_ * N + 1);
+    float *W32 = cv.take<float>((size_t)ctx->n_proj * N + 1);
     __nv_bfloat16 *Xb = cv.take<__nv_bfloat16>((size_t)nn * ldb);
     float *Ycells = cv.take<float>((size_t)ncells * mh.ne * ldy);
     EFE_CUDA(ctx, cudaMemcpyAsync(dck, ck.data(), sizeof(double) * ck.size(), cudaMemcpyHostToDevice, ctx->stream));
@@ -1208,7 +1220,7 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
             ctx->launches++;
         }
         k_pre_bf16<<<rb_fe, 256, 0, ctx->stream>>>(mh, (int)nn, Zcur, Ye, N, ldb, ctx->d_minv, ctx->d_node_ptr,
-                                                   ctx->d_node_ent, ctx->d_ent_atom, ctx->d_C, ctx->enrich ? 1 : 0,
+                                                   ctx->d_node_ent, ctx->d_ent_atom, ctx->d_C32, ctx->enrich ? 1 : 0,
                                                    Xb);
         ctx->launches++;
         EFE_TRY(efe_check_launch(ctx, "k_pre_bf16"));
@@ -1220,8 +1232,8 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
         }
         if (cpl) {
             k_support_reduce2<__nv_bfloat16><<<gred, 256, 0, ctx->stream>>>(
-                ctx->d_sup_off, ctx->d_sup_node, ctx->enrich ? ctx->d_Hca : ctx->d_Pc,
-                (ctx->enrich && ctx->nonlocal) ? ctx->d_Pc : nullptr, Xb, N, ldb, s.chunk, s.nch, s.part);
+                ctx->d_sup_off, ctx->d_sup_node, ctx->enrich ? ctx->d_Hca32 : ctx->d_Pc32,
+                (ctx->enrich && ctx->nonlocal) ? ctx->d_Pc32 : nullptr, Xb, N, ldb, s.chunk, s.nch, s.part);
             const long long n8 = (long long)ctx->natoms * 8 * N;
             k_support_sum<<<nblk(n8, 256), 256, 0, ctx->stream>>>(ctx->natoms, s.nch, N, s.part,
                                                                   ctx->enrich ? s.Rh : s.Wc,
@@ -1230,7 +1242,9 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
             if (ctx->nonlocal) {
                 k_proj_w<float><<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
                     ctx->n_proj, ne_, s.Wc, ctx->enrich ? ctx->d_Pa : nullptr, Ye, N, ctx->d_hproj, N, s.W);
-                ctx->launches++;
+                k_to_float_d<<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
+                    (long long)ctx->n_proj * N, s.W, W32);
+                ctx->launches += 2;
             }
             if (ctx->enrich) {
                 k_enr_raw<float><<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(
@@ -1239,14 +1253,14 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
             }
         }
         k_gather_rec<<<rb_fe, 256, 0, ctx->stream>>>(mh, (int)nn, N, Ycells, ldy, cpl ? ctx->d_node_ptr : nullptr,
-                                                     ctx->d_node_ent, ctx->d_ent_atom, ctx->d_Hca, ctx->d_Pc, Ye, s.W,
+                                                     ctx->d_node_ent, ctx->d_ent_atom, ctx->d_Hca32, ctx->d_Pc32, Ye, W32,
                                                      ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0, Zcur, Zprev, G,
                                                      fck + (size_t)(k - 1) * N, ak, cf, bk, Znext, HYs);
         ctx->launches++;
         EFE_TRY(efe_check_launch(ctx, "k_gather_rec"));
         if (ne_) {
-            k_support_reduce2<float><<<gred, 256, 0, ctx->stream>>>(ctx->d_sup_off, ctx->d_sup_node, ctx->d_C, nullptr,
-                                                                    HYs, N, N, s.chunk, s.nch, s.part);
+            k_support_reduce2<float><<<gred, 256, 0, ctx->stream>>>(ctx->d_sup_off, ctx->d_sup_node, ctx->d_C32,
+                                                                    nullptr, HYs, N, N, s.chunk, s.nch, s.part);
             const long long n8 = (long long)ctx->natoms * 8 * N;
             k_support_sum<<<nblk(n8, 256), 256, 0, ctx->stream>>>(ctx->natoms, s.nch, N, s.part, s.Q, nullptr);
             k_enr_rec<<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(
@@ -1467,7 +1481,8 @@ void efe_destroy(efe_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     void *ptrs[] = {ctx->d_B1, ctx->d_D1, ctx->d_wq, ctx->d_Khat, ctx->d_mcc, ctx->d_minv, ctx->d_He, ctx->d_He32,
                     ctx->d_He16, ctx->d_atoms, ctx->d_hproj, ctx->d_sup_off, ctx->d_sup_node, ctx->d_C, ctx->d_B,
-                    ctx->d_Kca, ctx->d_Hca, ctx->d_Pc, ctx->d_node_ptr, ctx->d_node_ent, ctx->d_ent_atom,
+                    ctx->d_Kca, ctx->d_Hca, ctx->d_Pc, ctx->d_C32, ctx->d_Hca32, ctx->d_Pc32, ctx->d_node_ptr,
+                    ctx->d_node_ent, ctx->d_ent_atom,
                     ctx->d_pairs, ctx->d_pair_pos, ctx->d_cell_atom_ptr, ctx->d_cell_atoms, ctx->d_Aee, ctx->d_Kaa,
                     ctx->d_Haa, ctx->d_Mee, ctx->d_Pa, ctx->d_Mblk_inv, ctx->d_Mblk, ctx->d_ws, ctx->d_part,
                     ctx->d_info, ctx->d_err, ctx->d_solver_ws};

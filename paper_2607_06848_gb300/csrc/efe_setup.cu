@@ -415,6 +415,10 @@ __global__ void k_cell_hamiltonian(MeshDev m, Tables1D T, const double *vq, cons
     }
 }
 
+__global__ void k_to_float(long long n, const double *a, float *b) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
 __global__ void k_copy(long long n, const double *a, double *b) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) b[i] = a[i];
@@ -793,6 +797,18 @@ efe_status efe_potential_assembly(efe_ctx *ctx, const double *veff_q) {
             m, T, fp, ctx->d_cell_atom_ptr, ctx->d_cell_atoms, ctx->d_atoms, veff_q, ctx->n_enr, nullptr,
             nullptr, nullptr, ctx->d_Haa);
         EFE_TRY(efe_check_launch(ctx, "k_enriched_pairs(v)"));
+    }
+    if ((ctx->enrich || ctx->nonlocal) && ctx->natoms) {
+        const long long S4 = 4 * std::max<long long>(ctx->sup_total, 1);
+        if (!ctx->d_Hca32) {
+            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_Hca32, sizeof(float) * S4));
+            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_C32, sizeof(float) * S4));
+            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_Pc32, sizeof(float) * S4));
+            k_to_float<<<nblk(S4, 256), 256, 0, ctx->stream>>>(S4, ctx->d_C, ctx->d_C32);
+            k_to_float<<<nblk(S4, 256), 256, 0, ctx->stream>>>(S4, ctx->d_Pc, ctx->d_Pc32);
+        }
+        k_to_float<<<nblk(S4, 256), 256, 0, ctx->stream>>>(S4, ctx->d_Hca, ctx->d_Hca32);
+        EFE_TRY(efe_check_launch(ctx, "k_to_float"));
     }
     ctx->have_potential = true;
     return EFE_OK;

@@ -97,3 +97,10 @@ def soft_coulomb_potential(points, atoms, depth=3.0, soft=0.5):
     for a in atoms:
         v -= depth / np.sqrt(soft + np.sum((points - a) ** 2, axis=1))
     return v
+
+
+def cluster8(seed=0):
+    """A small case with the 64-atom cluster's discretisation (h = 40/24, p = 6,
+    154 vectors): 8 atoms in a 20-bohr cube, 12^3 cells -- inputs above the L2
+    size but only a few GB on the device (profiling captures)."""
+    return cluster(8, 20.0, 12, 6, 154, 30, seed=seed, name="cluster8")
