@@ -513,6 +513,11 @@ __global__ void k_enr_rec(int n_enr, int N, const double *Yraw, const double *Q,
     Zn[idx] = a * (hy - c * Z1[idx]) - b * z0 + a * G[idx] * ck[j];
 }
 
+__global__ void k_to_float_strided(int rows, int N, const double *x, float *y, int ldy) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * N) return;
+    y[(size_t)(idx / N) * ldy + idx % N] = (float)x[idx];
+}
 __global__ void k_to_float_d(long long n, const double *x, float *y) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) y[i] = (float)x[i];
@@ -520,6 +525,239 @@ __global__ void k_to_float_d(long long n, const double *x, float *y) {
 __global__ void k_cast_scale(long long n, float s, const float *x, float *y) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) y[i] = s * x[i];
+}
+
+// ---------------------------------------------------------------------------
+// Vectorised row kernels of the tensor-core filter.  FE-row buffers use a row
+// stride ldz = N rounded up to 4 floats (16-byte rows): lanes move float4s.
+// ---------------------------------------------------------------------------
+__device__ inline float4 f4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ inline void fma4(float4 &a, float s, const float4 b) {
+    a.x += s * b.x; a.y += s * b.y; a.z += s * b.z; a.w += s * b.w;
+}
+
+// Xb[n][4q..4q+3] = bf16( minv[n] Z[n] - sum_e C_e . Ye[atom(e)] ) (ldb >= ldz, padding zero)
+__global__ void __launch_bounds__(256) k_pre_bf16_v(MeshDev m, int nn, const float *Z, int ldz, const float *Ye,
+                                                    int lde, int ldb, const double *minv, const long long *node_ptr,
+                                                    const int *node_ent, const int *ent_atom, const float *C,
+                                                    int use_c, __nv_bfloat16 *Xb) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = blockIdx.x * 8 + warp;
+    if (n >= nn) return;
+    int ix, iy, iz;
+    node_xyz(m, n, ix, iy, iz);
+    const bool inter = node_interior(m, ix, iy, iz);
+    const float mi = inter ? (float)minv[n] : 0.f;
+    long long e0 = 0, e1 = 0;
+    if (inter && use_c) { e0 = node_ptr[n]; e1 = node_ptr[n + 1]; }
+    const float *zr = Z + (size_t)n * ldz;
+    __nv_bfloat16 *out = Xb + (size_t)n * ldb;
+    for (int j = 4 * lane; j < ldb; j += 128) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (inter && j < ldz) {
+            const float4 z = f4(zr + j);
+            v = make_float4(mi * z.x, mi * z.y, mi * z.z, mi * z.w);
+            for (long long e = e0; e < e1; ++e) {
+                const int g = node_ent[e];
+                const int I = ent_atom[g];
+                const float4 c = f4(C + 4 * (long long)g);
+                fma4(v, -c.x, f4(Ye + (size_t)(4 * I + 0) * lde + j));
+                fma4(v, -c.y, f4(Ye + (size_t)(4 * I + 1) * lde + j));
+                fma4(v, -c.z, f4(Ye + (size_t)(4 * I + 2) * lde + j));
+                fma4(v, -c.w, f4(Ye + (size_t)(4 * I + 3) * lde + j));
+            }
+        }
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+        uint2 pk;
+        pk.x = *reinterpret_cast<uint32_t *>(&lo);
+        pk.y = *reinterpret_cast<uint32_t *>(&hi);
+        *reinterpret_cast<uint2 *>(out + j) = pk;
+    }
+}
+
+// Fused gather + coupling + FE-row recurrence on float4 columns (see k_gather_rec).
+__global__ void __launch_bounds__(256) k_gather_rec_v(MeshDev m, int nn, int ldz, const float *Yc, int ldy,
+                                                      const long long *node_ptr, const int *node_ent,
+                                                      const int *ent_atom, const float *Hca, const float *Pc,
+                                                      const float *Ye, const float *W, int lde, int use_h, int use_p,
+                                                      const float *Z1, const float *Z0, const float *G,
+                                                      const float *ck, float a, float c, float b, float *Zn,
+                                                      float *HYs) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = blockIdx.x * 8 + warp;
+    if (n >= nn) return;
+    int ix, iy, iz;
+    node_xyz(m, n, ix, iy, iz);
+    const size_t row = (size_t)n * ldz;
+    if (!node_interior(m, ix, iy, iz)) {
+        for (int j = 4 * lane; j < ldz; j += 128)
+            *reinterpret_cast<float4 *>(Zn + row + j) = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    int cv[3][2], av[3][2], cnt[3];
+    const int ii[3] = {ix, iy, iz}, nc[3] = {m.nx, m.ny, m.nz};
+    for (int d = 0; d < 3; ++d) {
+        const int q = ii[d] / m.p, r = ii[d] - q * m.p;
+        cnt[d] = 0;
+        if (r == 0) {
+            if (q - 1 >= 0) { cv[d][cnt[d]] = q - 1; av[d][cnt[d]] = m.p; ++cnt[d]; }
+            if (q < nc[d]) { cv[d][cnt[d]] = q; av[d][cnt[d]] = 0; ++cnt[d]; }
+        } else {
+            cv[d][0] = q; av[d][0] = r; cnt[d] = 1;
+        }
+    }
+    long long base[8];
+    int nb = 0;
+    for (int a2 = 0; a2 < cnt[2]; ++a2)
+        for (int b2 = 0; b2 < cnt[1]; ++b2)
+            for (int c2 = 0; c2 < cnt[0]; ++c2) {
+                const long long cell = ((long long)cv[2][a2] * m.ny + cv[1][b2]) * m.nx + cv[0][c2];
+                const int l = (av[2][a2] * m.np1 + av[1][b2]) * m.np1 + av[0][c2];
+                base[nb++] = (cell * m.ne + l) * ldy;
+            }
+    for (int t = nb; t < 8; ++t) base[t] = base[0];
+    long long e0 = 0, e1 = 0;
+    if (node_ptr) { e0 = node_ptr[n]; e1 = node_ptr[n + 1]; }
+    for (int j = 4 * lane; j < ldz; j += 128) {
+        // issue the independent loads first
+        float4 y[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) y[t] = (t < nb) ? f4(Yc + base[t] + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 z1 = f4(Z1 + row + j);
+        const float4 z0 = Z0 ? f4(Z0 + row + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 gg = f4(G + row + j);
+        const float4 kk = f4(ck + j);
+        float4 acc = y[0];
+#pragma unroll
+        for (int t = 1; t < 8; ++t) { acc.x += y[t].x; acc.y += y[t].y; acc.z += y[t].z; acc.w += y[t].w; }
+        for (long long e = e0; e < e1; ++e) {
+            const int g = node_ent[e];
+            const int I = ent_atom[g];
+            if (use_h) {
+                const float4 h = f4(Hca + 4 * (long long)g);
+                fma4(acc, h.x, f4(Ye + (size_t)(4 * I + 0) * lde + j));
+                fma4(acc, h.y, f4(Ye + (size_t)(4 * I + 1) * lde + j));
+                fma4(acc, h.z, f4(Ye + (size_t)(4 * I + 2) * lde + j));
+                fma4(acc, h.w, f4(Ye + (size_t)(4 * I + 3) * lde + j));
+            }
+            if (use_p) {
+                const float4 pc = f4(Pc + 4 * (long long)g);
+                fma4(acc, pc.x, f4(W + (size_t)(4 * I + 0) * lde + j));
+                fma4(acc, pc.y, f4(W + (size_t)(4 * I + 1) * lde + j));
+                fma4(acc, pc.z, f4(W + (size_t)(4 * I + 2) * lde + j));
+                fma4(acc, pc.w, f4(W + (size_t)(4 * I + 3) * lde + j));
+            }
+        }
+        float4 zn;
+        zn.x = a * (acc.x - c * z1.x) - b * z0.x + a * gg.x * kk.x;
+        zn.y = a * (acc.y - c * z1.y) - b * z0.y + a * gg.y * kk.y;
+        zn.z = a * (acc.z - c * z1.z) - b * z0.z + a * gg.z * kk.z;
+        zn.w = a * (acc.w - c * z1.w) - b * z0.w + a * gg.w * kk.w;
+        *reinterpret_cast<float4 *>(Zn + row + j) = zn;
+        if (e1 > e0) *reinterpret_cast<float4 *>(HYs + row + j) = acc;
+    }
+}
+
+// Support reduction, positions unrolled by 4 so the index and row loads overlap.
+template <typename T>
+__global__ void __launch_bounds__(256) k_support_reduce3(const long long *sup_off, const int *sup_node,
+                                                         const float *coefA, const float *coefB, const T *S,
+                                                         int N, int ld, int chunk, int nch, double *part) {
+    __shared__ float acc[8][128];
+    const int I = blockIdx.y, colg = blockIdx.z * 128;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < 8 * 128; i += blockDim.x) acc[i / 128][i % 128] = 0.f;
+    __syncthreads();
+    const long long beg = sup_off[I] + (long long)blockIdx.x * chunk;
+    const long long end = min(sup_off[I + 1], beg + chunk);
+    const int nr = coefB ? 8 : 4;
+    float r[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) r[i][t] = 0.f;
+    for (long long g0 = beg + 4 * warp; g0 < end; g0 += 32) {
+        int nodes[4];
+        float sv[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) nodes[u] = (g0 + u < end) ? sup_node[g0 + u] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int j = colg + lane + 32 * t;
+                sv[u][t] = (nodes[u] >= 0 && j < N) ? to_f(S[(long long)nodes[u] * ld + j]) : 0.f;
+            }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (nodes[u] < 0) continue;
+            const float4 qa = *reinterpret_cast<const float4 *>(coefA + 4 * (g0 + u));
+            const float4 qb = coefB ? *reinterpret_cast<const float4 *>(coefB + 4 * (g0 + u))
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                r[0][t] += qa.x * sv[u][t]; r[1][t] += qa.y * sv[u][t];
+                r[2][t] += qa.z * sv[u][t]; r[3][t] += qa.w * sv[u][t];
+                r[4][t] += qb.x * sv[u][t]; r[5][t] += qb.y * sv[u][t];
+                r[6][t] += qb.z * sv[u][t]; r[7][t] += qb.w * sv[u][t];
+            }
+        }
+    }
+    for (int i = 0; i < nr; ++i)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) atomicAdd(&acc[i][lane + 32 * t], r[i][t]);
+    __syncthreads();
+    double *o = part + ((long long)(I * nch + blockIdx.x) * 8) * N;
+    for (int i = threadIdx.x; i < nr * 128; i += blockDim.x) {
+        const int rr = i / 128, j = i % 128;
+        if (colg + j < N) o[(long long)rr * N + colg + j] = acc[rr][j];
+    }
+}
+
+// strided row kernels for the FP32 buffers of the tensor-core filter
+__global__ void __launch_bounds__(256) k_rows_residual_f(long long rows, int N, int ldz, const double *HV,
+                                                         const double *MV, const double *lam, float s1e, float *G,
+                                                         float *Z1) {
+    const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    for (int j = threadIdx.x & 31; j < ldz; j += 32) {
+        const float gv = j < N ? (float)(HV[r * N + j] - MV[r * N + j] * lam[j]) : 0.f;
+        G[r * ldz + j] = gv;
+        Z1[r * ldz + j] = s1e * gv;
+    }
+}
+__global__ void k_enr_minv_f(int n_enr, int N, int ld, const double *Binv, const float *X, float *Y, int ldy) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_enr * N) return;
+    const int k = idx / N, j = idx % N;
+    const int I = k / 4, f = k % 4;
+    const double *bb = Binv + 16 * I + 4 * f;
+    float s = 0.f;
+    for (int g = 0; g < 4; ++g) s += (float)bb[g] * X[(size_t)(4 * I + g) * ld + j];
+    Y[(size_t)k * ldy + j] = s;
+}
+__global__ void k_enr_rec_v(int n_enr, int N, int ldz, const double *Yraw, const double *Q, const float *Z1,
+                            const float *Z0, const float *G, const float *ck, float a, float c, float b, float *Zn) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_enr * ldz) return;
+    const int k = idx / ldz, j = idx % ldz;
+    const size_t o = (size_t)k * ldz + j;
+    if (j >= N) { Zn[o] = 0.f; return; }
+    const float hy = (float)(Yraw[(size_t)k * N + j] - Q[(size_t)k * N + j]);
+    const float z0 = Z0 ? Z0[o] : 0.f;
+    Zn[o] = a * (hy - c * Z1[o]) - b * z0 + a * G[o] * ck[j];
+}
+__global__ void __launch_bounds__(256) k_rows_minv_vout(long long nn, long long rows, int N, int ldz,
+                                                        const double *minv, const float *Z, const float *Ye, int lde,
+                                                        const double *V, const double *cm, double *Vout) {
+    const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    const bool fe = r < nn;
+    const float mi = fe ? (float)minv[r] : 0.f;
+    for (int j = threadIdx.x & 31; j < N; j += 32) {
+        const float y = fe ? mi * Z[r * ldz + j] : Ye[(r - nn) * lde + j];
+        Vout[r * N + j] = (double)y + V[r * N + j] * cm[j];
+    }
 }
 
 // Row-parallel elementwise helpers (warp per row, no 64-bit division)
@@ -1155,7 +1393,6 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
                                 int m, const double bounds[3], double *Vout) {
     const MeshDev &mh = ctx->m;
     const long long rows = ctx->n_rows, nn = ctx->n_nodes;
-    const long long n = rows * N;
     const int ne_ = ctx->n_enr;
     const double a0 = bounds[0], a = bounds[1], b = bounds[2];
     if (!(b > a) || !(a0 < a)) {
@@ -1172,26 +1409,32 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     std::vector<double> ck, sig;
     cheb_table(m, N, lam.data(), a, b, a0, ck, sig);
-    std::vector<float> ckf(ck.begin(), ck.end());
     const double e = 0.5 * (b - a), c = 0.5 * (b + a);
-    const int ldb = (N + 7) / 8 * 8, ldy = (N + 3) / 4 * 4;
+    const int ldz = (N + 3) / 4 * 4, ldb = (N + 7) / 8 * 8, ldy = ldz, lde = ldz;
+    std::vector<float> ckf((size_t)(m + 1) * ldz, 0.f);
+    for (int k = 0; k <= m; ++k)
+        for (int j = 0; j < N; ++j) ckf[(size_t)k * ldz + j] = (float)ck[(size_t)k * N + j];
     const long long ncells = (long long)mh.nx * mh.ny * mh.nz;
-    size_t need = 8192 + sizeof(float) * ((size_t)ctx->n_proj * N + 1) + sizeof(double) * n +
-                  sizeof(double) * (size_t)(m + 1) * N + sizeof(float) * (size_t)(m + 1) * N +
-                  sizeof(float) * (4 * n + (size_t)nn * N + (size_t)ne_ * N) + 2 * (size_t)nn * ldb +
+    const size_t nz = (size_t)rows * ldz;
+    size_t need = 16384 + sizeof(double) * (size_t)rows * N + sizeof(double) * (size_t)(m + 1) * N +
+                  sizeof(float) * ckf.size() + sizeof(float) * (4 * nz + (size_t)nn * ldz) +
+                  sizeof(float) * 2 * ((size_t)std::max(ne_, ctx->n_proj) * lde + 4) + 2 * (size_t)nn * ldb +
                   4 * (size_t)ncells * mh.ne * ldy;
     EFE_TRY(efe_workspace(ctx, need));
     Carver cv{(char *)ctx->d_ws, ctx->ws_bytes};
-    double *MV = cv.take<double>(n), *dck = cv.take<double>((size_t)(m + 1) * N);
-    float *fck = cv.take<float>((size_t)(m + 1) * N);
-    float *G = cv.take<float>(n), *Z0 = cv.take<float>(n), *Z1 = cv.take<float>(n), *Z2 = cv.take<float>(n);
-    float *HYs = cv.take<float>((size_t)nn * N), *Ye = cv.take<float>((size_t)ne_ * N + 1);
-    float *W32 = cv.take<float>((size_t)ctx->n_proj * N + 1);
+    double *MV = cv.take<double>((size_t)rows * N), *dck = cv.take<double>((size_t)(m + 1) * N);
+    float *fck = cv.take<float>(ckf.size());
+    float *G = cv.take<float>(nz), *Z0 = cv.take<float>(nz), *Z1 = cv.take<float>(nz), *Z2 = cv.take<float>(nz);
+    float *HYs = cv.take<float>((size_t)nn * ldz);
+    float *Ye = cv.take<float>((size_t)std::max(ne_, 1) * lde + 4);
+    float *W32 = cv.take<float>((size_t)std::max(ctx->n_proj, 1) * lde + 4);
     __nv_bfloat16 *Xb = cv.take<__nv_bfloat16>((size_t)nn * ldb);
     float *Ycells = cv.take<float>((size_t)ncells * mh.ne * ldy);
     EFE_CUDA(ctx, cudaMemcpyAsync(dck, ck.data(), sizeof(double) * ck.size(), cudaMemcpyHostToDevice, ctx->stream));
     EFE_CUDA(ctx, cudaMemcpyAsync(fck, ckf.data(), sizeof(float) * ckf.size(), cudaMemcpyHostToDevice, ctx->stream));
     EFE_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    EFE_CUDA(ctx, cudaMemsetAsync(Ye, 0, sizeof(float) * ((size_t)std::max(ne_, 1) * lde + 4), ctx->stream));
+    EFE_CUDA(ctx, cudaMemsetAsync(W32, 0, sizeof(float) * ((size_t)std::max(ctx->n_proj, 1) * lde + 4), ctx->stream));
     const bool cpl = (ctx->enrich || ctx->nonlocal) && ctx->natoms > 0;
     HxScratch s{};
     if (cpl) EFE_TRY(hx_scratch(ctx, N, s));
@@ -1201,29 +1444,22 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     Timer tm(ctx->stream);
     const long long l0 = ctx->launches;
     EFE_TRY(m_apply(ctx, V, MV, N, true));
-    k_rows_residual<float><<<rb_all, 256, 0, ctx->stream>>>(rows, N, HV, MV, lam_dev, G);
-    ctx->launches += 1;
-    // Z_1 = (s1/e) G
-    {
-        const float s1e = (float)(sig[1] / e);
-        k_cast_scale<<<nblk(n, 256), 256, 0, ctx->stream>>>(n, s1e, G, Z1);
-        ctx->launches++;
-    }
+    k_rows_residual_f<<<rb_all, 256, 0, ctx->stream>>>(rows, N, ldz, HV, MV, lam_dev, (float)(sig[1] / e), G, Z1);
+    ctx->launches++;
     float *Zprev = nullptr, *Zcur = Z1, *Znext = Z2, *Zspare = Z0;
     const dim3 gred(s.nch, std::max(ctx->natoms, 1), (N + 127) / 128);
     for (int k = 2; k <= m; ++k) {
         const float ak = (float)(2.0 * sig[k] / e), bk = (float)(sig[k - 1] * sig[k]), cf = (float)c;
-        // enriched rows of M~^-1 Z
         if (ne_) {
-            k_enr_mat<float><<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(ne_, N, ctx->d_Mblk_inv, 1,
-                                                                                     Zcur + nn * N, Ye);
+            k_enr_minv_f<<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(ne_, N, ldz, ctx->d_Mblk_inv,
+                                                                                Zcur + nn * ldz, Ye, lde);
             ctx->launches++;
         }
-        k_pre_bf16<<<rb_fe, 256, 0, ctx->stream>>>(mh, (int)nn, Zcur, Ye, N, ldb, ctx->d_minv, ctx->d_node_ptr,
-                                                   ctx->d_node_ent, ctx->d_ent_atom, ctx->d_C32, ctx->enrich ? 1 : 0,
-                                                   Xb);
+        k_pre_bf16_v<<<rb_fe, 256, 0, ctx->stream>>>(mh, (int)nn, Zcur, ldz, Ye, lde, ldb, ctx->d_minv,
+                                                     ctx->d_node_ptr, ctx->d_node_ent, ctx->d_ent_atom, ctx->d_C32,
+                                                     ctx->enrich ? 1 : 0, Xb);
         ctx->launches++;
-        EFE_TRY(efe_check_launch(ctx, "k_pre_bf16"));
+        EFE_TRY(efe_check_launch(ctx, "k_pre_bf16_v"));
         {
             auto *ev = cell_event_pair(ctx);
             if (ev) cudaEventRecord(ev->first, ctx->stream);
@@ -1231,7 +1467,7 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
             if (ev) cudaEventRecord(ev->second, ctx->stream);
         }
         if (cpl) {
-            k_support_reduce2<__nv_bfloat16><<<gred, 256, 0, ctx->stream>>>(
+            k_support_reduce3<__nv_bfloat16><<<gred, 256, 0, ctx->stream>>>(
                 ctx->d_sup_off, ctx->d_sup_node, ctx->enrich ? ctx->d_Hca32 : ctx->d_Pc32,
                 (ctx->enrich && ctx->nonlocal) ? ctx->d_Pc32 : nullptr, Xb, N, ldb, s.chunk, s.nch, s.part);
             const long long n8 = (long long)ctx->natoms * 8 * N;
@@ -1241,31 +1477,33 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
             ctx->launches += 2;
             if (ctx->nonlocal) {
                 k_proj_w<float><<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
-                    ctx->n_proj, ne_, s.Wc, ctx->enrich ? ctx->d_Pa : nullptr, Ye, N, ctx->d_hproj, N, s.W);
-                k_to_float_d<<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
-                    (long long)ctx->n_proj * N, s.W, W32);
+                    ctx->n_proj, ne_, s.Wc, ctx->enrich ? ctx->d_Pa : nullptr, Ye, lde, ctx->d_hproj, N, s.W);
+                k_to_float_strided<<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
+                    ctx->n_proj, N, s.W, W32, lde);
                 ctx->launches += 2;
             }
             if (ctx->enrich) {
                 k_enr_raw<float><<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(
-                    ne_, ctx->n_proj, s.Rh, ctx->d_Haa, ctx->nonlocal ? ctx->d_Pa : nullptr, s.W, Ye, N, N, s.Yraw);
+                    ne_, ctx->n_proj, s.Rh, ctx->d_Haa, ctx->nonlocal ? ctx->d_Pa : nullptr, s.W, Ye, lde, N,
+                    s.Yraw);
                 ctx->launches++;
             }
         }
-        k_gather_rec<<<rb_fe, 256, 0, ctx->stream>>>(mh, (int)nn, N, Ycells, ldy, cpl ? ctx->d_node_ptr : nullptr,
-                                                     ctx->d_node_ent, ctx->d_ent_atom, ctx->d_Hca32, ctx->d_Pc32, Ye, W32,
-                                                     ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0, Zcur, Zprev, G,
-                                                     fck + (size_t)(k - 1) * N, ak, cf, bk, Znext, HYs);
+        k_gather_rec_v<<<rb_fe, 256, 0, ctx->stream>>>(mh, (int)nn, ldz, Ycells, ldy, cpl ? ctx->d_node_ptr : nullptr,
+                                                       ctx->d_node_ent, ctx->d_ent_atom, ctx->d_Hca32, ctx->d_Pc32,
+                                                       Ye, W32, lde, ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0,
+                                                       Zcur, Zprev, G, fck + (size_t)(k - 1) * ldz, ak, cf, bk, Znext,
+                                                       HYs);
         ctx->launches++;
-        EFE_TRY(efe_check_launch(ctx, "k_gather_rec"));
+        EFE_TRY(efe_check_launch(ctx, "k_gather_rec_v"));
         if (ne_) {
-            k_support_reduce2<float><<<gred, 256, 0, ctx->stream>>>(ctx->d_sup_off, ctx->d_sup_node, ctx->d_C32,
-                                                                    nullptr, HYs, N, N, s.chunk, s.nch, s.part);
+            k_support_reduce3<float><<<gred, 256, 0, ctx->stream>>>(ctx->d_sup_off, ctx->d_sup_node, ctx->d_C32,
+                                                                    nullptr, HYs, N, ldz, s.chunk, s.nch, s.part);
             const long long n8 = (long long)ctx->natoms * 8 * N;
             k_support_sum<<<nblk(n8, 256), 256, 0, ctx->stream>>>(ctx->natoms, s.nch, N, s.part, s.Q, nullptr);
-            k_enr_rec<<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(
-                ne_, N, s.Yraw, s.Q, Zcur + nn * N, Zprev ? Zprev + nn * N : nullptr, G + nn * N,
-                fck + (size_t)(k - 1) * N, ak, cf, bk, Znext + nn * N);
+            k_enr_rec_v<<<nblk((long long)ne_ * ldz, 256), 256, 0, ctx->stream>>>(
+                ne_, N, ldz, s.Yraw, s.Q, Zcur + nn * ldz, Zprev ? Zprev + nn * ldz : nullptr, G + nn * ldz,
+                fck + (size_t)(k - 1) * ldz, ak, cf, bk, Znext + nn * ldz);
             ctx->launches += 3;
         }
         float *old_prev = Zprev ? Zprev : Zspare;
@@ -1274,13 +1512,14 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
         Znext = old_prev;
     }
     // V_out = M~^-1 Z_m + V diag(C_m(lam))
-    float *Y = Znext;
-    k_rows_minv<<<rb_fe, 256, 0, ctx->stream>>>(nn, N, ctx->d_minv, Zcur, Y);
-    if (ne_)
-        k_enr_mat<float><<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(ne_, N, ctx->d_Mblk_inv, 1,
-                                                                                 Zcur + nn * N, Y + nn * N);
-    k_rows_vout<<<rb_all, 256, 0, ctx->stream>>>(rows, N, Y, V, dck + (size_t)m * N, Vout);
-    ctx->launches += 3;
+    if (ne_) {
+        k_enr_minv_f<<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(ne_, N, ldz, ctx->d_Mblk_inv,
+                                                                            Zcur + nn * ldz, Ye, lde);
+        ctx->launches++;
+    }
+    k_rows_minv_vout<<<rb_all, 256, 0, ctx->stream>>>(nn, rows, N, ldz, ctx->d_minv, Zcur, Ye, lde, V,
+                                                      dck + (size_t)m * N, Vout);
+    ctx->launches++;
     EFE_TRY(efe_check_launch(ctx, "filter_tensor"));
     ctx->stats.ms_filter = tm.stop();
     ctx->stats.ms_cell = cell_events_ms(ctx);
