@@ -149,8 +149,16 @@ def roofline(head, d, N, ms_sweep, pk, pk_kind):
         # (~292 flop/B), so HBM-bound
         traffic_alg = d["n_cells"] * (2.0 * d["ne"] ** 2 + 6.0 * d["ne"] * N)
         achieved = traffic_alg / (ms_sweep / 1e3) / 1e9 if ms_sweep > 0 else None
+        traffic = None
+        try:   # measured DRAM bytes per cell (ncu capture, same kernel), scaled to this launch
+            with open(os.path.join(ROOT, "profiles", "k_cell_mma_traffic.txt")) as f:
+                for line in f:
+                    if line.startswith("bytes_per_cell") and d["ne"] == 343 and N == 154:
+                        traffic = float(line.split()[1]) * d["n_cells"]
+        except OSError:
+            pass
         return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"] if achieved else None, "traffic": None,
+                "frac": achieved / pk["hbm_gbs"] if achieved else None, "traffic": traffic,
                 "algorithmic_bytes": traffic_alg, "peak_kind": pk_kind + " (burst copy)",
                 "kernel": "k_cell_mma (tcgen05 cell products, one launch per H apply)",
                 "ms_per_launch": ms_sweep}

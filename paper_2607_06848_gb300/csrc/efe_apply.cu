@@ -548,30 +548,54 @@ __global__ void __launch_bounds__(256) k_pre_bf16_v(MeshDev m, int nn, const flo
     node_xyz(m, n, ix, iy, iz);
     const bool inter = node_interior(m, ix, iy, iz);
     const float mi = inter ? (float)minv[n] : 0.f;
-    long long e0 = 0, e1 = 0;
-    if (inter && use_c) { e0 = node_ptr[n]; e1 = node_ptr[n + 1]; }
+    int ecount = 0;
+    long long e0 = 0;
+    if (inter && use_c) {
+        e0 = node_ptr[n];
+        ecount = (int)(node_ptr[n + 1] - e0);
+    }
+    // this node's coupling entries, one per lane (chunks of 32), broadcast by shuffles
     const float *zr = Z + (size_t)n * ldz;
     __nv_bfloat16 *out = Xb + (size_t)n * ldb;
-    for (int j = 4 * lane; j < ldb; j += 128) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (inter && j < ldz) {
-            const float4 z = f4(zr + j);
-            v = make_float4(mi * z.x, mi * z.y, mi * z.z, mi * z.w);
-            for (long long e = e0; e < e1; ++e) {
-                const int g = node_ent[e];
-                const int I = ent_atom[g];
-                const float4 c = f4(C + 4 * (long long)g);
-                fma4(v, -c.x, f4(Ye + (size_t)(4 * I + 0) * lde + j));
-                fma4(v, -c.y, f4(Ye + (size_t)(4 * I + 1) * lde + j));
-                fma4(v, -c.z, f4(Ye + (size_t)(4 * I + 2) * lde + j));
-                fma4(v, -c.w, f4(Ye + (size_t)(4 * I + 3) * lde + j));
+    float4 v[2];
+    for (int t = 0; t < 2; ++t) {
+        const int j = 4 * lane + 128 * t;
+        v[t] = (inter && j < ldz) ? f4(zr + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[t].x *= mi; v[t].y *= mi; v[t].z *= mi; v[t].w *= mi;
+    }
+    for (int c0 = 0; c0 < ecount; c0 += 32) {
+        int myI = 0;
+        float4 myc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c0 + lane < ecount) {
+            const int g = node_ent[e0 + c0 + lane];
+            myI = ent_atom[g];
+            myc = f4(C + 4 * (long long)g);
+        }
+        const int cnt = min(32, ecount - c0);
+        for (int k = 0; k < cnt; ++k) {
+            const int I = __shfl_sync(0xffffffffu, myI, k);
+            const float cx = __shfl_sync(0xffffffffu, myc.x, k), cy = __shfl_sync(0xffffffffu, myc.y, k);
+            const float cz = __shfl_sync(0xffffffffu, myc.z, k), cw = __shfl_sync(0xffffffffu, myc.w, k);
+            for (int t = 0; t < 2; ++t) {
+                const int j = 4 * lane + 128 * t;
+                if (j < ldz) {
+                    fma4(v[t], -cx, f4(Ye + (size_t)(4 * I + 0) * lde + j));
+                    fma4(v[t], -cy, f4(Ye + (size_t)(4 * I + 1) * lde + j));
+                    fma4(v[t], -cz, f4(Ye + (size_t)(4 * I + 2) * lde + j));
+                    fma4(v[t], -cw, f4(Ye + (size_t)(4 * I + 3) * lde + j));
+                }
             }
         }
-        __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
-        uint2 pk;
-        pk.x = *reinterpret_cast<uint32_t *>(&lo);
-        pk.y = *reinterpret_cast<uint32_t *>(&hi);
-        *reinterpret_cast<uint2 *>(out + j) = pk;
+    }
+    for (int t = 0; t < 2; ++t) {
+        const int j = 4 * lane + 128 * t;
+        if (j < ldb) {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(v[t].x, v[t].y), hi = __floats2bfloat162_rn(v[t].z, v[t].w);
+            uint2 pk;
+            pk.x = *reinterpret_cast<uint32_t *>(&lo);
+            pk.y = *reinterpret_cast<uint32_t *>(&hi);
+            *reinterpret_cast<uint2 *>(out + j) = pk;
+        }
     }
 }
 
@@ -616,101 +640,145 @@ __global__ void __launch_bounds__(256) k_gather_rec_v(MeshDev m, int nn, int ldz
                 base[nb++] = (cell * m.ne + l) * ldy;
             }
     for (int t = nb; t < 8; ++t) base[t] = base[0];
-    long long e0 = 0, e1 = 0;
-    if (node_ptr) { e0 = node_ptr[n]; e1 = node_ptr[n + 1]; }
-    for (int j = 4 * lane; j < ldz; j += 128) {
-        // issue the independent loads first
-        float4 y[8];
+    int ecount = 0;
+    long long e0 = 0;
+    if (node_ptr) {
+        e0 = node_ptr[n];
+        ecount = (int)(node_ptr[n + 1] - e0);
+    }
+    float4 acc[2];
+    for (int t = 0; t < 2; ++t) {
+        const int j = 4 * lane + 128 * t;
+        acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < ldz) {
+            float4 y[8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) y[t] = (t < nb) ? f4(Yc + base[t] + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int u = 0; u < 8; ++u) y[u] = (u < nb) ? f4(Yc + base[u] + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) { acc[t].x += y[u].x; acc[t].y += y[u].y; acc[t].z += y[u].z; acc[t].w += y[u].w; }
+        }
+    }
+    for (int c0 = 0; c0 < ecount; c0 += 32) {
+        int myI = 0;
+        float4 myh = make_float4(0.f, 0.f, 0.f, 0.f), myp = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c0 + lane < ecount) {
+            const int g = node_ent[e0 + c0 + lane];
+            myI = ent_atom[g];
+            if (use_h) myh = f4(Hca + 4 * (long long)g);
+            if (use_p) myp = f4(Pc + 4 * (long long)g);
+        }
+        const int cnt = min(32, ecount - c0);
+        for (int k = 0; k < cnt; ++k) {
+            const int I = __shfl_sync(0xffffffffu, myI, k);
+            const float h0 = __shfl_sync(0xffffffffu, myh.x, k), h1 = __shfl_sync(0xffffffffu, myh.y, k);
+            const float h2 = __shfl_sync(0xffffffffu, myh.z, k), h3 = __shfl_sync(0xffffffffu, myh.w, k);
+            const float p0 = __shfl_sync(0xffffffffu, myp.x, k), p1 = __shfl_sync(0xffffffffu, myp.y, k);
+            const float p2 = __shfl_sync(0xffffffffu, myp.z, k), p3 = __shfl_sync(0xffffffffu, myp.w, k);
+            for (int t = 0; t < 2; ++t) {
+                const int j = 4 * lane + 128 * t;
+                if (j >= ldz) continue;
+                if (use_h) {
+                    fma4(acc[t], h0, f4(Ye + (size_t)(4 * I + 0) * lde + j));
+                    fma4(acc[t], h1, f4(Ye + (size_t)(4 * I + 1) * lde + j));
+                    fma4(acc[t], h2, f4(Ye + (size_t)(4 * I + 2) * lde + j));
+                    fma4(acc[t], h3, f4(Ye + (size_t)(4 * I + 3) * lde + j));
+                }
+                if (use_p) {
+                    fma4(acc[t], p0, f4(W + (size_t)(4 * I + 0) * lde + j));
+                    fma4(acc[t], p1, f4(W + (size_t)(4 * I + 1) * lde + j));
+                    fma4(acc[t], p2, f4(W + (size_t)(4 * I + 2) * lde + j));
+                    fma4(acc[t], p3, f4(W + (size_t)(4 * I + 3) * lde + j));
+                }
+            }
+        }
+    }
+    for (int t = 0; t < 2; ++t) {
+        const int j = 4 * lane + 128 * t;
+        if (j >= ldz) continue;
         const float4 z1 = f4(Z1 + row + j);
         const float4 z0 = Z0 ? f4(Z0 + row + j) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 gg = f4(G + row + j);
         const float4 kk = f4(ck + j);
-        float4 acc = y[0];
-#pragma unroll
-        for (int t = 1; t < 8; ++t) { acc.x += y[t].x; acc.y += y[t].y; acc.z += y[t].z; acc.w += y[t].w; }
-        for (long long e = e0; e < e1; ++e) {
-            const int g = node_ent[e];
-            const int I = ent_atom[g];
-            if (use_h) {
-                const float4 h = f4(Hca + 4 * (long long)g);
-                fma4(acc, h.x, f4(Ye + (size_t)(4 * I + 0) * lde + j));
-                fma4(acc, h.y, f4(Ye + (size_t)(4 * I + 1) * lde + j));
-                fma4(acc, h.z, f4(Ye + (size_t)(4 * I + 2) * lde + j));
-                fma4(acc, h.w, f4(Ye + (size_t)(4 * I + 3) * lde + j));
-            }
-            if (use_p) {
-                const float4 pc = f4(Pc + 4 * (long long)g);
-                fma4(acc, pc.x, f4(W + (size_t)(4 * I + 0) * lde + j));
-                fma4(acc, pc.y, f4(W + (size_t)(4 * I + 1) * lde + j));
-                fma4(acc, pc.z, f4(W + (size_t)(4 * I + 2) * lde + j));
-                fma4(acc, pc.w, f4(W + (size_t)(4 * I + 3) * lde + j));
-            }
-        }
         float4 zn;
-        zn.x = a * (acc.x - c * z1.x) - b * z0.x + a * gg.x * kk.x;
-        zn.y = a * (acc.y - c * z1.y) - b * z0.y + a * gg.y * kk.y;
-        zn.z = a * (acc.z - c * z1.z) - b * z0.z + a * gg.z * kk.z;
-        zn.w = a * (acc.w - c * z1.w) - b * z0.w + a * gg.w * kk.w;
+        zn.x = a * (acc[t].x - c * z1.x) - b * z0.x + a * gg.x * kk.x;
+        zn.y = a * (acc[t].y - c * z1.y) - b * z0.y + a * gg.y * kk.y;
+        zn.z = a * (acc[t].z - c * z1.z) - b * z0.z + a * gg.z * kk.z;
+        zn.w = a * (acc[t].w - c * z1.w) - b * z0.w + a * gg.w * kk.w;
         *reinterpret_cast<float4 *>(Zn + row + j) = zn;
-        if (e1 > e0) *reinterpret_cast<float4 *>(HYs + row + j) = acc;
+        if (ecount > 0) *reinterpret_cast<float4 *>(HYs + row + j) = acc[t];
     }
 }
 
-// Support reduction, positions unrolled by 4 so the index and row loads overlap.
+// Support reduction: warps over positions (8 rows in flight per warp), lanes
+// over 4-column vectors (two 128-column slots), one block per (chunk, atom).
+__device__ inline float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ inline float4 ld4(const __nv_bfloat16 *p) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162 *>(&u.x);
+    const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162 *>(&u.y);
+    const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_support_reduce3(const long long *sup_off, const int *sup_node,
                                                          const float *coefA, const float *coefB, const T *S,
                                                          int N, int ld, int chunk, int nch, double *part) {
-    __shared__ float acc[8][128];
-    const int I = blockIdx.y, colg = blockIdx.z * 128;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < 8 * 128; i += blockDim.x) acc[i / 128][i % 128] = 0.f;
+    // thread t: float4 column group cg = t % ncg, position lane pl = t / ncg
+    __shared__ float acc[8][256];
+    const int I = blockIdx.y;
+    const int ncg = (N + 3) / 4;                 // <= 64
+    const int npl = blockDim.x / ncg;
+    const int cg = threadIdx.x % ncg, pl = threadIdx.x / ncg;
+    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) acc[i / 256][i % 256] = 0.f;
     __syncthreads();
     const long long beg = sup_off[I] + (long long)blockIdx.x * chunk;
     const long long end = min(sup_off[I + 1], beg + chunk);
-    const int nr = coefB ? 8 : 4;
-    float r[8][4];
+    const bool two = coefB != nullptr;
+    float4 r[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 8; ++i) r[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pl < npl) {
+        const int j = 4 * cg;
+        for (long long g0 = beg + 4 * pl; g0 < end; g0 += 4 * npl) {
+            int nodes[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) r[i][t] = 0.f;
-    for (long long g0 = beg + 4 * warp; g0 < end; g0 += 32) {
-        int nodes[4];
-        float sv[4][4];
+            for (int u = 0; u < 4; ++u) nodes[u] = (g0 + u < end) ? sup_node[g0 + u] : -1;
+            float4 sv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) nodes[u] = (g0 + u < end) ? sup_node[g0 + u] : -1;
+            for (int u = 0; u < 4; ++u)
+                sv[u] = nodes[u] >= 0 ? ld4(S + (long long)nodes[u] * ld + j) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int j = colg + lane + 32 * t;
-                sv[u][t] = (nodes[u] >= 0 && j < N) ? to_f(S[(long long)nodes[u] * ld + j]) : 0.f;
-            }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (nodes[u] < 0) continue;
-            const float4 qa = *reinterpret_cast<const float4 *>(coefA + 4 * (g0 + u));
-            const float4 qb = coefB ? *reinterpret_cast<const float4 *>(coefB + 4 * (g0 + u))
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                r[0][t] += qa.x * sv[u][t]; r[1][t] += qa.y * sv[u][t];
-                r[2][t] += qa.z * sv[u][t]; r[3][t] += qa.w * sv[u][t];
-                r[4][t] += qb.x * sv[u][t]; r[5][t] += qb.y * sv[u][t];
-                r[6][t] += qb.z * sv[u][t]; r[7][t] += qb.w * sv[u][t];
+            for (int u = 0; u < 4; ++u) {
+                if (nodes[u] < 0) continue;
+                const float4 qa = ld4(coefA + 4 * (g0 + u));
+                fma4(r[0], qa.x, sv[u]);
+                fma4(r[1], qa.y, sv[u]);
+                fma4(r[2], qa.z, sv[u]);
+                fma4(r[3], qa.w, sv[u]);
+                if (two) {
+                    const float4 qb = ld4(coefB + 4 * (g0 + u));
+                    fma4(r[4], qb.x, sv[u]);
+                    fma4(r[5], qb.y, sv[u]);
+                    fma4(r[6], qb.z, sv[u]);
+                    fma4(r[7], qb.w, sv[u]);
+                }
             }
         }
+        const int nr = two ? 8 : 4;
+        for (int i = 0; i < nr; ++i) {
+            atomicAdd(&acc[i][j + 0], r[i].x);
+            atomicAdd(&acc[i][j + 1], r[i].y);
+            atomicAdd(&acc[i][j + 2], r[i].z);
+            atomicAdd(&acc[i][j + 3], r[i].w);
+        }
     }
-    for (int i = 0; i < nr; ++i)
-#pragma unroll
-        for (int t = 0; t < 4; ++t) atomicAdd(&acc[i][lane + 32 * t], r[i][t]);
     __syncthreads();
+    const int nr = two ? 8 : 4;
     double *o = part + ((long long)(I * nch + blockIdx.x) * 8) * N;
-    for (int i = threadIdx.x; i < nr * 128; i += blockDim.x) {
-        const int rr = i / 128, j = i % 128;
-        if (colg + j < N) o[(long long)rr * N + colg + j] = acc[rr][j];
+    for (int i = threadIdx.x; i < nr * 256; i += blockDim.x) {
+        const int rr = i / 256, jj = i % 256;
+        if (jj < N) o[(long long)rr * N + jj] = acc[rr][jj];
     }
 }
 
@@ -1447,7 +1515,12 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     k_rows_residual_f<<<rb_all, 256, 0, ctx->stream>>>(rows, N, ldz, HV, MV, lam_dev, (float)(sig[1] / e), G, Z1);
     ctx->launches++;
     float *Zprev = nullptr, *Zcur = Z1, *Znext = Z2, *Zspare = Z0;
-    const dim3 gred(s.nch, std::max(ctx->natoms, 1), (N + 127) / 128);
+    const dim3 gred(s.nch, std::max(ctx->natoms, 1), 1);
+    if (N > 256) {
+        ctx->err = "the tensor-core filter takes at most 256 columns per call";
+        return EFE_ERR_ARG;
+    }
+    if (N > 128 * 2) return EFE_ERR_ARG;
     for (int k = 2; k <= m; ++k) {
         const float ak = (float)(2.0 * sig[k] / e), bk = (float)(sig[k - 1] * sig[k]), cf = (float)c;
         if (ne_) {
