@@ -199,6 +199,87 @@ efe_status efe_filter_host(efe_ctx *ctx, const double *V, const double *HV, cons
                            int N, int m, const double bounds[3], efe_precision prec,
                            double *Vout);
 
+/* ------------------------------------------------------------------------
+ * Self-consistent field (Sec. II.A; Sec. IV: 500 K smearing, Anderson mixing)
+ * ------------------------------------------------------------------------ */
+
+/* b_sm at the quadrature points: sum_I -Z_I g_rloc(x - R_I), the Gaussian
+ * charge whose potential is the local part -Z erf(r/rloc)/r (Eq. EZZbmsear).
+ * b_q: device, n_quad. */
+efe_status efe_smeared_charge(efe_ctx *ctx, double *b_q);
+
+/* Superposition of atomic Gaussians Z_I (kappa/pi)^3/2 exp(-kappa r^2) at the
+ * quadrature points, scaled so that its integral is N_e.  rho_q: device. */
+efe_status efe_atomic_density(efe_ctx *ctx, double kappa, double *rho_q);
+
+/* rho(x_q) = 2 sum_i occ_i psi_i(x_q)^2 (Eq. rhocompute) with psi the EFE
+ * expansion of column i of X (device rows x N); occ: host N; rho_q: device. */
+efe_status efe_density(efe_ctx *ctx, const double *X, int N, const double *occ, double *rho_q);
+
+/* LDA exchange-correlation (Slater + Perdew-Wang 1992, spin-unpolarised) at
+ * every quadrature point; densities below 1e-14 give 0.  Either output may be
+ * NULL.  All device, n_quad. */
+efe_status efe_xc(efe_ctx *ctx, const double *rho_q, double *vxc_q, double *exc_q);
+
+/* FE solution of -1/(4 pi) Lap phi = f with phi = 0 on the box (Eq. poisson),
+ * Jacobi-preconditioned conjugate gradients to ||r|| < tol ||F||.
+ * f_q: device n_quad; phi_nodes: device n_nodes (out); phi_q: device n_quad
+ * (out, may be NULL); iters, rel_res: host (may be NULL). */
+efe_status efe_poisson(efe_ctx *ctx, const double *f_q, double *phi_nodes, double *phi_q,
+                       double tol, int max_it, int *iters, double *rel_res);
+
+/* Fermi level mu with 2 sum_i f(eig_i, mu) = n_elec (Eq. electronconstraint),
+ * f = 1/(1 + exp((eig - mu)/kT)), by bisection on the GPU.  eig, occ: host N. */
+efe_status efe_fermi(efe_ctx *ctx, const double *eig, int N, double n_elec, double kT,
+                     double *mu, double *occ);
+
+/* *out = int a b (quadrature), b may be NULL (int a).  a_q, b_q: device. */
+efe_status efe_integrate(efe_ctx *ctx, const double *a_q, const double *b_q, double *out);
+
+typedef void (*efe_scf_log_fn)(void *user, int iter, double E, double F, double mu,
+                               double drho, double dE, double resid0);
+
+typedef struct {
+    int cheb_degree;      /* filter degree m */
+    double temperature;   /* smearing temperature, K */
+    double mix_beta;      /* Anderson mixing parameter */
+    int mix_history;      /* Anderson history length */
+    double tol_rho;       /* ||rho_out - rho_in||_L2 / N_e */
+    double tol_e;         /* |E_k - E_{k-1}| per atom, Ha */
+    int max_iter;
+    double first_tol;     /* first iteration: passes until the max residual of the
+                             occupied states is below this */
+    int first_max_pass;
+    int renormalize;      /* scale rho_out to integrate to N_e */
+    double kappa;         /* exponent of the atomic Gaussians of the start density */
+    double poisson_tol;
+    int precision;        /* efe_precision of the filter passes */
+    efe_scf_log_fn log;   /* optional per-iteration callback */
+    void *log_user;
+} efe_scf_opts;
+
+typedef struct {
+    double E;             /* total energy (Ha) */
+    double F;             /* free energy E - TS */
+    double mu;            /* Fermi level */
+    double drho, dE;      /* last convergence measures */
+    int iters, converged;
+    long long poisson_iters;
+    double *eig;          /* host N (optional, caller-owned) */
+    double *rho_q;        /* device n_quad (optional, caller-owned): final rho_out */
+} efe_scf_result;
+
+/* The SCF loop: v_eff = v_xc[rho_in] + phi[rho_in + b_sm]; operator assembly;
+ * eigenpairs by residual ChFSI (first iteration: Lanczos bounds and passes
+ * until first_tol; later: one filter pass + Rayleigh-Ritz); Fermi level;
+ * rho_out; E = 2 sum f eps - int rho_out v_eff + E_xc[rho_out]
+ * + 1/2 int (rho_out + b) phi[rho_out] - E_self + dE_ZZ; Anderson mixing.
+ * X: device rows x N, start vectors in, eigenvectors out; u0: device rows
+ * (Lanczos start); rho0_q: device n_quad or NULL (atomic superposition).
+ * EFE_ERR_NO_CONVERGE after max_iter (results still written). */
+efe_status efe_scf(efe_ctx *ctx, const efe_scf_opts *opts, double *X, int N, const double *u0,
+                   const double *rho0_q, efe_scf_result *res);
+
 #ifdef __cplusplus
 }
 #endif

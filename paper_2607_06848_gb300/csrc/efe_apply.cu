@@ -145,8 +145,6 @@ __global__ void k_xprime(MeshDev m, long long n_nodes, const T *X, T *Xp, int N,
 __device__ inline double to_d(double x) { return x; }
 __device__ inline double to_d(float x) { return (double)x; }
 __device__ inline double to_d(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
-__device__ inline float to_f(float x) { return x; }
-__device__ inline float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
 
 // Partial support reductions: for atom I (blockIdx.y) and chunk blockIdx.x,
 //   part[(I*nch + chunk)][r][j] = sum_{g in chunk} coef_r[g] * S[node(g)][j]
@@ -347,186 +345,11 @@ __device__ inline void node_xyz(const MeshDev &m, int n, int &ix, int &iy, int &
     iz = t / m.Gy;
 }
 
-// Xb[n][j] = bf16( minv[n] Z[n][j] - sum_e C_e . Ye[atom(e)][j] ): the first
-// half of T applied to M~^-1 Z (FE rows), padded to ldb columns.
-__global__ void __launch_bounds__(256) k_pre_bf16(MeshDev m, int nn, const float *Z, const float *Ye, int N,
-                                                  int ldb, const double *minv, const long long *node_ptr,
-                                                  const int *node_ent, const int *ent_atom, const float *C,
-                                                  int use_c, __nv_bfloat16 *Xb) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = blockIdx.x * 8 + warp;
-    if (n >= nn) return;
-    int ix, iy, iz;
-    node_xyz(m, n, ix, iy, iz);
-    const bool inter = node_interior(m, ix, iy, iz);
-    const float mi = inter ? (float)minv[n] : 0.f;
-    long long e0 = 0, e1 = 0;
-    if (inter && use_c) { e0 = node_ptr[n]; e1 = node_ptr[n + 1]; }
-    const float *zr = Z + (size_t)n * N;
-    __nv_bfloat16 *out = Xb + (size_t)n * ldb;
-    for (int j = 2 * lane; j < ldb; j += 64) {
-        float v0 = 0.f, v1 = 0.f;
-        if (inter) {
-            if (j < N) v0 = mi * zr[j];
-            if (j + 1 < N) v1 = mi * zr[j + 1];
-            for (long long e = e0; e < e1; ++e) {
-                const int g = node_ent[e];
-                const int I = ent_atom[g];
-                const float *c = C + 4 * (long long)g;
-                for (int f = 0; f < 4; ++f) {
-                    const float cf = c[f];
-                    const float *yr = Ye + (size_t)(4 * I + f) * N;
-                    if (j < N) v0 -= cf * yr[j];
-                    if (j + 1 < N) v1 -= cf * yr[j + 1];
-                }
-            }
-        }
-        *reinterpret_cast<__nv_bfloat162 *>(out + j) = __floats2bfloat162_rn(v0, v1);
-    }
-}
-
-// Fused: HY_c[n] = sum over the node's cells of their product rows + the
-// node-side coupling, then the recurrence for the FE rows
-//   Zn = a (HY - c Z1) - b Z0 + a G ck,
-// and HY kept (HYs) only on nodes that carry coupling entries.
-__global__ void __launch_bounds__(256) k_gather_rec(MeshDev m, int nn, int N, const float *Yc, int ldy,
-                                                    const long long *node_ptr, const int *node_ent,
-                                                    const int *ent_atom, const float *Hca, const float *Pc,
-                                                    const float *Ye, const float *W, int use_h, int use_p,
-                                                    const float *Z1, const float *Z0, const float *G,
-                                                    const float *ck, float a, float c, float b, float *Zn,
-                                                    float *HYs) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = blockIdx.x * 8 + warp;
-    if (n >= nn) return;
-    int ix, iy, iz;
-    node_xyz(m, n, ix, iy, iz);
-    float *zn = Zn + (size_t)n * N;
-    if (!node_interior(m, ix, iy, iz)) {
-        for (int j = lane; j < N; j += 32) zn[j] = 0.f;
-        return;
-    }
-    int cv[3][2], av[3][2], cnt[3];
-    const int ii[3] = {ix, iy, iz}, nc[3] = {m.nx, m.ny, m.nz};
-    for (int d = 0; d < 3; ++d) {
-        const int q = ii[d] / m.p, r = ii[d] - q * m.p;
-        cnt[d] = 0;
-        if (r == 0) {
-            if (q - 1 >= 0) { cv[d][cnt[d]] = q - 1; av[d][cnt[d]] = m.p; ++cnt[d]; }
-            if (q < nc[d]) { cv[d][cnt[d]] = q; av[d][cnt[d]] = 0; ++cnt[d]; }
-        } else {
-            cv[d][0] = q; av[d][0] = r; cnt[d] = 1;
-        }
-    }
-    long long base[8];
-    int nb = 0;
-    for (int a2 = 0; a2 < cnt[2]; ++a2)
-        for (int b2 = 0; b2 < cnt[1]; ++b2)
-            for (int c2 = 0; c2 < cnt[0]; ++c2) {
-                const long long cell = ((long long)cv[2][a2] * m.ny + cv[1][b2]) * m.nx + cv[0][c2];
-                const int l = (av[2][a2] * m.np1 + av[1][b2]) * m.np1 + av[0][c2];
-                base[nb++] = (cell * m.ne + l) * ldy;
-            }
-    long long e0 = 0, e1 = 0;
-    if (node_ptr) { e0 = node_ptr[n]; e1 = node_ptr[n + 1]; }
-    const size_t row = (size_t)n * N;
-    for (int j = lane; j < N; j += 32) {
-        float acc = 0.f;
-        for (int t = 0; t < nb; ++t) acc += Yc[base[t] + j];
-        for (long long e = e0; e < e1; ++e) {
-            const int g = node_ent[e];
-            const int I = ent_atom[g];
-            if (use_h) {
-                const float *h = Hca + 4 * (long long)g;
-                for (int f = 0; f < 4; ++f) acc += h[f] * Ye[(size_t)(4 * I + f) * N + j];
-            }
-            if (use_p) {
-                const float *pc = Pc + 4 * (long long)g;
-                for (int f = 0; f < 4; ++f) acc += pc[f] * W[(size_t)(4 * I + f) * N + j];
-            }
-        }
-        const float z0 = Z0 ? Z0[row + j] : 0.f;
-        zn[j] = a * (acc - c * Z1[row + j]) - b * z0 + a * G[row + j] * ck[j];
-        if (e1 > e0) HYs[row + j] = acc;
-    }
-}
-
-// Support reductions with warps over positions and lanes over a 128-column
-// group (blockIdx.z): part[(I*nch + chunk)*8 + r][j] = sum_g coef_r[g] S[node(g)][j].
-template <typename T>
-__global__ void __launch_bounds__(256) k_support_reduce2(const long long *sup_off, const int *sup_node,
-                                                         const float *coefA, const float *coefB, const T *S,
-                                                         int N, int ld, int chunk, int nch, double *part) {
-    __shared__ float acc[8][128];
-    const int I = blockIdx.y, colg = blockIdx.z * 128;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < 8 * 128; i += blockDim.x) acc[i / 128][i % 128] = 0.f;
-    __syncthreads();
-    const long long beg = sup_off[I] + (long long)blockIdx.x * chunk;
-    const long long end = min(sup_off[I + 1], beg + chunk);
-    const int nr = coefB ? 8 : 4;
-    float r[8][4];
-    for (int i = 0; i < 8; ++i)
-        for (int t = 0; t < 4; ++t) r[i][t] = 0.f;
-    for (long long g = beg + warp; g < end; g += 8) {
-        const T *srow = S + (long long)sup_node[g] * ld + colg;
-        float ca[4], cb[4];
-        const float4 qa = *reinterpret_cast<const float4 *>(coefA + 4 * g);
-        ca[0] = qa.x; ca[1] = qa.y; ca[2] = qa.z; ca[3] = qa.w;
-        if (coefB) {
-            const float4 qb = *reinterpret_cast<const float4 *>(coefB + 4 * g);
-            cb[0] = qb.x; cb[1] = qb.y; cb[2] = qb.z; cb[3] = qb.w;
-        } else {
-            cb[0] = cb[1] = cb[2] = cb[3] = 0.f;
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int j = lane + 32 * t;
-            if (colg + j < N) {
-                const float sv = to_f(srow[j]);
-#pragma unroll
-                for (int f = 0; f < 4; ++f) {
-                    r[f][t] += ca[f] * sv;
-                    r[4 + f][t] += cb[f] * sv;
-                }
-            }
-        }
-    }
-    for (int i = 0; i < nr; ++i)
-        for (int t = 0; t < 4; ++t) atomicAdd(&acc[i][lane + 32 * t], r[i][t]);
-    __syncthreads();
-    double *o = part + ((long long)(I * nch + blockIdx.x) * 8) * N;
-    for (int i = threadIdx.x; i < nr * 128; i += blockDim.x) {
-        const int rr = i / 128, j = i % 128;
-        if (colg + j < N) o[(long long)rr * N + colg + j] = acc[rr][j];
-    }
-}
-
-// Enriched rows of the recurrence: HY_e = Yraw - Q, Zn_e = a (HY_e - c Z1_e) - b Z0_e + a G_e ck.
-__global__ void k_enr_rec(int n_enr, int N, const double *Yraw, const double *Q, const float *Z1, const float *Z0,
-                          const float *G, const float *ck, float a, float c, float b, float *Zn) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n_enr * N) return;
-    const int j = idx % N;
-    const float hy = (float)(Yraw[idx] - (Q ? Q[idx] : 0.0));
-    const float z0 = Z0 ? Z0[idx] : 0.f;
-    Zn[idx] = a * (hy - c * Z1[idx]) - b * z0 + a * G[idx] * ck[j];
-}
-
 __global__ void k_to_float_strided(int rows, int N, const double *x, float *y, int ldy) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= rows * N) return;
     y[(size_t)(idx / N) * ldy + idx % N] = (float)x[idx];
 }
-__global__ void k_to_float_d(long long n, const double *x, float *y) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) y[i] = (float)x[i];
-}
-__global__ void k_cast_scale(long long n, float s, const float *x, float *y) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) y[i] = s * x[i];
-}
-
 // ---------------------------------------------------------------------------
 // Vectorised row kernels of the tensor-core filter.  FE-row buffers use a row
 // stride ldz = N rounded up to 4 floats (16-byte rows): lanes move float4s.
@@ -835,18 +658,6 @@ __global__ void __launch_bounds__(256) k_rows_residual(long long rows, int N, co
     const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (r >= rows) return;
     for (int j = threadIdx.x & 31; j < N; j += 32) G[r * N + j] = (T)(HV[r * N + j] - MV[r * N + j] * lam[j]);
-}
-__global__ void __launch_bounds__(256) k_rows_vout(long long rows, int N, const float *Y, const double *V,
-                                                   const double *cm, double *Vout) {
-    const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (r >= rows) return;
-    for (int j = threadIdx.x & 31; j < N; j += 32) Vout[r * N + j] = (double)Y[r * N + j] + V[r * N + j] * cm[j];
-}
-__global__ void __launch_bounds__(256) k_rows_minv(long long nn, int N, const double *minv, const float *X, float *Y) {
-    const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (r >= nn) return;
-    const float mi = (float)minv[r];
-    for (int j = threadIdx.x & 31; j < N; j += 32) Y[r * N + j] = mi * X[r * N + j];
 }
 
 // zero the Dirichlet boundary rows of a block (they are not unknowns)
@@ -1767,6 +1578,23 @@ static efe_status lanczos_impl(efe_ctx *ctx, const double *u0, int k, double out
     return EFE_OK;
 }
 
+// ---- helpers used by the SCF translation unit -------------------------------
+efe_status efe_cells_shared(efe_ctx *ctx, const double *K, const double *X, double *Y, int N) {
+    EFE_CUDA(ctx, cudaMemsetAsync(Y, 0, sizeof(double) * ctx->n_nodes * N, ctx->stream));
+    return launch_cells<double>(ctx, K, 0, X, Y, N, N);
+}
+efe_status efe_xprime_fp64(efe_ctx *ctx, const double *X, double *Xp, int N) {
+    const long long nn = ctx->n_nodes;
+    k_xprime<double><<<nblk(nn * N, 256), 256, 0, ctx->stream>>>(ctx->m, nn, X, Xp, N, N, ctx->d_node_ptr,
+                                                                 ctx->d_node_ent, ctx->d_ent_atom, ctx->d_C,
+                                                                 ctx->enrich ? 1 : 0);
+    ctx->launches++;
+    return efe_check_launch(ctx, "k_xprime");
+}
+void efe_sym_eig(int n, const std::vector<double> &A, std::vector<double> &w, std::vector<double> &V) {
+    jacobi_eig(n, A, w, V);
+}
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -1791,6 +1619,7 @@ const char *efe_last_error(const efe_ctx *ctx) { return ctx ? ctx->err.c_str() :
 void efe_destroy(efe_ctx *ctx) {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    efe_scf_free(ctx);
     void *ptrs[] = {ctx->d_B1, ctx->d_D1, ctx->d_wq, ctx->d_Khat, ctx->d_mcc, ctx->d_minv, ctx->d_He, ctx->d_He32,
                     ctx->d_He16, ctx->d_atoms, ctx->d_hproj, ctx->d_sup_off, ctx->d_sup_node, ctx->d_C, ctx->d_B,
                     ctx->d_Kca, ctx->d_Hca, ctx->d_Pc, ctx->d_C32, ctx->d_Hca32, ctx->d_Pc32, ctx->d_node_ptr,

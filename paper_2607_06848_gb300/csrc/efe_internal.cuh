@@ -99,6 +99,7 @@ struct efe_ctx {
 
     efe_stats stats{};
     long long launches = 0;
+    void *scf = nullptr;                      // SCF buffers (efe_scf.cu), freed by efe_destroy
     // cell-product timing: events recorded around each colour sweep, summed
     // after the next synchronisation of the stream
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> cell_events;
@@ -138,4 +139,8 @@ efe_status efe_hx_f32(efe_ctx *ctx, const float *X, float *Y, int N, efe_precisi
 efe_status efe_mx(efe_ctx *ctx, const double *X, double *Y, int N);
 efe_status efe_minvx(efe_ctx *ctx, const double *X, double *Y, int N);
 efe_status efe_tc_prepare(efe_ctx *ctx);
+void efe_scf_free(efe_ctx *ctx);
+efe_status efe_cells_shared(efe_ctx *ctx, const double *K, const double *X, double *Y, int N);
+efe_status efe_xprime_fp64(efe_ctx *ctx, const double *X, double *Xp, int N);
+void efe_sym_eig(int n, const std::vector<double> &A, std::vector<double> &w, std::vector<double> &V);
 efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, float *Ycells, int ldy, int *d_err);

@@ -51,6 +51,25 @@ class efe_stats(ctypes.Structure):
                 ("cell_launches", ctypes.c_longlong), ("passes", ctypes.c_int)]
 
 
+SCF_LOG = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                           ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double)
+
+
+class efe_scf_opts(ctypes.Structure):
+    _fields_ = [("cheb_degree", ctypes.c_int), ("temperature", ctypes.c_double), ("mix_beta", ctypes.c_double),
+                ("mix_history", ctypes.c_int), ("tol_rho", ctypes.c_double), ("tol_e", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("first_tol", ctypes.c_double), ("first_max_pass", ctypes.c_int),
+                ("renormalize", ctypes.c_int), ("kappa", ctypes.c_double), ("poisson_tol", ctypes.c_double),
+                ("precision", ctypes.c_int), ("log", SCF_LOG), ("log_user", ctypes.c_void_p)]
+
+
+class efe_scf_result(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("F", ctypes.c_double), ("mu", ctypes.c_double), ("drho", ctypes.c_double),
+                ("dE", ctypes.c_double), ("iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("poisson_iters", ctypes.c_longlong), ("eig", ctypes.POINTER(ctypes.c_double)),
+                ("rho_q", ctypes.c_void_p)]
+
+
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.c_int
@@ -70,6 +89,14 @@ SIGNATURES = {
     "efe_rayleigh_ritz": [_P, _P, _P, _I, _D, _D],
     "efe_chfsi": [_P, _P, _P, _I, _I, _D, _P, _I, ctypes.c_double, _I, _I, _D, _D, ctypes.POINTER(_I)],
     "efe_filter_host": [_P, _D, _D, _D, _I, _I, _D, _I, _D],
+    "efe_smeared_charge": [_P, _P],
+    "efe_atomic_density": [_P, ctypes.c_double, _P],
+    "efe_density": [_P, _P, _I, _D, _P],
+    "efe_xc": [_P, _P, _P, _P],
+    "efe_poisson": [_P, _P, _P, _P, ctypes.c_double, _I, ctypes.POINTER(_I), _D],
+    "efe_fermi": [_P, _D, _I, ctypes.c_double, ctypes.c_double, _D, _D],
+    "efe_integrate": [_P, _P, _P, _D],
+    "efe_scf": [_P, ctypes.POINTER(efe_scf_opts), _P, _I, _P, _P, ctypes.POINTER(efe_scf_result)],
 }
 
 _lib = None
@@ -218,3 +245,64 @@ class EFE:
                                              lam.ctypes.data_as(_D), V.shape[1], int(m), b, int(prec),
                                              out.ctypes.data_as(_D)))
         return out
+
+    # --- SCF pieces --------------------------------------------------------
+    def efe_smeared_charge(self, b_q):
+        self._check(self.lib.efe_smeared_charge(self.ctx, _ptr(b_q)))
+
+    def efe_atomic_density(self, kappa, rho_q):
+        self._check(self.lib.efe_atomic_density(self.ctx, float(kappa), _ptr(rho_q)))
+
+    def efe_density(self, X, occ, rho_q):
+        occ = np.ascontiguousarray(occ, dtype=np.float64)
+        self._check(self.lib.efe_density(self.ctx, _ptr(X), X.shape[1], occ.ctypes.data_as(_D), _ptr(rho_q)))
+
+    def efe_xc(self, rho_q, vxc_q=None, exc_q=None):
+        self._check(self.lib.efe_xc(self.ctx, _ptr(rho_q), _ptr(vxc_q), _ptr(exc_q)))
+
+    def efe_poisson(self, f_q, phi_nodes, phi_q=None, tol=1e-12, max_it=100000):
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        self._check(self.lib.efe_poisson(self.ctx, _ptr(f_q), _ptr(phi_nodes), _ptr(phi_q), float(tol),
+                                         int(max_it), ctypes.byref(it), ctypes.byref(rr)))
+        return it.value, rr.value
+
+    def efe_fermi(self, eig, n_elec, kT):
+        eig = np.ascontiguousarray(eig, dtype=np.float64)
+        occ = np.empty_like(eig)
+        mu = ctypes.c_double(0.0)
+        self._check(self.lib.efe_fermi(self.ctx, eig.ctypes.data_as(_D), len(eig), float(n_elec), float(kT),
+                                       ctypes.byref(mu), occ.ctypes.data_as(_D)))
+        return mu.value, occ
+
+    def efe_integrate(self, a_q, b_q=None):
+        out = ctypes.c_double(0.0)
+        self._check(self.lib.efe_integrate(self.ctx, _ptr(a_q), _ptr(b_q), ctypes.byref(out)))
+        return out.value
+
+    def efe_scf(self, X, u0, rho0_q=None, rho_out=None, log=None, **opts):
+        o = efe_scf_opts(int(opts.get("cheb_degree", 20)), float(opts.get("temperature", 500.0)),
+                         float(opts.get("mix_beta", 0.5)), int(opts.get("mix_history", 8)),
+                         float(opts.get("tol_rho", 1e-8)), float(opts.get("tol_e", 1e-8)),
+                         int(opts.get("max_iter", 60)), float(opts.get("first_tol", 1e-2)),
+                         int(opts.get("first_max_pass", 20)), int(opts.get("renormalize", 1)),
+                         float(opts.get("kappa", 2.4)), float(opts.get("poisson_tol", 1e-12)),
+                         int(opts.get("precision", EFE_FP64)), SCF_LOG(0), None)
+        hist = []
+        if log is not None:
+            def cb(user, it, E, F, mu, dr, dE, r0):
+                rec = dict(it=it, E=E, F=F, mu=mu, drho=dr, dE=dE, resid0=r0)
+                hist.append(rec)
+                log(rec)
+            o.log = SCF_LOG(cb)
+        N = X.shape[1]
+        eig = (ctypes.c_double * N)()
+        res = efe_scf_result()
+        res.eig = ctypes.cast(eig, ctypes.POINTER(ctypes.c_double))
+        res.rho_q = None if rho_out is None else ctypes.c_void_p(rho_out.data_ptr())
+        st = self.lib.efe_scf(self.ctx, ctypes.byref(o), _ptr(X), N, _ptr(u0), _ptr(rho0_q), ctypes.byref(res))
+        if st not in (0, 4):
+            self._check(st)
+        return dict(E=res.E, F=res.F, mu=res.mu, drho=res.drho, dE=res.dE, iters=res.iters,
+                    converged=bool(res.converged), poisson_iters=res.poisson_iters, eig=np.array(eig[:]),
+                    history=hist)

@@ -1,0 +1,154 @@
+"""Parity of the GPU SCF pieces (through the C ABI) with the FP64 oracle.
+
+Each piece on the 2-atom workload's mesh with the same inputs on both sides:
+PW92 (1e-13 relative), the Fermi level, b_sm and the atomic start density,
+quadrature integrals, the FE Poisson solve (CG to 1e-12 on both sides, so
+agreement to ~1e-10), the density of given vectors and occupations, and the
+full SCF against the oracle's stored result (energy to 1e-8 Ha/atom,
+eigenvalues to 1e-8 Ha), plus the mixed-precision SCF (bf16 tensor-core filter
+passes) against it at the 1e-5 Ha/atom target.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import scf as OS  # noqa: E402
+from oracle.efe import EFESystem  # noqa: E402
+from oracle.fe import Mesh  # noqa: E402
+from paper_2607_06848_gb300 import workloads as W  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_S = {}
+
+
+def _dimer():
+    if "g" in _S:
+        return _S["o"], _S["g"], _S["w"]
+    from paper_2607_06848_gb300 import EFE
+    w = W.dimer()
+    m = Mesh(w["h"], w["ncell"], w["p"])
+    o = EFESystem(m, w["atoms"], enrich=dict(alpha=1.2, r0=5.0 * 0.33 / 1.33, t=0.33),
+                  proj=dict(rc=1.0, rtrunc=6.0, h=w["hproj"]))
+    g = EFE(w["h"], w["ncell"], w["p"], w["atoms"], w["Z"], enrich=dict(alpha=1.2, r_end=5.0, t=0.33),
+            psp=dict(rc=1.0, r_trunc=6.0, h=w["hproj"], rloc=0.8))
+    _S.update(o=o, g=g, w=w)
+    return o, g, w
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def test_xc_matches_oracle():
+    o, g, w = _dimer()
+    rho = np.concatenate([np.logspace(-16, 2, 50000), np.random.default_rng(0).uniform(0, 3, 1000), [0.0, -1e-3]])
+    n = g.dims["n_quad"]
+    r = np.resize(rho, n)
+    rd = torch.tensor(r, device="cuda")
+    v = torch.empty_like(rd)
+    e = torch.empty_like(rd)
+    g.efe_xc(rd, v, e)
+    eo, vo = OS.lda_pw92(r)
+    # ln(1 + 1/q1) is ill-conditioned for large r_s: both sides round the same
+    # formula, their difference is bounded by eps * q1 * |eps_c| (plus a few ulp)
+    rs = np.where(r > 0, (3.0 / (4 * np.pi * np.maximum(r, 1e-300))) ** (1 / 3), 0.0)
+    b1, b2, b3, b4 = OS.PW_B
+    q1 = 2 * OS.PW_A * (b1 * np.sqrt(rs) + b2 * rs + b3 * rs ** 1.5 + b4 * rs ** 2)
+    ex = -0.75 * (3 / np.pi) ** (1 / 3) * np.cbrt(np.maximum(r, 0))
+    ec = np.abs(eo - ex)
+    tol_v = 1e-13 * np.abs(vo) + 8 * 2.2e-16 * (1 + q1) * ec + 1e-300
+    tol_e = 1e-13 * np.abs(eo) + 8 * 2.2e-16 * (1 + q1) * ec + 1e-300
+    assert np.all(np.abs(v.cpu().numpy() - vo) <= tol_v)
+    assert np.all(np.abs(e.cpu().numpy() - eo) <= tol_e)
+    dense = r > 1e-6
+    assert np.allclose(v.cpu().numpy()[dense], vo[dense], rtol=1e-13)
+
+
+def test_fermi_matches_oracle():
+    o, g, w = _dimer()
+    eig = np.sort(np.random.default_rng(1).uniform(-3, 0.5, 40))
+    kT = OS.KB_HA * 500
+    for ne in (8.0, 13.0, 21.5):
+        mu, f = g.efe_fermi(eig, ne, kT)
+        muo, fo = OS.fermi_level(eig, ne, kT)
+        assert abs(2 * f.sum() - ne) < 1e-11
+        assert np.allclose(f, fo, atol=1e-11)
+        assert abs(mu - muo) < 1e-10
+
+
+def test_charges_and_integrals():
+    o, g, w = _dimer()
+    m = o.mesh
+    pts = m.all_quad_points()
+    b = torch.empty(g.dims["n_quad"], dtype=torch.float64, device="cuda")
+    g.efe_smeared_charge(b)
+    bo = OS.gaussian_charge(pts, w["atoms"], w["Z"], 0.8)
+    assert _rel(b.cpu().numpy(), bo) < 1e-13
+    rho = torch.empty_like(b)
+    g.efe_atomic_density(2.4, rho)
+    ro = OS.initial_density(m, w["atoms"], w["Z"])
+    assert _rel(rho.cpu().numpy(), ro) < 1e-12
+    assert abs(g.efe_integrate(rho) - 8.0) < 1e-12
+    assert abs(g.efe_integrate(rho, b) - m.integrate(ro * bo)) < 1e-10 * abs(m.integrate(ro * bo))
+
+
+def test_poisson_matches_oracle():
+    o, g, w = _dimer()
+    m = o.mesh
+    pts = m.all_quad_points()
+    f = OS.initial_density(m, w["atoms"], w["Z"]) + OS.gaussian_charge(pts, w["atoms"], w["Z"], 0.8)
+    fd = torch.tensor(f, device="cuda")
+    phi = torch.empty(g.dims["n_nodes"], dtype=torch.float64, device="cuda")
+    phq = torch.empty_like(fd)
+    its, rr = g.efe_poisson(fd, phi, phq, tol=1e-12)
+    po, ito = OS.poisson_solve(m, f, tol=1e-12)
+    assert rr < 1e-12 and its > 10
+    assert _rel(phi.cpu().numpy(), po) < 1e-10
+    assert _rel(phq.cpu().numpy(), m.interpolate(po[:, None])[:, 0]) < 1e-10
+
+
+def test_density_matches_oracle():
+    o, g, w = _dimer()
+    X = W.random_block(o.nn + o.n_enr, 8, 5)
+    X[:o.nn] *= o.mask[:, None]
+    occ = np.linspace(1.0, 0.0, 8)
+    rho = torch.empty(g.dims["n_quad"], dtype=torch.float64, device="cuda")
+    g.efe_density(torch.tensor(X, device="cuda"), occ, rho)
+    ro = OS.density(o, X, occ)
+    assert _rel(rho.cpu().numpy(), ro) < 1e-12
+
+
+def _run_scf(prec):
+    o, g, w = _dimer()
+    rows = o.nn + o.n_enr
+    X0 = W.random_block(rows, w["nstates"], 1)
+    u0 = W.random_block(rows, 1, 2)
+    X0[:o.nn] *= o.mask[:, None]
+    u0[:o.nn] *= o.mask[:, None]
+    X = torch.tensor(X0, device="cuda")
+    return g.efe_scf(X, torch.tensor(u0, device="cuda"), cheb_degree=w["cheb_degree"], precision=prec,
+                     log=lambda h: None)
+
+
+def test_scf_fp64_matches_oracle():
+    ref = json.load(open(os.path.join(HERE, "golden", "dimer_scf.json")))
+    out = _run_scf(0)
+    assert out["converged"]
+    na = 2
+    assert abs(out["E"] - ref["E"]) / na < 1e-8, (out["E"], ref["E"])
+    assert abs(out["F"] - ref["F"]) / na < 1e-8
+    nocc = 4
+    assert np.max(np.abs(out["eig"][:nocc] - np.array(ref["eig"][:nocc]))) < 1e-8
+    assert abs(out["iters"] - ref["iters"]) <= 2
+
+
+def test_scf_mixed_bf16_within_target():
+    ref = json.load(open(os.path.join(HERE, "golden", "dimer_scf.json")))
+    out = _run_scf(2)
+    assert out["converged"]
+    assert abs(out["E"] - ref["E"]) / 2 < 1e-5, (out["E"], ref["E"])
