@@ -236,6 +236,21 @@ efe_status efe_fermi(efe_ctx *ctx, const double *eig, int N, double n_elec, doub
 /* *out = int a b (quadrature), b may be NULL (int a).  a_q, b_q: device. */
 efe_status efe_integrate(efe_ctx *ctx, const double *a_q, const double *b_q, double *out);
 
+/* *out = int a b, like efe_integrate, without allocating any device memory:
+ * for callers that cannot call cudaMalloc while they run (code whose device
+ * memory belongs to another allocator, or a host that must not grow device
+ * memory after start-up).  The paper has no counterpart; this is a library
+ * service.  The per-cell partial sums go to a fixed array in the library's
+ * device memory, sized for at most 65,536 cells (512 KB, held by every GPU
+ * that loads the library until the process exits); larger meshes get
+ * EFE_ERR_ARG.  The first call on a device looks the array up for that
+ * device, so make that first call before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU (several streams, several
+ * contexts on one device) race; serialise them.  Nothing in the array needs
+ * to start at zero: each call overwrites what it reads.  a_q, b_q: device
+ * n_quad (b_q may be NULL); out: host. */
+efe_status efe_integrate_noalloc(efe_ctx *ctx, const double *a_q, const double *b_q, double *out);
+
 typedef void (*efe_scf_log_fn)(void *user, int iter, double E, double F, double mu,
                                double drho, double dE, double resid0);
 

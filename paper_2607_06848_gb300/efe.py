@@ -96,6 +96,7 @@ SIGNATURES = {
     "efe_poisson": [_P, _P, _P, _P, ctypes.c_double, _I, ctypes.POINTER(_I), _D],
     "efe_fermi": [_P, _D, _I, ctypes.c_double, ctypes.c_double, _D, _D],
     "efe_integrate": [_P, _P, _P, _D],
+    "efe_integrate_noalloc": [_P, _P, _P, _D],
     "efe_scf": [_P, ctypes.POINTER(efe_scf_opts), _P, _I, _P, _P, ctypes.POINTER(efe_scf_result)],
 }
 
@@ -278,6 +279,11 @@ class EFE:
     def efe_integrate(self, a_q, b_q=None):
         out = ctypes.c_double(0.0)
         self._check(self.lib.efe_integrate(self.ctx, _ptr(a_q), _ptr(b_q), ctypes.byref(out)))
+        return out.value
+
+    def efe_integrate_noalloc(self, a_q, b_q=None):
+        out = ctypes.c_double(0.0)
+        self._check(self.lib.efe_integrate_noalloc(self.ctx, _ptr(a_q), _ptr(b_q), ctypes.byref(out)))
         return out.value
 
     def efe_scf(self, X, u0, rho0_q=None, rho_out=None, log=None, **opts):
