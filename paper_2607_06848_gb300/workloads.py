@@ -104,3 +104,38 @@ def cluster8(seed=0):
     154 vectors): 8 atoms in a 20-bohr cube, 12^3 cells -- inputs above the L2
     size but only a few GB on the device (profiling captures)."""
     return cluster(8, 20.0, 12, 6, 154, 30, seed=seed, name="cluster8")
+
+
+# learned warm start: parameter vector layout of the 32 -> 128 -> 128 -> 128 -> 8 network
+MLP_LAYERS = ((128, 32), (128, 128), (128, 128), (8, 128))
+MLP_N_TRAIN = sum(m * n + m for m, n in MLP_LAYERS)          # 38,280
+MLP_N_PARAMS = MLP_N_TRAIN + 2 * 32 + 2 * 8                 # + x_mean, x_std, y_mean, y_std
+
+
+def mlp_init(seed):
+    """Seeded initial parameters: weights and biases U(-1/sqrt(fan_in), 1/sqrt(fan_in)),
+    layer by layer ([out][in] row-major weights, then biases); normalisation
+    x_mean = y_mean = 0, x_std = y_std = 1."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for m, n in MLP_LAYERS:
+        s = 1.0 / np.sqrt(n)
+        parts.append(rng.uniform(-s, s, size=m * n))
+        parts.append(rng.uniform(-s, s, size=m))
+    parts += [np.zeros(32), np.ones(32), np.zeros(8), np.ones(8)]
+    return np.concatenate(parts)
+
+
+def species_strengths(n_atoms, seed=7):
+    """One element: the same seeded s and p projector strengths on every atom, (n_atoms, 2)."""
+    return np.tile(projector_strengths(1, seed), (n_atoms, 1))
+
+
+def ws_cluster(n_atoms, seed, h=2.0, p=4, pad=7.0):
+    """Clusters of the learned warm start: small_cluster's geometry and mesh (2-bohr cells
+    of degree 4, box = extent + 14 bohr) with one element's projector strengths on every
+    atom.  Training clusters use seeds 1000-1299, held-out ones 2000-2019."""
+    w = small_cluster(n_atoms, seed, h=h, p=p, pad=pad)
+    w["hproj"] = species_strengths(n_atoms)
+    w["name"] = f"ws{n_atoms}_{seed}"
+    return w
