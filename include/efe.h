@@ -258,7 +258,7 @@ typedef struct {
     int cheb_degree;      /* filter degree m */
     double temperature;   /* smearing temperature, K */
     double mix_beta;      /* Anderson mixing parameter */
-    int mix_history;      /* Anderson history length */
+    int mix_history;      /* Anderson history length, 0..8 */
     double tol_rho;       /* ||rho_out - rho_in||_L2 / N_e */
     double tol_e;         /* |E_k - E_{k-1}| per atom, Ha */
     int max_iter;
@@ -271,6 +271,13 @@ typedef struct {
     int precision;        /* efe_precision of the filter passes */
     efe_scf_log_fn log;   /* optional per-iteration callback */
     void *log_user;
+    double bf16_resid;    /* with precision EFE_BF16: the passes of the first iteration
+                             run in bf16; a later pass runs in bf16 while the largest
+                             residual of the occupied states after the last
+                             Rayleigh-Ritz exceeds this, in FP32 below it (0: every
+                             pass in bf16) */
+    int profile;          /* nonzero: synchronise at phase ends and report the
+                             phase times in efe_scf_result.ms_phase */
 } efe_scf_opts;
 
 typedef struct {
@@ -282,6 +289,10 @@ typedef struct {
     long long poisson_iters;
     double *eig;          /* host N (optional, caller-owned) */
     double *rho_q;        /* device n_quad (optional, caller-owned): final rho_out */
+    double ms_phase[5];   /* with opts.profile: wall time of the potential (Poisson, XC,
+                             operator assembly), the eigensolver (Lanczos, filter,
+                             Rayleigh-Ritz), the density (Fermi level, rho_out), the
+                             energy (Poisson of rho_out, integrals) and the mixing */
 } efe_scf_result;
 
 /* The SCF loop: v_eff = v_xc[rho_in] + phi[rho_in + b_sm]; operator assembly;
@@ -294,6 +305,105 @@ typedef struct {
  * EFE_ERR_NO_CONVERGE after max_iter (results still written). */
 efe_status efe_scf(efe_ctx *ctx, const efe_scf_opts *opts, double *X, int N, const double *u0,
                    const double *rho0_q, efe_scf_result *res);
+
+
+/* ------------------------------------------------------------------------
+ * Learned density warm start.  The paper starts the SCF from a superposition
+ * of atomic densities (Sec. II.A, Sec. IV); the learned correction on top of
+ * it is an addition of this library, with the superposition as its fallback
+ * and the converged SCF as the measure of its worth.
+ *
+ *   descriptors  D_Ik = sum_{J != I, r_IJ < 10} Z_J exp(-(r_IJ - mu_k)^2 / 0.32)
+ *                       * (1 + cos(pi r_IJ / 10)) / 2,   mu_k = 2 + 8 k / 31,
+ *                k = 0..31, lengths in bohr (computed in double, stored float)
+ *   network      x = (D - x_mean) / x_std; three hidden layers of 128 SiLU units
+ *                (silu(z) = z / (1 + e^-z)); linear output y (8);
+ *                coefficients c = y_mean + y_std * y.  Float arithmetic.
+ *   correction   drho(x) = sum_I sum_k c_Ik phi_k(|x - R_I|), zero beyond 8 bohr;
+ *                phi = L^-1 g, the per-atom orthonormal combinations of the
+ *                normalised Gaussians g_j(r) = (kappa_j/pi)^{3/2} exp(-kappa_j r^2),
+ *                kappa_j = 0.5 * 16^{j/7} (j = 0..7), S = L L^T, S = int g g^T.
+ *   warm start   rho_0 = max(rho_sup + drho, 0) scaled to N_e.
+ *   training     loss = mean over samples and outputs of (y - (c* - y_mean)/y_std)^2,
+ *                c* the least-squares coefficients of rho_scf - rho_sup
+ *                (efe_fit_correction); full-batch Adam.
+ *
+ * Parameter vector theta: EFE_MLP_N_PARAMS floats, device, caller-owned:
+ *   W1[128][32] b1[128] W2[128][128] b2[128] W3[128][128] b3[128] W4[8][128] b4[8]
+ *   (EFE_MLP_N_TRAIN trained values, weights row-major [out][in]), then
+ *   x_mean[32] x_std[32] y_mean[8] y_std[8] (set by efe_mlp_normalise).
+ * Samples are rows: D is n x 32, targets T and coefficients C are n x 8 (floats).
+ * ------------------------------------------------------------------------ */
+#define EFE_MLP_N_DESC 32
+#define EFE_MLP_N_OUT 8
+#define EFE_MLP_N_TRAIN 38280
+#define EFE_MLP_N_PARAMS 38360
+
+typedef struct efe_mlp efe_mlp; /* opaque: training workspace, owned by the library */
+
+typedef struct {
+    float lr, beta1, beta2, eps;   /* Adam (Kingma & Ba 2015) step size and decay rates */
+} efe_adam;
+
+/* Workspace for training on up to max_samples samples at a time, working on
+ * `stream` (a cudaStream_t; NULL = the default stream).  Training steps are
+ * replayed from a CUDA graph captured on a private stream that is ordered
+ * after, and before, the given stream. */
+efe_status efe_mlp_create(void *stream, int max_samples, efe_mlp **out);
+void efe_mlp_destroy(efe_mlp *mlp);
+/* Last failure of a call on this workspace (NULL: of efe_mlp_create). */
+const char *efe_mlp_last_error(const efe_mlp *mlp);
+
+/* Descriptors of n atoms.  xyz: device n x 3 (bohr); zval: device n; D: device
+ * n x 32 (out). */
+efe_status efe_descriptors(efe_mlp *mlp, const double *xyz, const double *zval, int n, float *D);
+
+/* C = network(D) in physical units.  theta: device; D: device n x 32; C: device
+ * n x 8 (out).  Any n >= 0. */
+efe_status efe_mlp_forward(efe_mlp *mlp, const float *theta, const float *D, int n, float *C);
+
+/* Sets x_mean, x_std (floor 1e-2), y_mean, y_std (floor 1e-8) of theta to the
+ * per-column mean and standard deviation of D and T (n samples, device). */
+efe_status efe_mlp_normalise(efe_mlp *mlp, float *theta, const float *D, const float *T, int n);
+
+/* Loss of the normalised outputs against targets T (device n x 8) and its
+ * gradient (device EFE_MLP_N_TRAIN, out) by back-propagation; loss: host.
+ * 1 <= n <= max_samples.  Per-CTA partial gradients are summed in a fixed
+ * order, so repeated calls give identical bits. */
+efe_status efe_mlp_loss_grad(efe_mlp *mlp, const float *theta, const float *D, const float *T, int n,
+                             float *grad, double *loss);
+
+/* One Adam update of the trained part of theta with gradient grad (device),
+ * step number t >= 1; m, v: device EFE_MLP_N_TRAIN moments (start at zero). */
+efe_status efe_mlp_adam(efe_mlp *mlp, float *theta, float *m, float *v, const float *grad, int t,
+                        const efe_adam *hp);
+
+/* `steps` full-batch Adam steps numbered t0+1 .. t0+steps on (D, T): each step
+ * is the loss/gradient pass and the update, replayed from one CUDA graph.
+ * loss_hist: device `steps` floats (out), the loss before each update. */
+efe_status efe_mlp_train(efe_mlp *mlp, float *theta, float *m, float *v, const float *D, const float *T,
+                         int n, int steps, int t0, const efe_adam *hp, float *loss_hist);
+
+/* drho at the quadrature points of ctx's mesh from coefficients c (device
+ * natoms x 8, atom order of efe_setup).  drho_q: device n_quad (out). */
+efe_status efe_density_correction(efe_ctx *ctx, const double *c, double *drho_q);
+
+/* Least-squares coefficients of the density difference drho = rho_q - base_q
+ * (device n_quad each; base_q may be NULL for drho = rho_q):
+ * (Phi^T W Phi + ridge I) c = Phi^T W drho, W the quadrature weights, Phi the
+ * phi_Ik at the quadrature points (Gram matrix by the same quadrature; FP64,
+ * Cholesky).  c: device natoms x 8 (out).  EFE_ERR_NOT_SPD if the system is
+ * not positive definite (ridge = 0 with dependent functions). */
+efe_status efe_fit_correction(efe_ctx *ctx, const double *rho_q, const double *base_q, double ridge, double *c);
+
+/* Start density: the superposition (as efe_atomic_density with kappa) plus the
+ * network's correction, clipped at zero and scaled to N_e.  theta: device
+ * parameters, or NULL for the superposition alone.  The superposition is also
+ * returned when the corrected density has no positive charge or is not finite.
+ * rho_q: device n_quad (out); fallback: host (may be NULL), 1 when rho_q is the
+ * superposition. */
+efe_status efe_warm_start(efe_ctx *ctx, efe_mlp *mlp, const float *theta, double kappa, double *rho_q,
+                          int *fallback);
 
 #ifdef __cplusplus
 }

@@ -7,6 +7,7 @@
 #include "efe_funcs.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -257,10 +258,6 @@ __global__ void k_axpy_n(long long n, double a, const double *x, double b, const
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) out[i] = a * x[i] + b * y[i];
 }
-__global__ void k_mul_n(long long n, const double *a, const double *b, double *out) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) out[i] = a[i] * b[i];
-}
 __global__ void k_add3(long long n, const double *a, const double *b, double *out) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) out[i] = a[i] + b[i];
@@ -283,28 +280,253 @@ __global__ void k_dotp(long long n, const double *a, const double *b, double *pa
         part[blockIdx.x] = t;
     }
 }
-// weighted dot over quadrature fields (Anderson inner product)
-__global__ void k_wdot(MeshDev m, Tables1D T, const double *a, const double *b, double *part) {
-    __shared__ double red[32];
-    const long long n = (long long)m.nx * m.ny * m.nz * m.nq3;
-    const double J = 0.125 * m.h * m.h * m.h;
-    double s = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int q = (int)(i % m.nq3);
-        const int qx = q % m.nq, qy = (q / m.nq) % m.nq, qz = q / (m.nq * m.nq);
-        s += T.wq[qx] * T.wq[qy] * T.wq[qz] * J * a[i] * b[i];
+constexpr int NRED = 512;
+
+// --- the Poisson operator by sum factorisation -------------------------------
+// On a cube cell with Gauss quadrature the stiffness integrand separates, so
+// (1/4 pi) K_e = c (S x M x M + M x S x M + M x M x S) with the 1-D matrices
+// S_ab = sum_q w_q N'_a N'_b, M_ab = sum_q w_q N_a N_b on [-1, 1] and
+// c = (h/2) / (4 pi).  Applied as w1 = M_z u, w2 = S_z u; t1 = M_y w1,
+// t2 = S_y w1 + M_y w2; y = S_x t1 + M_x t2: 7 (p+1)^4 FMAs per cell instead
+// of (p+1)^6 for the dense matrix.  One CTA per cell of one colour.
+struct Lap1D {
+    double S[(EFE_MAXP + 1) * (EFE_MAXP + 1)], M[(EFE_MAXP + 1) * (EFE_MAXP + 1)];
+    double c;
+};
+
+constexpr int kLapMax = (EFE_MAXP + 1) * (EFE_MAXP + 1) * (EFE_MAXP + 1);
+__global__ void __launch_bounds__(256) k_lap_colour(MeshDev m, Lap1D L, int colour, const double *X, double *Y) {
+    __shared__ double u[kLapMax], w1[kLapMax], w2[kLapMax], w3[kLapMax];
+    const int np1 = m.np1, ne = m.ne;
+    const int ox = colour & 1, oy = (colour >> 1) & 1, oz = (colour >> 2) & 1;
+    const int hx = (m.nx - ox + 1) / 2, hy = (m.ny - oy + 1) / 2;
+    const int b = blockIdx.x;
+    const int cx = 2 * (b % hx) + ox, cy = 2 * ((b / hx) % hy) + oy, cz = 2 * (b / (hx * hy)) + oz;
+    for (int l = threadIdx.x; l < ne; l += blockDim.x) {
+        const int ax = l % np1, ay = (l / np1) % np1, az = l / (np1 * np1);
+        u[l] = X[((long long)(cz * m.p + az) * m.Gy + (cy * m.p + ay)) * m.Gx + (cx * m.p + ax)];
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        part[blockIdx.x] = t;
+    for (int l = threadIdx.x; l < ne; l += blockDim.x) {         // along z: w1 = M u, w2 = S u
+        const int axy = l % (np1 * np1), az = l / (np1 * np1);
+        double a = 0.0, s = 0.0;
+        for (int k = 0; k < np1; ++k) {
+            const double v = u[k * np1 * np1 + axy];
+            a += L.M[az * np1 + k] * v;
+            s += L.S[az * np1 + k] * v;
+        }
+        w1[l] = a;
+        w2[l] = s;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < ne; l += blockDim.x) {         // along y: u = M w1, w3 = S w1 + M w2
+        const int ax = l % np1, ay = (l / np1) % np1, az = l / (np1 * np1);
+        double a = 0.0, s = 0.0;
+        for (int k = 0; k < np1; ++k) {
+            const int src = (az * np1 + k) * np1 + ax;
+            a += L.M[ay * np1 + k] * w1[src];
+            s += L.S[ay * np1 + k] * w1[src] + L.M[ay * np1 + k] * w2[src];
+        }
+        u[l] = a;
+        w3[l] = s;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < ne; l += blockDim.x) {         // along x: S u + M w3, scatter
+        const int ax = l % np1, ay = (l / np1) % np1, az = l / (np1 * np1);
+        const int ix = cx * m.p + ax, iy = cy * m.p + ay, iz = cz * m.p + az;
+        if (!interior_node(m, ix, iy, iz)) continue;
+        double s = 0.0;
+        for (int k = 0; k < np1; ++k) {
+            const int src = (az * np1 + ay) * np1 + k;
+            s += L.S[ax * np1 + k] * u[src] + L.M[ax * np1 + k] * w3[src];
+        }
+        Y[((long long)iz * m.Gy + iy) * m.Gx + ix] += L.c * s;
     }
 }
 
-constexpr int NRED = 512;
+// --- conjugate gradients with the scalars kept on the device ------------------
+// sc[]: rz, alpha, beta, threshold tol*||F||, done flag, iterations, ||r||
+enum { CG_RZ = 0, CG_ALPHA, CG_BETA, CG_THR, CG_DONE, CG_IT, CG_RR, CG_NSC };
+
+// fixed-order sum of NRED partials by one warp (lane l takes l, l+32, ...)
+__device__ __forceinline__ double warp_sum_parts(const double *part) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < NRED; i += 32) s += part[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// alpha = rz / (p . Ap), zero once converged
+__global__ void k_cg_alpha(const double *part, double *sc) {
+    const double pAp = warp_sum_parts(part);
+    if (threadIdx.x == 0) sc[CG_ALPHA] = sc[CG_DONE] != 0.0 ? 0.0 : sc[CG_RZ] / pAp;
+}
+
+// phi += alpha p; r -= alpha Ap; z = D^-1 r; partials of r.r (part[b]) and r.z (part[NRED + b])
+__global__ void k_cg_update(long long n, const double *sc, double *phi, double *r, const double *p,
+                            const double *Ap, const double *dinv, double *z, double *part) {
+    __shared__ double red[2][32];
+    const double a = sc[CG_ALPHA];
+    double s1 = 0.0, s2 = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double ri = r[i];
+        if (a != 0.0) {     // alpha = 0 (the start, or after convergence) leaves phi and r as they are
+            phi[i] += a * p[i];
+            ri -= a * Ap[i];
+            r[i] = ri;
+        }
+        const double zi = dinv[i] * ri;
+        z[i] = zi;
+        s1 += ri * ri;
+        s2 += ri * zi;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = s1;
+        red[1][threadIdx.x >> 5] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t1 += red[0][w];
+            t2 += red[1][w];
+        }
+        part[blockIdx.x] = t1;
+        part[NRED + blockIdx.x] = t2;
+    }
+}
+
+// convergence test on ||r||, then beta = rz_new / rz (first = true: the start,
+// which only records rz and the test)
+__global__ void k_cg_beta(const double *part, double *sc, int first) {
+    const double r2 = warp_sum_parts(part);
+    const double rzn = warp_sum_parts(part + NRED);
+    if (threadIdx.x != 0) return;
+    if (first) {
+        sc[CG_RR] = sqrt(r2);
+        sc[CG_RZ] = rzn;
+        sc[CG_DONE] = sqrt(r2) < sc[CG_THR] ? 1.0 : 0.0;
+        sc[CG_IT] = 0.0;
+        return;
+    }
+    if (sc[CG_DONE] != 0.0) {
+        sc[CG_BETA] = 0.0;
+        return;
+    }
+    sc[CG_IT] += 1.0;
+    sc[CG_RR] = sqrt(r2);
+    if (sqrt(r2) < sc[CG_THR]) {
+        sc[CG_DONE] = 1.0;
+        sc[CG_BETA] = 0.0;
+    } else {
+        sc[CG_BETA] = rzn / sc[CG_RZ];
+        sc[CG_RZ] = rzn;
+    }
+}
+
+// p = z + beta p
+__global__ void k_cg_p(long long n, const double *sc, const double *z, double *p) {
+    const double b = sc[CG_BETA];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = z[i] + b * p[i];
+}
+
+__global__ void k_set_scalar(double *sc, int k, double v) { sc[k] = v; }
+
+// --- Anderson mixing: history rings of rho_in (x) and residuals R = rho_out - rho_in
+constexpr int kMixMax = 8;                                           // dR vectors at most
+constexpr int kMixNV = kMixMax * (kMixMax + 1) / 2 + kMixMax;       // A (upper) and b
+struct MixRing {
+    const double *x[kMixMax + 1];    // oldest first
+    const double *R[kMixMax + 1];
+};
+__host__ __device__ constexpr int mix_idx(int i, int j) { return i * kMixMax - i * (i - 1) / 2 + (j - i); }
+
+// partials of A_ij = <dR_i, dR_j>_w (i <= j < mm) and b_i = <dR_i, R_mm>_w,
+// dR_j = R_{j+1} - R_j, w the quadrature weights; part[block][kMixNV]
+__global__ void __launch_bounds__(256) k_mix_gram(MeshDev m, Tables1D T, MixRing ring, int mm, double *part) {
+    __shared__ double red[8][kMixNV];
+    const long long n = (long long)m.nx * m.ny * m.nz * m.nq3;
+    const double J = 0.125 * m.h * m.h * m.h;
+    const double *Rk = ring.R[0];
+#pragma unroll
+    for (int j = 1; j <= kMixMax; ++j)
+        if (j == mm) Rk = ring.R[j];
+    double acc[kMixNV];
+#pragma unroll
+    for (int k = 0; k < kMixNV; ++k) acc[k] = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(i % m.nq3);
+        const int qx = q % m.nq, qy = (q / m.nq) % m.nq, qz = q / (m.nq * m.nq);
+        const double w = T.wq[qx] * T.wq[qy] * T.wq[qz] * J;
+        double d[kMixMax];
+        double prev = ring.R[0][i];
+#pragma unroll
+        for (int j = 0; j < kMixMax; ++j) {
+            double nxt = 0.0;
+            if (j < mm) nxt = ring.R[j + 1][i];
+            d[j] = (j < mm) ? nxt - prev : 0.0;
+            prev = nxt;
+        }
+        const double rk = Rk[i];
+#pragma unroll
+        for (int a = 0; a < kMixMax; ++a) {
+            const double wa = w * d[a];
+#pragma unroll
+            for (int b = a; b < kMixMax; ++b) acc[mix_idx(a, b)] += wa * d[b];
+            acc[kMixNV - kMixMax + a] += wa * rk;
+        }
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kMixNV; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[wp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kMixNV) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+        part[(size_t)blockIdx.x * kMixNV + threadIdx.x] = t;
+    }
+}
+
+// out[k] = sum over blocks of part[block][k] (fixed order)
+__global__ void k_mix_sum(int nblk, const double *part, double *out) {
+    const int k = threadIdx.x;
+    if (k >= kMixNV) return;
+    double t = 0.0;
+    for (int b = 0; b < nblk; ++b) t += part[(size_t)b * kMixNV + k];
+    out[k] = t;
+}
+
+struct MixCoef {
+    double g[kMixMax];
+};
+
+// rho = x_mm + beta R_mm - sum_j gamma_j ((x_{j+1} - x_j) + beta (R_{j+1} - R_j))
+__global__ void k_mix_update(long long n, MixRing ring, int mm, MixCoef gc, double beta, double *rho) {
+    const double *xk = ring.x[0], *Rk = ring.R[0];
+#pragma unroll
+    for (int j = 1; j <= kMixMax; ++j)
+        if (j == mm) {
+            xk = ring.x[j];
+            Rk = ring.R[j];
+        }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double v = xk[i] + beta * Rk[i];
+#pragma unroll
+        for (int j = 0; j < kMixMax; ++j)
+            if (j < mm)
+                v -= gc.g[j] * ((ring.x[j + 1][i] - ring.x[j][i]) + beta * (ring.R[j + 1][i] - ring.R[j][i]));
+        rho[i] = v;
+    }
+}
 
 }  // namespace
 
@@ -320,6 +542,10 @@ struct ScfState {
     double *d_dinv = nullptr;       // Jacobi preconditioner of the Poisson matrix
     double *d_part = nullptr;       // reduction partials
     double *d_Z = nullptr;          // valence charges
+    // conjugate-gradient work vectors (n_nodes), scalars and partials
+    double *cg_F = nullptr, *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_Ap = nullptr;
+    double *cg_sc = nullptr, *cg_part = nullptr;
+    Lap1D lap{};                    // 1-D factors of the Poisson operator
 };
 
 static ScfState &scf_state(efe_ctx *ctx) {
@@ -331,7 +557,8 @@ void efe_scf_free(efe_ctx *ctx) {
     if (!ctx->scf) return;
     ScfState *S = static_cast<ScfState *>(ctx->scf);
     void *ptrs[] = {S->d_b, S->d_avals, S->d_cell_pair_ptr, S->d_cell_pair_idx, S->d_pair_atom, S->d_Kpois,
-                    S->d_dinv, S->d_part, S->d_Z};
+                    S->d_dinv, S->d_part, S->d_Z, S->cg_F, S->cg_r, S->cg_z, S->cg_p, S->cg_Ap, S->cg_sc,
+                    S->cg_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete S;
@@ -360,6 +587,21 @@ static efe_status scf_prepare(efe_ctx *ctx) {
     if (ctx->natoms)
         EFE_CUDA(ctx, cudaMemcpy(S.d_Z, ctx->zval.data(), sizeof(double) * ctx->natoms, cudaMemcpyHostToDevice));
     k_gaussians<<<nb(nq, 256), 256, 0, ctx->stream>>>(m, T, ctx->natoms, ctx->d_atoms, S.d_Z, ctx->rloc, 0, S.d_b);
+    // 1-D factors of the Poisson operator (Gauss quadrature on [-1, 1])
+    {
+        const int np1 = m.np1, nq = m.nq;
+        for (int a = 0; a < np1; ++a)
+            for (int b = 0; b < np1; ++b) {
+                double sv = 0.0, mv = 0.0;
+                for (int q = 0; q < nq; ++q) {
+                    sv += ctx->wq[q] * ctx->D1[q * np1 + a] * ctx->D1[q * np1 + b];
+                    mv += ctx->wq[q] * ctx->B1[q * np1 + a] * ctx->B1[q * np1 + b];
+                }
+                S.lap.S[a * np1 + b] = sv;
+                S.lap.M[a * np1 + b] = mv;
+            }
+        S.lap.c = 0.5 * m.h / (4.0 * kPi);
+    }
     // Poisson cell matrix (1/4pi) K_e = (1/2pi) (1/2 K_e) and its assembled diagonal
     const int ne = m.ne;
     std::vector<double> Kh((size_t)ne * ne);
@@ -441,23 +683,37 @@ static efe_status cell_values(efe_ctx *ctx, const double *U, const double *Ue, i
     return efe_check_launch(ctx, "k_cell_values");
 }
 
-// FE solution of -1/(4 pi) Lap phi = f, phi = 0 on the box (Jacobi CG)
+// Y = (1/4 pi) K X for one nodal vector (Dirichlet rows left at zero)
+static efe_status lap_apply(efe_ctx *ctx, const double *X, double *Y) {
+    ScfState &S = scf_state(ctx);
+    const MeshDev &m = ctx->m;
+    EFE_CUDA(ctx, cudaMemsetAsync(Y, 0, sizeof(double) * ctx->n_nodes, ctx->stream));
+    for (int colour = 0; colour < 8; ++colour) {
+        const int ox = colour & 1, oy = (colour >> 1) & 1, oz = (colour >> 2) & 1;
+        const int ncol = ((m.nx - ox + 1) / 2) * ((m.ny - oy + 1) / 2) * ((m.nz - oz + 1) / 2);
+        if (ncol) k_lap_colour<<<ncol, 256, 0, ctx->stream>>>(m, S.lap, colour, X, Y);
+    }
+    return efe_check_launch(ctx, "k_lap_colour");
+}
+
+// FE solution of -1/(4 pi) Lap phi = f, phi = 0 on the box: Jacobi-preconditioned
+// CG to ||r|| < tol ||F||.  warm: start from the phi passed in (else from 0).
+// The scalars stay on the device; the host reads the convergence flag once
+// every kCgBlock iterations, and iterations after convergence change nothing.
+constexpr int kCgBlock = 16;
 static efe_status poisson(efe_ctx *ctx, const double *fq, double *phi, double *phi_q, double tol, int max_it,
-                          int *iters, double *rel_res) {
+                          int *iters, double *rel_res, bool warm = false) {
     ScfState &S = scf_state(ctx);
     const MeshDev &m = ctx->m;
     const long long n = ctx->n_nodes;
     Tables1D T = make_tables(ctx);
-    double *F = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
-    std::vector<void *> own;
-    for (double **pp : {&F, &r, &z, &p, &Ap}) {
-        EFE_TRY(efe_alloc(ctx, (void **)pp, sizeof(double) * n));
-        own.push_back(*pp);
+    if (!S.cg_r) {
+        for (double **pp : {&S.cg_F, &S.cg_r, &S.cg_z, &S.cg_p, &S.cg_Ap})
+            EFE_TRY(efe_alloc(ctx, (void **)pp, sizeof(double) * n));
+        EFE_TRY(efe_alloc(ctx, (void **)&S.cg_sc, sizeof(double) * CG_NSC));
+        EFE_TRY(efe_alloc(ctx, (void **)&S.cg_part, sizeof(double) * 2 * NRED));
     }
-    auto cleanup = [&]() {
-        cudaStreamSynchronize(ctx->stream);
-        for (void *q : own) cudaFree(q);
-    };
+    double *F = S.cg_F, *r = S.cg_r, *z = S.cg_z, *p = S.cg_p, *Ap = S.cg_Ap, *sc = S.cg_sc;
     EFE_CUDA(ctx, cudaMemsetAsync(F, 0, sizeof(double) * n, ctx->stream));
     const size_t shm = sizeof(double) * (m.nq3 + m.nq * m.nq * m.np1 + m.nq * m.np1 * m.np1);
     EFE_CUDA(ctx, cudaFuncSetAttribute(k_project_colour, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
@@ -470,36 +726,53 @@ static efe_status poisson(efe_ctx *ctx, const double *fq, double *phi, double *p
     double bnorm2;
     EFE_TRY(dot(ctx, n, F, F, bnorm2));
     const double bnorm = std::sqrt(bnorm2);
-    EFE_CUDA(ctx, cudaMemsetAsync(phi, 0, sizeof(double) * n, ctx->stream));
     int it = 0;
-    double rr = bnorm;
-    if (bnorm > 0.0) {
-        EFE_CUDA(ctx, cudaMemcpyAsync(r, F, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-        k_mul_n<<<nb(n, 256), 256, 0, ctx->stream>>>(n, S.d_dinv, r, z);
-        EFE_CUDA(ctx, cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-        double rz;
-        EFE_TRY(dot(ctx, n, r, z, rz));
-        while (it < max_it) {
-            EFE_TRY(efe_cells_shared(ctx, S.d_Kpois, p, Ap, 1));
-            double pAp;
-            EFE_TRY(dot(ctx, n, p, Ap, pAp));
-            const double alpha = rz / pAp;
-            k_axpy_n<<<nb(n, 256), 256, 0, ctx->stream>>>(n, 1.0, phi, alpha, p, phi);
-            k_axpy_n<<<nb(n, 256), 256, 0, ctx->stream>>>(n, 1.0, r, -alpha, Ap, r);
-            ++it;
-            double r2;
-            EFE_TRY(dot(ctx, n, r, r, r2));
-            rr = std::sqrt(r2);
-            if (rr < tol * bnorm) break;
-            k_mul_n<<<nb(n, 256), 256, 0, ctx->stream>>>(n, S.d_dinv, r, z);
-            double rz_new;
-            EFE_TRY(dot(ctx, n, r, z, rz_new));
-            k_axpy_n<<<nb(n, 256), 256, 0, ctx->stream>>>(n, 1.0, z, rz_new / rz, p, p);
-            rz = rz_new;
+    double rr = 0.0;
+    if (!(bnorm > 0.0)) {
+        EFE_CUDA(ctx, cudaMemsetAsync(phi, 0, sizeof(double) * n, ctx->stream));
+    } else {
+        // r = F - K phi0 (warm) or F (cold, phi0 = 0); z = D^-1 r; p = z
+        if (warm) {
+            EFE_TRY(lap_apply(ctx, phi, Ap));
+            k_axpy_n<<<nb(n, 256), 256, 0, ctx->stream>>>(n, 1.0, F, -1.0, Ap, r);
+        } else {
+            EFE_CUDA(ctx, cudaMemsetAsync(phi, 0, sizeof(double) * n, ctx->stream));
+            EFE_CUDA(ctx, cudaMemcpyAsync(r, F, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
         }
+        k_set_scalar<<<1, 1, 0, ctx->stream>>>(sc, CG_THR, tol * bnorm);
+        k_set_scalar<<<1, 1, 0, ctx->stream>>>(sc, CG_ALPHA, 0.0);
+        // with alpha = 0 the update only forms z = D^-1 r and the partials of r.r, r.z
+        // (p and Ap are not read)
+        k_cg_update<<<NRED, 256, 0, ctx->stream>>>(n, sc, phi, r, p, Ap, S.d_dinv, z, S.cg_part);
+        k_cg_beta<<<1, 32, 0, ctx->stream>>>(S.cg_part, sc, 1);
+        EFE_CUDA(ctx, cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        EFE_TRY(efe_check_launch(ctx, "poisson start"));
+        double hs[CG_NSC];
+        EFE_CUDA(ctx, cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+        EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        rr = hs[CG_RR];
+        int issued = 0;
+        bool done = hs[CG_DONE] != 0.0;
+        while (!done && issued < max_it) {
+            const int blk = std::min(kCgBlock, max_it - issued);
+            for (int k = 0; k < blk; ++k) {
+                EFE_TRY(lap_apply(ctx, p, Ap));
+                k_dotp<<<NRED, 256, 0, ctx->stream>>>(n, p, Ap, S.cg_part);
+                k_cg_alpha<<<1, 32, 0, ctx->stream>>>(S.cg_part, sc);
+                k_cg_update<<<NRED, 256, 0, ctx->stream>>>(n, sc, phi, r, p, Ap, S.d_dinv, z, S.cg_part);
+                k_cg_beta<<<1, 32, 0, ctx->stream>>>(S.cg_part, sc, 0);
+                k_cg_p<<<nb(n, 256), 256, 0, ctx->stream>>>(n, sc, z, p);
+            }
+            EFE_TRY(efe_check_launch(ctx, "poisson iterations"));
+            issued += blk;
+            EFE_CUDA(ctx, cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+            EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            done = hs[CG_DONE] != 0.0;
+        }
+        it = (int)hs[CG_IT];
+        rr = hs[CG_RR];
     }
     if (phi_q) EFE_TRY(cell_values(ctx, phi, nullptr, 1, nullptr, 1, phi_q));
-    cleanup();
     if (iters) *iters = it;
     if (rel_res) *rel_res = bnorm > 0 ? rr / bnorm : 0.0;
     return EFE_OK;
@@ -599,7 +872,11 @@ efe_status efe_scf(efe_ctx *ctx, const efe_scf_opts *o, double *X, int N, const 
     EFE_TRY(scf_prepare(ctx));
     ScfState &S = scf_state(ctx);
     const long long nq = ctx->n_quad, nn = ctx->n_nodes, rows = ctx->n_rows;
-    const int hist = std::max(0, o->mix_history);
+    if (o->mix_history < 0 || o->mix_history > kMixMax) {
+        ctx->err = "efe_scf: mix_history must be in [0, 8]";
+        return EFE_ERR_ARG;
+    }
+    const int hist = o->mix_history;
     double ne = 0.0;
     for (double z : ctx->zval) ne += z;
     const double kT = 3.166811563e-6 * o->temperature;
@@ -631,11 +908,13 @@ efe_status efe_scf(efe_ctx *ctx, const efe_scf_opts *o, double *X, int N, const 
     const int HS = hist + 1;
     double *rho_in = take(sizeof(double) * nq), *rho_out = take(sizeof(double) * nq), *veff = take(sizeof(double) * nq),
            *vxc = take(sizeof(double) * nq), *exc = take(sizeof(double) * nq), *phi = take(sizeof(double) * nn),
+           *phi2 = take(sizeof(double) * nn),
            *phi_q = take(sizeof(double) * nq), *tmp = take(sizeof(double) * nq),
            *HX = take(sizeof(double) * rows * N), *Vout = take(sizeof(double) * rows * N),
-           *dlam = take(sizeof(double) * N), *hin = take(sizeof(double) * nq * HS), *hout = take(sizeof(double) * nq * HS);
-    if (!rho_in || !rho_out || !veff || !vxc || !exc || !phi || !phi_q || !tmp || !HX || !Vout || !dlam || !hin ||
-        !hout) {
+           *dlam = take(sizeof(double) * N), *hin = take(sizeof(double) * nq * HS), *hres = take(sizeof(double) * nq * HS),
+           *mixpart = take(sizeof(double) * (NRED + 1) * kMixNV);
+    if (!rho_in || !rho_out || !veff || !vxc || !exc || !phi || !phi2 || !phi_q || !tmp || !HX || !Vout || !dlam || !hin ||
+        !hres || !mixpart) {
         cleanup();
         return EFE_ERR_OOM;
     }
@@ -659,19 +938,31 @@ efe_status efe_scf(efe_ctx *ctx, const efe_scf_opts *o, double *X, int N, const 
     std::vector<double> eig(N), resid(N), occ(N), lam(N);
     double E = 0.0, F = 0.0, mu = 0.0, E_prev = 0.0, dr = 0.0, dE = 0.0;
     bool have_prev = false, conv = false;
+    double maxres = 1e300;            // largest occupied residual after the last Rayleigh-Ritz
     int nh = 0;                       // history entries stored (ring of HS)
     int it = 0;
     const efe_precision prec = (efe_precision)o->precision;
     res->poisson_iters = 0;
+    for (int k = 0; k < 5; ++k) res->ms_phase[k] = 0.0;
+    auto tprev = std::chrono::steady_clock::now();
+    auto mark = [&](int k) {
+        if (!o->profile) return;
+        cudaStreamSynchronize(ctx->stream);
+        const auto t = std::chrono::steady_clock::now();
+        res->ms_phase[k] += std::chrono::duration<double, std::milli>(t - tprev).count();
+        tprev = t;
+    };
     for (it = 1; it <= o->max_iter; ++it) {
         int pit = 0;
         // v_eff = v_xc[rho_in] + phi[rho_in + b]
+        // each Poisson solve starts from the previous solution of the same kind
         k_add3<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, rho_in, S.d_b, tmp);
-        SCF_TRY(poisson(ctx, tmp, phi, phi_q, o->poisson_tol, 100000, &pit, nullptr));
+        SCF_TRY(poisson(ctx, tmp, phi, phi_q, o->poisson_tol, 100000, &pit, nullptr, it > 1));
         res->poisson_iters += pit;
         k_lda<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, rho_in, vxc, nullptr);
         k_add3<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, vxc, phi_q, veff);
         SCF_TRY(efe_potential_assembly(ctx, veff));
+        mark(0);
         if (it == 1) {
             int passes = 0;
             st = efe_chfsi(ctx, X, HX, N, o->cheb_degree, nullptr, u0, o->first_max_pass, o->first_tol, nocc, prec,
@@ -690,7 +981,11 @@ efe_status efe_scf(efe_ctx *ctx, const efe_scf_opts *o, double *X, int N, const 
                 return EFE_ERR_CUDA;
             }
             const double bd[3] = {eig[0], eig[N - 1], lz[2]};
-            SCF_TRY(efe_filter(ctx, X, HX, dlam, N, o->cheb_degree, bd, prec, Vout));
+            // mixed schedule: after the first iteration, bf16 passes only while the
+            // occupied residuals are large
+            const efe_precision pp =
+                (prec == EFE_BF16 && o->bf16_resid > 0.0 && maxres <= o->bf16_resid) ? EFE_FP32 : prec;
+            SCF_TRY(efe_filter(ctx, X, HX, dlam, N, o->cheb_degree, bd, pp, Vout));
             SCF_TRY(efe_rayleigh_ritz(ctx, Vout, HX, N, eig.data(), resid.data()));
             if (cudaMemcpyAsync(X, Vout, sizeof(double) * rows * N, cudaMemcpyDeviceToDevice, ctx->stream) !=
                 cudaSuccess) {
@@ -698,6 +993,9 @@ efe_status efe_scf(efe_ctx *ctx, const efe_scf_opts *o, double *X, int N, const 
                 return EFE_ERR_CUDA;
             }
         }
+        mark(1);
+        maxres = 0.0;
+        for (int j = 0; j < std::min(nocc, N); ++j) maxres = std::max(maxres, resid[j]);
         SCF_TRY(efe_fermi(ctx, eig.data(), N, ne, kT, &mu, occ.data()));
         SCF_TRY(efe_density(ctx, X, N, occ.data(), rho_out));
         if (o->renormalize) {
@@ -705,9 +1003,10 @@ efe_status efe_scf(efe_ctx *ctx, const efe_scf_opts *o, double *X, int N, const 
             SCF_TRY(integrate(ctx, rho_out, nullptr, tot));
             k_scale_n<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, ne / tot, rho_out);
         }
+        mark(2);
         // energies
         k_add3<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, rho_out, S.d_b, tmp);
-        SCF_TRY(poisson(ctx, tmp, phi, phi_q, o->poisson_tol, 100000, &pit, nullptr));
+        SCF_TRY(poisson(ctx, tmp, phi2, phi_q, o->poisson_tol, 100000, &pit, nullptr, it > 1));
         res->poisson_iters += pit;
         k_lda<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, rho_out, nullptr, exc);
         double i_rv, i_rexc, i_hart;
@@ -727,6 +1026,7 @@ efe_status efe_scf(efe_ctx *ctx, const efe_scf_opts *o, double *X, int N, const 
         SCF_TRY(integrate(ctx, tmp, tmp, d2));
         dr = std::sqrt(std::max(d2, 0.0)) / ne;
         dE = have_prev ? std::fabs(E - E_prev) / std::max(1, ctx->natoms) : 1e300;
+        mark(3);
         if (o->log) o->log(o->log_user, it, E, F, mu, dr, dE, resid[0]);
         if (dr < o->tol_rho && dE < o->tol_e) {
             conv = true;
@@ -734,44 +1034,35 @@ efe_status efe_scf(efe_ctx *ctx, const efe_scf_opts *o, double *X, int N, const 
         }
         E_prev = E;
         have_prev = true;
-        // Anderson (Walker-Ni form) on the quadrature-point densities
+        // Anderson (Walker-Ni form) on the quadrature-point densities: rings of
+        // rho_in and of R = rho_out - rho_in; one pass forms the normal equations
         const int slot = nh % HS;
         cudaMemcpyAsync(hin + (size_t)slot * nq, rho_in, sizeof(double) * nq, cudaMemcpyDeviceToDevice, ctx->stream);
-        cudaMemcpyAsync(hout + (size_t)slot * nq, rho_out, sizeof(double) * nq, cudaMemcpyDeviceToDevice, ctx->stream);
+        k_axpy_n<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, 1.0, rho_out, -1.0, rho_in, hres + (size_t)slot * nq);
         ++nh;
         const int have = std::min(nh, HS);           // entries, oldest first
         auto at = [&](double *base, int k) { return base + (size_t)((nh - have + k) % HS) * nq; };
         const int mm = have - 1;
-        double *xk = at(hin, mm);
-        // R_k = out_k - in_k (into tmp)
-        k_axpy_n<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, 1.0, at(hout, mm), -1.0, xk, tmp);
-        std::vector<double> gamma(mm, 0.0);
+        MixRing ring{};
+        for (int k = 0; k < have; ++k) {
+            ring.x[k] = at(hin, k);
+            ring.R[k] = at(hres, k);
+        }
+        MixCoef gc{};
         if (mm > 0) {
-            // dR_j = R_{j+1} - R_j ; A = dR^T W dR, b = dR^T W R_k (normal equations)
-            double *dRj = nullptr, *dRi = nullptr;
-            dRj = take(sizeof(double) * nq);
-            dRi = take(sizeof(double) * nq);
-            if (!dRj || !dRi) { cleanup(); return EFE_ERR_OOM; }
-            std::vector<double> A(mm * mm), bvec(mm);
-            auto make_dR = [&](int j, double *out) {
-                // (out_{j+1} - in_{j+1}) - (out_j - in_j)
-                k_axpy_n<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, 1.0, at(hout, j + 1), -1.0, at(hin, j + 1), out);
-                k_axpy_n<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, 1.0, out, -1.0, at(hout, j), out);
-                k_axpy_n<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, 1.0, out, 1.0, at(hin, j), out);
-            };
+            k_mix_gram<<<NRED, 256, 0, ctx->stream>>>(ctx->m, T, ring, mm, mixpart);
+            k_mix_sum<<<1, 64, 0, ctx->stream>>>(NRED, mixpart, mixpart + (size_t)NRED * kMixNV);
+            double hv[kMixNV];
+            if (cudaMemcpyAsync(hv, mixpart + (size_t)NRED * kMixNV, sizeof(hv), cudaMemcpyDeviceToHost,
+                                ctx->stream) != cudaSuccess ||
+                cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+                cleanup();
+                return EFE_ERR_CUDA;
+            }
+            std::vector<double> A(mm * mm), bvec(mm), gamma(mm, 0.0);
             for (int i = 0; i < mm; ++i) {
-                make_dR(i, dRi);
-                for (int j = i; j < mm; ++j) {
-                    make_dR(j, dRj);
-                    double v;
-                    k_wdot<<<NRED, 256, 0, ctx->stream>>>(ctx->m, T, dRi, dRj, S.d_part);
-                    SCF_TRY(reduce_host(ctx, S, v));
-                    A[i * mm + j] = A[j * mm + i] = v;
-                }
-                double v;
-                k_wdot<<<NRED, 256, 0, ctx->stream>>>(ctx->m, T, dRi, tmp, S.d_part);
-                SCF_TRY(reduce_host(ctx, S, v));
-                bvec[i] = v;
+                for (int j = i; j < mm; ++j) A[i * mm + j] = A[j * mm + i] = hv[mix_idx(i, j)];
+                bvec[i] = hv[kMixNV - kMixMax + i];
             }
             // least squares by the pseudo-inverse (eigen-decomposition of A)
             std::vector<double> w, Vv;
@@ -785,24 +1076,10 @@ efe_status efe_scf(efe_ctx *ctx, const efe_scf_opts *o, double *X, int N, const 
                 for (int i = 0; i < mm; ++i) proj += Vv[i * mm + k] * bvec[i];
                 for (int i = 0; i < mm; ++i) gamma[i] += Vv[i * mm + k] * proj / w[k];
             }
-            cudaStreamSynchronize(ctx->stream);
-            cudaFree(dRj);
-            cudaFree(dRi);
-            own.pop_back();
-            own.pop_back();
+            for (int i = 0; i < mm; ++i) gc.g[i] = gamma[i];
         }
-        // rho_next = (x_k - dX gamma) + beta (R_k - dR gamma), built in rho_in
-        k_axpy_n<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, 1.0, xk, o->mix_beta, tmp, rho_in);
-        for (int j = 0; j < mm; ++j) {
-            if (gamma[j] == 0.0) continue;
-            // dX_j = in_{j+1} - in_j ; dR_j = (out_{j+1}-in_{j+1}) - (out_j-in_j)
-            const double gj = gamma[j], bt = o->mix_beta;
-            // rho -= g (in_{j+1} - in_j) + beta g (dR_j)
-            k_axpy_n<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, 1.0, rho_in, -gj * (1.0 - bt), at(hin, j + 1), rho_in);
-            k_axpy_n<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, 1.0, rho_in, gj * (1.0 - bt), at(hin, j), rho_in);
-            k_axpy_n<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, 1.0, rho_in, -gj * bt, at(hout, j + 1), rho_in);
-            k_axpy_n<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, 1.0, rho_in, gj * bt, at(hout, j), rho_in);
-        }
+        k_mix_update<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, ring, mm, gc, o->mix_beta, rho_in);
+        mark(4);
         if (cudaGetLastError() != cudaSuccess) {
             cleanup();
             return EFE_ERR_CUDA;

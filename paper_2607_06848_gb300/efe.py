@@ -60,14 +60,15 @@ class efe_scf_opts(ctypes.Structure):
                 ("mix_history", ctypes.c_int), ("tol_rho", ctypes.c_double), ("tol_e", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("first_tol", ctypes.c_double), ("first_max_pass", ctypes.c_int),
                 ("renormalize", ctypes.c_int), ("kappa", ctypes.c_double), ("poisson_tol", ctypes.c_double),
-                ("precision", ctypes.c_int), ("log", SCF_LOG), ("log_user", ctypes.c_void_p)]
+                ("precision", ctypes.c_int), ("log", SCF_LOG), ("log_user", ctypes.c_void_p),
+                ("bf16_resid", ctypes.c_double), ("profile", ctypes.c_int)]
 
 
 class efe_scf_result(ctypes.Structure):
     _fields_ = [("E", ctypes.c_double), ("F", ctypes.c_double), ("mu", ctypes.c_double), ("drho", ctypes.c_double),
                 ("dE", ctypes.c_double), ("iters", ctypes.c_int), ("converged", ctypes.c_int),
                 ("poisson_iters", ctypes.c_longlong), ("eig", ctypes.POINTER(ctypes.c_double)),
-                ("rho_q", ctypes.c_void_p)]
+                ("rho_q", ctypes.c_void_p), ("ms_phase", ctypes.c_double * 5)]
 
 
 _P = ctypes.c_void_p
@@ -98,7 +99,26 @@ SIGNATURES = {
     "efe_integrate": [_P, _P, _P, _D],
     "efe_integrate_noalloc": [_P, _P, _P, _D],
     "efe_scf": [_P, ctypes.POINTER(efe_scf_opts), _P, _I, _P, _P, ctypes.POINTER(efe_scf_result)],
+    "efe_mlp_create": [_P, _I, ctypes.POINTER(_P)],
+    "efe_mlp_destroy": [_P],
+    "efe_mlp_last_error": [_P],
+    "efe_descriptors": [_P, _P, _P, _I, _P],
+    "efe_mlp_forward": [_P, _P, _P, _I, _P],
+    "efe_mlp_normalise": [_P, _P, _P, _P, _I],
+    "efe_mlp_loss_grad": [_P, _P, _P, _P, _I, _P, _D],
+    "efe_mlp_adam": [_P, _P, _P, _P, _P, _I, _P],
+    "efe_mlp_train": [_P, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P],
+    "efe_density_correction": [_P, _P, _P],
+    "efe_fit_correction": [_P, _P, _P, ctypes.c_double, _P],
+    "efe_warm_start": [_P, _P, _P, ctypes.c_double, _P, ctypes.POINTER(_I)],
 }
+
+MLP_N_DESC, MLP_N_OUT, MLP_N_TRAIN, MLP_N_PARAMS = 32, 8, 38280, 38360
+
+
+class efe_adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float)]
 
 _lib = None
 
@@ -115,7 +135,8 @@ def load():
     for name, args in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name == "efe_last_error" else (None if name == "efe_destroy" else ctypes.c_int)
+        fn.restype = (ctypes.c_char_p if name in ("efe_last_error", "efe_mlp_last_error") else
+                      None if name in ("efe_destroy", "efe_mlp_destroy") else ctypes.c_int)
     _lib = lib
     return lib
 
@@ -293,7 +314,8 @@ class EFE:
                          int(opts.get("max_iter", 60)), float(opts.get("first_tol", 1e-2)),
                          int(opts.get("first_max_pass", 20)), int(opts.get("renormalize", 1)),
                          float(opts.get("kappa", 2.4)), float(opts.get("poisson_tol", 1e-12)),
-                         int(opts.get("precision", EFE_FP64)), SCF_LOG(0), None)
+                         int(opts.get("precision", EFE_FP64)), SCF_LOG(0), None,
+                         float(opts.get("bf16_resid", 1.0)), int(opts.get("profile", 0)))
         hist = []
         if log is not None:
             def cb(user, it, E, F, mu, dr, dE, r0):
@@ -311,4 +333,75 @@ class EFE:
             self._check(st)
         return dict(E=res.E, F=res.F, mu=res.mu, drho=res.drho, dE=res.dE, iters=res.iters,
                     converged=bool(res.converged), poisson_iters=res.poisson_iters, eig=np.array(eig[:]),
-                    history=hist)
+                    history=hist, ms_phase=list(res.ms_phase))
+
+    # --- learned warm start (ctx part) -----------------------------------
+    def efe_density_correction(self, c, drho_q):
+        self._check(self.lib.efe_density_correction(self.ctx, _ptr(c), _ptr(drho_q)))
+
+    def efe_fit_correction(self, rho_q, c, base_q=None, ridge=1e-3):
+        self._check(self.lib.efe_fit_correction(self.ctx, _ptr(rho_q), _ptr(base_q), float(ridge), _ptr(c)))
+
+    def efe_warm_start(self, mlp, theta, rho_q, kappa=2.4):
+        """Returns True when rho_q holds the superposition (no network or fallback)."""
+        fb = ctypes.c_int(1)
+        self._check(self.lib.efe_warm_start(self.ctx, None if mlp is None else mlp.h, _ptr(theta),
+                                            float(kappa), _ptr(rho_q), ctypes.byref(fb)))
+        return bool(fb.value)
+
+
+class MLP:
+    """Training workspace of the warm-start network (efe_mlp_*): marshalling only."""
+
+    def __init__(self, max_samples, stream=None):
+        import torch
+        self.lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = self.lib.efe_mlp_create(ctypes.c_void_p(stream.cuda_stream), int(max_samples), ctypes.byref(h))
+        if st != 0:
+            raise EFEError(st, self.lib.efe_mlp_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st):
+        if st != 0:
+            raise EFEError(st, self.lib.efe_mlp_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.efe_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def efe_descriptors(self, xyz, zval, D):
+        self._check(self.lib.efe_descriptors(self.h, _ptr(xyz), _ptr(zval), xyz.shape[0], _ptr(D)))
+
+    def efe_mlp_forward(self, theta, D, C):
+        self._check(self.lib.efe_mlp_forward(self.h, _ptr(theta), _ptr(D), D.shape[0], _ptr(C)))
+
+    def efe_mlp_normalise(self, theta, D, T):
+        self._check(self.lib.efe_mlp_normalise(self.h, _ptr(theta), _ptr(D), _ptr(T), D.shape[0]))
+
+    def efe_mlp_loss_grad(self, theta, D, T, grad):
+        loss = ctypes.c_double(0.0)
+        self._check(self.lib.efe_mlp_loss_grad(self.h, _ptr(theta), _ptr(D), _ptr(T), D.shape[0], _ptr(grad),
+                                               ctypes.byref(loss)))
+        return loss.value
+
+    def efe_mlp_adam(self, theta, m, v, grad, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        hp = efe_adam(lr, beta1, beta2, eps)
+        self._check(self.lib.efe_mlp_adam(self.h, _ptr(theta), _ptr(m), _ptr(v), _ptr(grad), int(t),
+                                          ctypes.byref(hp)))
+
+    def efe_mlp_train(self, theta, m, v, D, T, steps, loss_hist, t0=0, lr=1e-3, beta1=0.9, beta2=0.999,
+                      eps=1e-8):
+        hp = efe_adam(lr, beta1, beta2, eps)
+        self._check(self.lib.efe_mlp_train(self.h, _ptr(theta), _ptr(m), _ptr(v), _ptr(D), _ptr(T), D.shape[0],
+                                           int(steps), int(t0), ctypes.byref(hp), _ptr(loss_hist)))
