@@ -155,29 +155,58 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def roofline(head, d, N, ms_sweep, pk, pk_kind):
-    """Roofline of the dominant kernel (the cell products), from its live CUDA-event time."""
-    if head == "bf16":
-        # tensor-core cell products stream H_e (bf16, n_e^2), gather X'_e (bf16,
-        # n_e N) and write Y_e (fp32, n_e N) per cell: 2 n_e^2 N flop against
-        # 2 n_e^2 + 6 n_e N bytes -> ~66 flop/B at N = 154, below the ridge
-        # (~292 flop/B), so HBM-bound
-        traffic_alg = d["n_cells"] * (2.0 * d["ne"] ** 2 + 6.0 * d["ne"] * N)
-        achieved = traffic_alg / (ms_sweep / 1e3) / 1e9 if ms_sweep > 0 else None
+def _traffic_per_unit(name, key):
+    """A per-unit DRAM traffic figure recorded from an ncu capture (profiles/<name>)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            for line in f:
+                if line.startswith(key):
+                    return float(line.split()[1])
+    except OSError:
+        pass
+    return None
+
+
+def roofline_bf16(w, d, N, m, ms_cell_launch, ms_rec_launch, pk, pk_kind):
+    """HBM rooflines of the two heaviest kernels of the bf16 filter, from their
+    live CUDA-event times; the one with the larger share of the step comes first.
+
+    k_cell_mma (tensor-core cell products) streams per cell the bf16 H_e tile
+    (n_e^2 x 2 B), gathers X'_e (n_e N x 2 B) and writes Y_e (n_e N x 4 B):
+    2 n_e^2 N flop against 2 n_e^2 + 6 n_e N bytes -> ~66 flop/B at N = 154,
+    below the ridge (~292 flop/B), so HBM-bound.
+    k_gather_rec_f (node recurrence) reads, per interior node, its cell rows
+    (one per cell containing the node) and Z_{k-1}, Z_{k-2}, G, writes Z_k, and
+    writes HY at support nodes and zeros at Dirichlet nodes, 4 N bytes each."""
+    p = w["p"]
+    nx, ny, nz = w["ncell"]
+    inc = (nx * (p + 1) - 2) * (ny * (p + 1) - 2) * (nz * (p + 1) - 2)   # interior (cell, node) pairs
+    z0 = (m - 2) / (m - 1)                       # the first recurrence step has no Z_{k-2}
+    rec_bytes = 4.0 * N * (inc + (2 + z0 + 1) * d["n_fe_dof"] + d["n_support_nodes"]
+                           + (d["n_nodes"] - d["n_fe_dof"]))
+    cell_bytes = d["n_cells"] * (2.0 * d["ne"] ** 2 + 6.0 * d["ne"] * N)
+    hbm = pk["hbm_gbs"]
+    out = []
+    for name, bytes_, ms, traffic_key in (
+            ("k_gather_rec_f (FE-node recurrence: gather of cell products, coupling, Eq. residualapprox)",
+             rec_bytes, ms_rec_launch, None),
+            ("k_cell_mma (tcgen05 cell products, one launch per H apply)", cell_bytes, ms_cell_launch,
+             "bytes_per_cell")):
+        achieved = bytes_ / (ms / 1e3) / 1e9 if ms and ms > 0 else None
         traffic = None
-        try:   # measured DRAM bytes per cell (ncu capture, same kernel), scaled to this launch
-            with open(os.path.join(ROOT, "profiles", "k_cell_mma_traffic.txt")) as f:
-                for line in f:
-                    if line.startswith("bytes_per_cell") and d["ne"] == 343 and N == 154:
-                        traffic = float(line.split()[1]) * d["n_cells"]
-        except OSError:
-            pass
-        return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"] if achieved else None, "traffic": traffic,
-                "algorithmic_bytes": traffic_alg, "peak_kind": pk_kind + " (burst copy)",
-                "kernel": "k_cell_mma (tcgen05 cell products, one launch per H apply)",
-                "ms_per_launch": ms_sweep}
-    # SIMT cell products: FP32 (or FP64) FMA pipes, 152 SMs x lanes x 2 flop x max clock
+        if traffic_key and d["ne"] == 343 and N == 154:   # counters taken on this kernel at this shape
+            per = _traffic_per_unit("k_cell_mma_traffic.txt", traffic_key)
+            traffic = per * d["n_cells"] if per else None
+        out.append({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm if achieved else None, "traffic": traffic,
+                    "algorithmic_bytes": bytes_, "peak_kind": pk_kind + " (burst copy)", "kernel": name,
+                    "ms_per_launch": ms, "ms_per_step": ms * (m - 1) if ms else None})
+    out.sort(key=lambda r: -(r["ms_per_step"] or 0.0))
+    return out
+
+
+def roofline_simt(head, d, N, ms_sweep, pk):
+    """SIMT cell products: FP32 (or FP64) FMA pipes, 152 SMs x lanes x 2 flop x max clock."""
     lanes = 128 if head == "fp32" else 2
     peak = 152 * lanes * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     flops = d["n_cells"] * 2.0 * d["ne"] ** 2 * N
@@ -190,27 +219,32 @@ def roofline(head, d, N, ms_sweep, pk, pk_kind):
 
 
 def scf_time_to_solution(torch, dev):
-    """SCF time-to-solution on the 2-atom workload (8^3 cells, p = 4, 8 states,
-    degree 20), FP64 and with bf16 tensor-core filter passes; |dE| per atom of
-    the mixed run against the FP64 run."""
+    """SCF time-to-solution, FP64 and mixed (bf16 passes in the first iteration, FP32
+    after), from the same start vectors, with |dE| per atom of mixed against FP64:
+    the 2-atom workload (8^3 cells, p = 4, 8 states, degree 20) and an 8-atom cluster
+    at the same resolution (12x13x11 cells, 20 states)."""
     from paper_2607_06848_gb300 import EFE, workloads as W, EFE_FP64, EFE_BF16
-    w = W.dimer()
-    g = EFE(w["h"], w["ncell"], w["p"], w["atoms"], w["Z"], enrich=dict(alpha=ALPHA, r_end=R_END, t=T_ENR),
-            psp=dict(rc=1.0, r_trunc=6.0, h=w["hproj"], rloc=0.8))
-    rows = g.dims["n_rows"]
     out = {}
-    for name, prec in (("fp64", EFE_FP64), ("mixed_bf16", EFE_BF16)):
-        X = torch.tensor(W.random_block(rows, w["nstates"], 1), device=dev)
-        u0 = torch.tensor(W.random_block(rows, 1, 2), device=dev)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r = g.efe_scf(X, u0, cheb_degree=w["cheb_degree"], precision=prec)
-        torch.cuda.synchronize()
-        out[name] = {"seconds": time.perf_counter() - t0, "iters": r["iters"], "converged": r["converged"],
-                     "E_Ha": r["E"]}
-    out["dE_mixed_vs_fp64_Ha_per_atom"] = abs(out["mixed_bf16"]["E_Ha"] - out["fp64"]["E_Ha"]) / len(w["atoms"])
-    out["workload"] = "dimer: 2 atoms, 8^3 cells p=4 (29,791 FE DOF + 8 enriched), 8 states, degree 20"
-    g.close()
+    for key, w in (("dimer", W.dimer()), ("cluster8_h2p4", W.ws_cluster(8, 1008))):
+        g = EFE(w["h"], w["ncell"], w["p"], w["atoms"], w["Z"], enrich=dict(alpha=ALPHA, r_end=R_END, t=T_ENR),
+                psp=dict(rc=1.0, r_trunc=6.0, h=w["hproj"], rloc=0.8))
+        rows = g.dims["n_rows"]
+        rec = {}
+        for name, prec in (("fp64", EFE_FP64), ("mixed_bf16", EFE_BF16)):
+            X = torch.tensor(W.random_block(rows, w["nstates"], 1), device=dev)
+            u0 = torch.tensor(W.random_block(rows, 1, 2), device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = g.efe_scf(X, u0, cheb_degree=w["cheb_degree"], precision=prec)
+            torch.cuda.synchronize()
+            rec[name] = {"seconds": time.perf_counter() - t0, "iters": r["iters"], "converged": r["converged"],
+                         "E_Ha": r["E"], "poisson_cg_iters": r["poisson_iters"]}
+        rec["dE_mixed_vs_fp64_Ha_per_atom"] = abs(rec["mixed_bf16"]["E_Ha"] - rec["fp64"]["E_Ha"]) / len(w["atoms"])
+        d = g.dims
+        rec["workload"] = "%d atoms, %dx%dx%d cells p=%d (%d FE DOF + %d enriched), %d states, degree %d" % (
+            len(w["atoms"]), *w["ncell"], w["p"], d["n_fe_dof"], d["n_enr"], w["nstates"], w["cheb_degree"])
+        out[key] = rec
+        g.close()
     return out
 
 
@@ -272,28 +306,30 @@ def run_ours(args):
         barrier()
         s = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        cells_ms = 0.0
-        launches = 0
+        cells_ms = rec_ms = 0.0
+        launches = rec_n = 0
         e0.record(s)
         for _ in range(steps):
             g.efe_filter(X, HX, lam, m, bounds, Vout, prec=prec)
             st = g.stats()
             cells_ms += st["ms_cell"]
+            rec_ms += st["ms_rec"]
+            rec_n += st["rec_launches"]
             launches += st["launches"]
         e1.record(s)
         barrier()
         ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist, dev)
-        return ms, cells_ms / steps, launches
+        return ms, cells_ms / steps, launches, (rec_ms / rec_n if rec_n else None)
 
     precs = {"fp64": EFE_FP64, "fp32": EFE_FP32, "bf16": EFE_BF16}
     head = args.prec
     clk = ClockSampler(local)
-    ms, cell_ms, launches = timed(precs[head], args.steps, args.warmup)
+    ms, cell_ms, launches, rec_ms_launch = timed(precs[head], args.steps, args.warmup)
     clocks = clk.stop()
     by_prec = {head: {"ms_per_step": ms, "value": units / (ms / 1e3) / 1e9, "steps": args.steps}}
     for extra in args.also:
         if extra != head:
-            mse, _, _ = timed(precs[extra], 1, 0)
+            mse, _, _, _ = timed(precs[extra], 1, 0)
             by_prec[extra] = {"ms_per_step": mse, "value": units / (mse / 1e3) / 1e9, "steps": 1}
 
     # end to end through the public call with host buffers (pinned)
@@ -316,6 +352,10 @@ def run_ours(args):
 
     pk, pk_kind = peaks()
     ms_sweep = cell_ms / (m - 1)          # m - 1 H applies per filter pass
+    if head == "bf16":
+        rl = roofline_bf16(w, d, N, m, ms_sweep, rec_ms_launch, pk, pk_kind)
+    else:
+        rl = [roofline_simt(head, d, N, ms_sweep, pk)]
     line = {
         "metric": METRIC, "value": job_value(units, world, ms), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -329,7 +369,8 @@ def run_ours(args):
                    "potential": "Harris v_xc[rho0] + phi[rho0 + b_sm] of superposed atomic densities "
                                 "(Poisson CG %d iterations)" % poisson_its},
         "by_precision": by_prec,
-        "roofline": roofline(head, d, N, ms_sweep, pk, pk_kind),
+        "roofline": rl[0],
+        "roofline_kernels": rl,
         "e2e": {"value": job_value(units, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,

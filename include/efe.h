@@ -112,6 +112,8 @@ typedef struct {
     int ne;              /* (p+1)^3 nodes per cell */
     int nq;              /* Gauss points per axis */
     int grid[3];         /* Gx, Gy, Gz */
+    long long n_support_nodes; /* FE nodes inside the support of at least one
+                                  enrichment or projector function */
 } efe_dims;
 
 /* Timings of the last efe_chfsi / efe_filter call, from CUDA events on the
@@ -124,6 +126,10 @@ typedef struct {
     long long launches;  /* kernels launched by the last filter */
     long long cell_launches; /* of which cell-product kernels */
     int passes;
+    double ms_rec;       /* the FE-node recurrence kernels (gather of the cell
+                            products, coupling, Eq. residualapprox) inside the last
+                            bf16 filter */
+    long long rec_launches;
 } efe_stats;
 
 /* Build the discretisation, enrichment, orthogonalization (C = B^T (M^cc)^-1,
@@ -383,6 +389,13 @@ efe_status efe_mlp_adam(efe_mlp *mlp, float *theta, float *m, float *v, const fl
  * loss_hist: device `steps` floats (out), the loss before each update. */
 efe_status efe_mlp_train(efe_mlp *mlp, float *theta, float *m, float *v, const float *D, const float *T,
                          int n, int steps, int t0, const efe_adam *hp, float *loss_hist);
+
+/* Parameter file: the 8-byte tag "EFEMLP01", the count EFE_MLP_N_PARAMS as a
+ * little-endian int32, then the floats of theta (little-endian).  theta:
+ * device.  efe_mlp_load fails with EFE_ERR_ARG (nothing written to theta) if
+ * the file is missing, truncated or carries another tag or count. */
+efe_status efe_mlp_save(efe_mlp *mlp, const float *theta, const char *path);
+efe_status efe_mlp_load(efe_mlp *mlp, const char *path, float *theta);
 
 /* drho at the quadrature points of ctx's mesh from coefficients c (device
  * natoms x 8, atom order of efe_setup).  drho_q: device n_quad (out). */

@@ -70,6 +70,26 @@ std::pair<cudaEvent_t, cudaEvent_t> *cell_event_pair(efe_ctx *ctx) {
     return &ctx->cell_events[ctx->cell_events_used++];
 }
 
+std::pair<cudaEvent_t, cudaEvent_t> *rec_event_pair(efe_ctx *ctx) {
+    if (ctx->rec_events_used == ctx->rec_events.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess) return nullptr;
+        if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return nullptr; }
+        ctx->rec_events.push_back({a, b});
+    }
+    return &ctx->rec_events[ctx->rec_events_used++];
+}
+
+double rec_events_ms(efe_ctx *ctx) {
+    double t = 0.0;
+    for (size_t i = 0; i < ctx->rec_events_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->rec_events[i].first, ctx->rec_events[i].second) == cudaSuccess) t += ms;
+    }
+    ctx->rec_events_used = 0;
+    return t;
+}
+
 // sum of the recorded sweeps (the stream must have been synchronised)
 double cell_events_ms(efe_ctx *ctx) {
     double t = 0.0;
@@ -360,177 +380,177 @@ __device__ inline void fma4(float4 &a, float s, const float4 b) {
     a.x += s * b.x; a.y += s * b.y; a.z += s * b.z; a.w += s * b.w;
 }
 
+// Per-node row kernels of the bf16 filter.  A block holds npb nodes x ncg
+// float4 column groups (thread = one float4 of one node row), so no lane idles
+// when the row length is not a multiple of 128 floats; the per-node indices
+// (interior flag, cell rows, coupling range) are formed once per node in
+// shared memory.
+constexpr int kRowThreads = 512, kRowNodes = 64;
+inline int row_npb(int ncg) { return std::max(1, std::min(kRowNodes, kRowThreads / ncg)); }
+
 // Xb[n][4q..4q+3] = bf16( minv[n] Z[n] - sum_e C_e . Ye[atom(e)] ) (ldb >= ldz, padding zero)
-__global__ void __launch_bounds__(256) k_pre_bf16_v(MeshDev m, int nn, const float *Z, int ldz, const float *Ye,
-                                                    int lde, int ldb, const double *minv, const long long *node_ptr,
-                                                    const int *node_ent, const int *ent_atom, const float *C,
-                                                    int use_c, __nv_bfloat16 *Xb) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = blockIdx.x * 8 + warp;
-    if (n >= nn) return;
-    int ix, iy, iz;
-    node_xyz(m, n, ix, iy, iz);
-    const bool inter = node_interior(m, ix, iy, iz);
-    const float mi = inter ? (float)minv[n] : 0.f;
-    int ecount = 0;
-    long long e0 = 0;
-    if (inter && use_c) {
-        e0 = node_ptr[n];
-        ecount = (int)(node_ptr[n + 1] - e0);
-    }
-    // this node's coupling entries, one per lane (chunks of 32), broadcast by shuffles
-    const float *zr = Z + (size_t)n * ldz;
-    __nv_bfloat16 *out = Xb + (size_t)n * ldb;
-    float4 v[2];
-    for (int t = 0; t < 2; ++t) {
-        const int j = 4 * lane + 128 * t;
-        v[t] = (inter && j < ldz) ? f4(zr + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-        v[t].x *= mi; v[t].y *= mi; v[t].z *= mi; v[t].w *= mi;
-    }
-    for (int c0 = 0; c0 < ecount; c0 += 32) {
-        int myI = 0;
-        float4 myc = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c0 + lane < ecount) {
-            const int g = node_ent[e0 + c0 + lane];
-            myI = ent_atom[g];
-            myc = f4(C + 4 * (long long)g);
-        }
-        const int cnt = min(32, ecount - c0);
-        for (int k = 0; k < cnt; ++k) {
-            const int I = __shfl_sync(0xffffffffu, myI, k);
-            const float cx = __shfl_sync(0xffffffffu, myc.x, k), cy = __shfl_sync(0xffffffffu, myc.y, k);
-            const float cz = __shfl_sync(0xffffffffu, myc.z, k), cw = __shfl_sync(0xffffffffu, myc.w, k);
-            for (int t = 0; t < 2; ++t) {
-                const int j = 4 * lane + 128 * t;
-                if (j < ldz) {
-                    fma4(v[t], -cx, f4(Ye + (size_t)(4 * I + 0) * lde + j));
-                    fma4(v[t], -cy, f4(Ye + (size_t)(4 * I + 1) * lde + j));
-                    fma4(v[t], -cz, f4(Ye + (size_t)(4 * I + 2) * lde + j));
-                    fma4(v[t], -cw, f4(Ye + (size_t)(4 * I + 3) * lde + j));
+__global__ void __launch_bounds__(kRowThreads) k_pre_bf16_f(MeshDev m, int nn, int npb, const float *Z, int ldz,
+                                                          const float *Ye, int lde, int ldb, const double *minv,
+                                                          const long long *node_ptr, const int *node_ent,
+                                                          const int *ent_atom, const float *C, int use_c,
+                                                          __nv_bfloat16 *Xb) {
+    __shared__ float s_mi[kRowNodes];
+    __shared__ long long s_e0[kRowNodes];
+    __shared__ int s_cnt[kRowNodes];
+    const int ncg = ldb / 4;
+    const long long nbase = (long long)blockIdx.x * npb;
+    if (threadIdx.x < npb) {
+        const long long n = nbase + threadIdx.x;
+        float mi = 0.f;
+        long long e0 = 0;
+        int cnt = 0;
+        if (n < nn) {
+            int ix, iy, iz;
+            node_xyz(m, (int)n, ix, iy, iz);
+            if (node_interior(m, ix, iy, iz)) {
+                mi = (float)minv[n];
+                if (use_c) {
+                    e0 = node_ptr[n];
+                    cnt = (int)(node_ptr[n + 1] - e0);
                 }
             }
         }
+        s_mi[threadIdx.x] = mi;
+        s_e0[threadIdx.x] = e0;
+        s_cnt[threadIdx.x] = cnt;
     }
-    for (int t = 0; t < 2; ++t) {
-        const int j = 4 * lane + 128 * t;
-        if (j < ldb) {
-            __nv_bfloat162 lo = __floats2bfloat162_rn(v[t].x, v[t].y), hi = __floats2bfloat162_rn(v[t].z, v[t].w);
-            uint2 pk;
-            pk.x = *reinterpret_cast<uint32_t *>(&lo);
-            pk.y = *reinterpret_cast<uint32_t *>(&hi);
-            *reinterpret_cast<uint2 *>(out + j) = pk;
+    __syncthreads();
+    const int ln = threadIdx.x / ncg, cg = threadIdx.x - ln * ncg;
+    const long long n = nbase + ln;
+    if (ln >= npb || n >= nn) return;
+    const int j = 4 * cg;
+    const float mi = s_mi[ln];
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j < ldz && mi != 0.f) {
+        v = f4(Z + (size_t)n * ldz + j);
+        v.x *= mi; v.y *= mi; v.z *= mi; v.w *= mi;
+        const long long e0 = s_e0[ln];
+        const int cnt = s_cnt[ln];
+        for (int k = 0; k < cnt; ++k) {
+            const int g = node_ent[e0 + k];
+            const int I = ent_atom[g];
+            const float4 cc = f4(C + 4 * (long long)g);
+            fma4(v, -cc.x, f4(Ye + (size_t)(4 * I + 0) * lde + j));
+            fma4(v, -cc.y, f4(Ye + (size_t)(4 * I + 1) * lde + j));
+            fma4(v, -cc.z, f4(Ye + (size_t)(4 * I + 2) * lde + j));
+            fma4(v, -cc.w, f4(Ye + (size_t)(4 * I + 3) * lde + j));
         }
     }
+    __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+    uint2 pk;
+    pk.x = *reinterpret_cast<uint32_t *>(&lo);
+    pk.y = *reinterpret_cast<uint32_t *>(&hi);
+    *reinterpret_cast<uint2 *>(Xb + (size_t)n * ldb + j) = pk;
 }
 
-// Fused gather + coupling + FE-row recurrence on float4 columns (see k_gather_rec).
-__global__ void __launch_bounds__(256) k_gather_rec_v(MeshDev m, int nn, int ldz, const float *Yc, int ldy,
-                                                      const long long *node_ptr, const int *node_ent,
-                                                      const int *ent_atom, const float *Hca, const float *Pc,
-                                                      const float *Ye, const float *W, int lde, int use_h, int use_p,
-                                                      const float *Z1, const float *Z0, const float *G,
-                                                      const float *ck, float a, float c, float b, float *Zn,
-                                                      float *HYs) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = blockIdx.x * 8 + warp;
-    if (n >= nn) return;
-    int ix, iy, iz;
-    node_xyz(m, n, ix, iy, iz);
+// One recurrence step at the FE nodes, fused with the gather of the cell
+// products and the FE-enrichment coupling:
+//   HY[n] = sum over the cells of n of Y_cell[row(n)] + sum_e (Hca_e . Ye + Pc_e . W)
+//   Zn[n] = a (HY[n] - c Z1[n]) - b Z0[n] + a G[n] ck      (Eq. residualapprox)
+// HY is kept at support nodes (HYs) for the enrichment rows.  ldz = ncg * 4.
+__global__ void __launch_bounds__(kRowThreads) k_gather_rec_f(MeshDev m, int nn, int npb, int ldz, const float *Yc,
+                                                            int ldy, const long long *node_ptr, const int *node_ent,
+                                                            const int *ent_atom, const float *Hca, const float *Pc,
+                                                            const float *Ye, const float *W, int lde, int use_h,
+                                                            int use_p, const float *Z1, const float *Z0,
+                                                            const float *G, const float *ck, float a, float c, float b,
+                                                            float *Zn, float *HYs) {
+    __shared__ long long s_base[kRowNodes][8];
+    __shared__ long long s_e0[kRowNodes];
+    __shared__ int s_nb[kRowNodes], s_cnt[kRowNodes];
+    const int ncg = ldz / 4;
+    const long long nbase = (long long)blockIdx.x * npb;
+    if (threadIdx.x < npb) {
+        const long long n = nbase + threadIdx.x;
+        int nb = -1, cnt = 0;
+        long long e0 = 0;
+        if (n < nn) {
+            int ix, iy, iz;
+            node_xyz(m, (int)n, ix, iy, iz);
+            if (node_interior(m, ix, iy, iz)) {
+                int cv[3][2], av[3][2], cc[3];
+                const int ii[3] = {ix, iy, iz}, nc[3] = {m.nx, m.ny, m.nz};
+                for (int d = 0; d < 3; ++d) {
+                    const int q = ii[d] / m.p, r = ii[d] - q * m.p;
+                    cc[d] = 0;
+                    if (r == 0) {
+                        if (q - 1 >= 0) { cv[d][cc[d]] = q - 1; av[d][cc[d]] = m.p; ++cc[d]; }
+                        if (q < nc[d]) { cv[d][cc[d]] = q; av[d][cc[d]] = 0; ++cc[d]; }
+                    } else {
+                        cv[d][0] = q; av[d][0] = r; cc[d] = 1;
+                    }
+                }
+                nb = 0;
+                for (int a2 = 0; a2 < cc[2]; ++a2)
+                    for (int b2 = 0; b2 < cc[1]; ++b2)
+                        for (int c2 = 0; c2 < cc[0]; ++c2) {
+                            const long long cell = ((long long)cv[2][a2] * m.ny + cv[1][b2]) * m.nx + cv[0][c2];
+                            const int l = (av[2][a2] * m.np1 + av[1][b2]) * m.np1 + av[0][c2];
+                            s_base[threadIdx.x][nb++] = (cell * m.ne + l) * ldy;
+                        }
+                if (node_ptr) {
+                    e0 = node_ptr[n];
+                    cnt = (int)(node_ptr[n + 1] - e0);
+                }
+            }
+        }
+        s_nb[threadIdx.x] = nb;
+        s_e0[threadIdx.x] = e0;
+        s_cnt[threadIdx.x] = cnt;
+    }
+    __syncthreads();
+    const int ln = threadIdx.x / ncg, cg = threadIdx.x - ln * ncg;
+    const long long n = nbase + ln;
+    if (ln >= npb || n >= nn) return;
+    const int j = 4 * cg;
     const size_t row = (size_t)n * ldz;
-    if (!node_interior(m, ix, iy, iz)) {
-        for (int j = 4 * lane; j < ldz; j += 128)
-            *reinterpret_cast<float4 *>(Zn + row + j) = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int nb = s_nb[ln];
+    if (nb < 0) {                       // Dirichlet node: held at zero
+        *reinterpret_cast<float4 *>(Zn + row + j) = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
-    int cv[3][2], av[3][2], cnt[3];
-    const int ii[3] = {ix, iy, iz}, nc[3] = {m.nx, m.ny, m.nz};
-    for (int d = 0; d < 3; ++d) {
-        const int q = ii[d] / m.p, r = ii[d] - q * m.p;
-        cnt[d] = 0;
-        if (r == 0) {
-            if (q - 1 >= 0) { cv[d][cnt[d]] = q - 1; av[d][cnt[d]] = m.p; ++cnt[d]; }
-            if (q < nc[d]) { cv[d][cnt[d]] = q; av[d][cnt[d]] = 0; ++cnt[d]; }
-        } else {
-            cv[d][0] = q; av[d][0] = r; cnt[d] = 1;
-        }
-    }
-    long long base[8];
-    int nb = 0;
-    for (int a2 = 0; a2 < cnt[2]; ++a2)
-        for (int b2 = 0; b2 < cnt[1]; ++b2)
-            for (int c2 = 0; c2 < cnt[0]; ++c2) {
-                const long long cell = ((long long)cv[2][a2] * m.ny + cv[1][b2]) * m.nx + cv[0][c2];
-                const int l = (av[2][a2] * m.np1 + av[1][b2]) * m.np1 + av[0][c2];
-                base[nb++] = (cell * m.ne + l) * ldy;
-            }
-    for (int t = nb; t < 8; ++t) base[t] = base[0];
-    int ecount = 0;
-    long long e0 = 0;
-    if (node_ptr) {
-        e0 = node_ptr[n];
-        ecount = (int)(node_ptr[n + 1] - e0);
-    }
-    float4 acc[2];
-    for (int t = 0; t < 2; ++t) {
-        const int j = 4 * lane + 128 * t;
-        acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (j < ldz) {
-            float4 y[8];
+    float4 y[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) y[u] = (u < nb) ? f4(Yc + base[u] + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int u = 0; u < 8; ++u) y[u] = (u < nb) ? f4(Yc + s_base[ln][u] + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) { acc[t].x += y[u].x; acc[t].y += y[u].y; acc[t].z += y[u].z; acc[t].w += y[u].w; }
+    for (int u = 0; u < 8; ++u) { acc.x += y[u].x; acc.y += y[u].y; acc.z += y[u].z; acc.w += y[u].w; }
+    const long long e0 = s_e0[ln];
+    const int cnt = s_cnt[ln];
+    for (int k = 0; k < cnt; ++k) {
+        const int g = node_ent[e0 + k];
+        const int I = ent_atom[g];
+        if (use_h) {
+            const float4 h = f4(Hca + 4 * (long long)g);
+            fma4(acc, h.x, f4(Ye + (size_t)(4 * I + 0) * lde + j));
+            fma4(acc, h.y, f4(Ye + (size_t)(4 * I + 1) * lde + j));
+            fma4(acc, h.z, f4(Ye + (size_t)(4 * I + 2) * lde + j));
+            fma4(acc, h.w, f4(Ye + (size_t)(4 * I + 3) * lde + j));
+        }
+        if (use_p) {
+            const float4 pp = f4(Pc + 4 * (long long)g);
+            fma4(acc, pp.x, f4(W + (size_t)(4 * I + 0) * lde + j));
+            fma4(acc, pp.y, f4(W + (size_t)(4 * I + 1) * lde + j));
+            fma4(acc, pp.z, f4(W + (size_t)(4 * I + 2) * lde + j));
+            fma4(acc, pp.w, f4(W + (size_t)(4 * I + 3) * lde + j));
         }
     }
-    for (int c0 = 0; c0 < ecount; c0 += 32) {
-        int myI = 0;
-        float4 myh = make_float4(0.f, 0.f, 0.f, 0.f), myp = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c0 + lane < ecount) {
-            const int g = node_ent[e0 + c0 + lane];
-            myI = ent_atom[g];
-            if (use_h) myh = f4(Hca + 4 * (long long)g);
-            if (use_p) myp = f4(Pc + 4 * (long long)g);
-        }
-        const int cnt = min(32, ecount - c0);
-        for (int k = 0; k < cnt; ++k) {
-            const int I = __shfl_sync(0xffffffffu, myI, k);
-            const float h0 = __shfl_sync(0xffffffffu, myh.x, k), h1 = __shfl_sync(0xffffffffu, myh.y, k);
-            const float h2 = __shfl_sync(0xffffffffu, myh.z, k), h3 = __shfl_sync(0xffffffffu, myh.w, k);
-            const float p0 = __shfl_sync(0xffffffffu, myp.x, k), p1 = __shfl_sync(0xffffffffu, myp.y, k);
-            const float p2 = __shfl_sync(0xffffffffu, myp.z, k), p3 = __shfl_sync(0xffffffffu, myp.w, k);
-            for (int t = 0; t < 2; ++t) {
-                const int j = 4 * lane + 128 * t;
-                if (j >= ldz) continue;
-                if (use_h) {
-                    fma4(acc[t], h0, f4(Ye + (size_t)(4 * I + 0) * lde + j));
-                    fma4(acc[t], h1, f4(Ye + (size_t)(4 * I + 1) * lde + j));
-                    fma4(acc[t], h2, f4(Ye + (size_t)(4 * I + 2) * lde + j));
-                    fma4(acc[t], h3, f4(Ye + (size_t)(4 * I + 3) * lde + j));
-                }
-                if (use_p) {
-                    fma4(acc[t], p0, f4(W + (size_t)(4 * I + 0) * lde + j));
-                    fma4(acc[t], p1, f4(W + (size_t)(4 * I + 1) * lde + j));
-                    fma4(acc[t], p2, f4(W + (size_t)(4 * I + 2) * lde + j));
-                    fma4(acc[t], p3, f4(W + (size_t)(4 * I + 3) * lde + j));
-                }
-            }
-        }
-    }
-    for (int t = 0; t < 2; ++t) {
-        const int j = 4 * lane + 128 * t;
-        if (j >= ldz) continue;
-        const float4 z1 = f4(Z1 + row + j);
-        const float4 z0 = Z0 ? f4(Z0 + row + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 gg = f4(G + row + j);
-        const float4 kk = f4(ck + j);
-        float4 zn;
-        zn.x = a * (acc[t].x - c * z1.x) - b * z0.x + a * gg.x * kk.x;
-        zn.y = a * (acc[t].y - c * z1.y) - b * z0.y + a * gg.y * kk.y;
-        zn.z = a * (acc[t].z - c * z1.z) - b * z0.z + a * gg.z * kk.z;
-        zn.w = a * (acc[t].w - c * z1.w) - b * z0.w + a * gg.w * kk.w;
-        *reinterpret_cast<float4 *>(Zn + row + j) = zn;
-        if (ecount > 0) *reinterpret_cast<float4 *>(HYs + row + j) = acc[t];
-    }
+    const float4 z1 = f4(Z1 + row + j);
+    const float4 z0 = Z0 ? f4(Z0 + row + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 gg = f4(G + row + j);
+    const float4 kk = f4(ck + j);
+    float4 zn;
+    zn.x = a * (acc.x - c * z1.x) - b * z0.x + a * gg.x * kk.x;
+    zn.y = a * (acc.y - c * z1.y) - b * z0.y + a * gg.y * kk.y;
+    zn.z = a * (acc.z - c * z1.z) - b * z0.z + a * gg.z * kk.z;
+    zn.w = a * (acc.w - c * z1.w) - b * z0.w + a * gg.w * kk.w;
+    *reinterpret_cast<float4 *>(Zn + row + j) = zn;
+    if (cnt > 0) *reinterpret_cast<float4 *>(HYs + row + j) = acc;
 }
 
 // Support reduction: warps over positions (8 rows in flight per warp), lanes
@@ -1318,8 +1338,11 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     const bool cpl = (ctx->enrich || ctx->nonlocal) && ctx->natoms > 0;
     HxScratch s{};
     if (cpl) EFE_TRY(hx_scratch(ctx, N, s));
-    const unsigned rb_all = (unsigned)((rows + 7) / 8), rb_fe = (unsigned)((nn + 7) / 8);
+    const unsigned rb_all = (unsigned)((rows + 7) / 8);
+    const int npb_b = row_npb(ldb / 4), npb_z = row_npb(ldz / 4);
+    const unsigned gpre = (unsigned)((nn + npb_b - 1) / npb_b), ggat = (unsigned)((nn + npb_z - 1) / npb_z);
     ctx->cell_events_used = 0;
+    ctx->rec_events_used = 0;
     ctx->cell_launches = 0;
     Timer tm(ctx->stream);
     const long long l0 = ctx->launches;
@@ -1340,11 +1363,11 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
                                                                                 Zcur + nn * ldz, Ye, lde);
             ctx->launches++;
         }
-        k_pre_bf16_v<<<rb_fe, 256, 0, ctx->stream>>>(mh, (int)nn, Zcur, ldz, Ye, lde, ldb, ctx->d_minv,
-                                                     ctx->d_node_ptr, ctx->d_node_ent, ctx->d_ent_atom, ctx->d_C32,
-                                                     ctx->enrich ? 1 : 0, Xb);
+        k_pre_bf16_f<<<gpre, npb_b * (ldb / 4), 0, ctx->stream>>>(mh, (int)nn, npb_b, Zcur, ldz, Ye, lde, ldb,
+                                                                 ctx->d_minv, ctx->d_node_ptr, ctx->d_node_ent,
+                                                                 ctx->d_ent_atom, ctx->d_C32, ctx->enrich ? 1 : 0, Xb);
         ctx->launches++;
-        EFE_TRY(efe_check_launch(ctx, "k_pre_bf16_v"));
+        EFE_TRY(efe_check_launch(ctx, "k_pre_bf16_f"));
         {
             auto *ev = cell_event_pair(ctx);
             if (ev) cudaEventRecord(ev->first, ctx->stream);
@@ -1374,13 +1397,15 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
                 ctx->launches++;
             }
         }
-        k_gather_rec_v<<<rb_fe, 256, 0, ctx->stream>>>(mh, (int)nn, ldz, Ycells, ldy, cpl ? ctx->d_node_ptr : nullptr,
-                                                       ctx->d_node_ent, ctx->d_ent_atom, ctx->d_Hca32, ctx->d_Pc32,
-                                                       Ye, W32, lde, ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0,
-                                                       Zcur, Zprev, G, fck + (size_t)(k - 1) * ldz, ak, cf, bk, Znext,
-                                                       HYs);
+        auto *rev = rec_event_pair(ctx);
+        if (rev) cudaEventRecord(rev->first, ctx->stream);
+        k_gather_rec_f<<<ggat, npb_z * (ldz / 4), 0, ctx->stream>>>(
+            mh, (int)nn, npb_z, ldz, Ycells, ldy, cpl ? ctx->d_node_ptr : nullptr, ctx->d_node_ent, ctx->d_ent_atom,
+            ctx->d_Hca32, ctx->d_Pc32, Ye, W32, lde, ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0, Zcur, Zprev, G,
+            fck + (size_t)(k - 1) * ldz, ak, cf, bk, Znext, HYs);
+        if (rev) cudaEventRecord(rev->second, ctx->stream);
         ctx->launches++;
-        EFE_TRY(efe_check_launch(ctx, "k_gather_rec_v"));
+        EFE_TRY(efe_check_launch(ctx, "k_gather_rec_f"));
         if (ne_) {
             k_support_reduce3<float><<<gred, 256, 0, ctx->stream>>>(ctx->d_sup_off, ctx->d_sup_node, ctx->d_C32,
                                                                     nullptr, HYs, N, ldz, s.chunk, s.nch, s.part);
@@ -1408,6 +1433,8 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     EFE_TRY(efe_check_launch(ctx, "filter_tensor"));
     ctx->stats.ms_filter = tm.stop();
     ctx->stats.ms_cell = cell_events_ms(ctx);
+    ctx->stats.rec_launches = (long long)ctx->rec_events_used;
+    ctx->stats.ms_rec = rec_events_ms(ctx);
     ctx->stats.launches = ctx->launches - l0;
     ctx->stats.cell_launches = ctx->cell_launches;
     int flag = 0;
@@ -1632,10 +1659,11 @@ void efe_destroy(efe_ctx *ctx) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
-    for (auto &e : ctx->cell_events) {
-        cudaEventDestroy(e.first);
-        cudaEventDestroy(e.second);
-    }
+    for (auto *ev : {&ctx->cell_events, &ctx->rec_events})
+        for (auto &e : *ev) {
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
     if (ctx->solver) cusolverDnDestroy(ctx->solver);
     delete ctx;
 }
@@ -1767,6 +1795,7 @@ efe_status efe_get_dims(const efe_ctx *ctx, efe_dims *d) {
     d->grid[0] = ctx->m.Gx;
     d->grid[1] = ctx->m.Gy;
     d->grid[2] = ctx->m.Gz;
+    d->n_support_nodes = ctx->n_support_nodes;
     return EFE_OK;
 }
 

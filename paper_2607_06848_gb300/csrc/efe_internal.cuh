@@ -104,6 +104,10 @@ struct efe_ctx {
     // after the next synchronisation of the stream
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> cell_events;
     size_t cell_events_used = 0;
+    // the same for the node-recurrence kernels of the bf16 filter
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> rec_events;
+    size_t rec_events_used = 0;
+    long long n_support_nodes = 0;
     long long cell_launches = 0;
 };
 

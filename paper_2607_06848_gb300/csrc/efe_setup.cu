@@ -490,7 +490,11 @@ efe_status efe_static_integrals(efe_ctx *ctx) {
     // node CSR
     std::vector<long long> node_ptr(ctx->n_nodes + 1, 0);
     for (long long g = 0; g < ctx->sup_total; ++g) node_ptr[sup_node[g] + 1]++;
-    for (long long n = 0; n < ctx->n_nodes; ++n) node_ptr[n + 1] += node_ptr[n];
+    ctx->n_support_nodes = 0;
+    for (long long n = 0; n < ctx->n_nodes; ++n) {
+        if (node_ptr[n + 1] > 0) ++ctx->n_support_nodes;
+        node_ptr[n + 1] += node_ptr[n];
+    }
     std::vector<int> node_ent(ctx->sup_total);
     {
         std::vector<long long> fill(node_ptr.begin(), node_ptr.end() - 1);

@@ -16,6 +16,9 @@
 #include "efe_funcs.cuh"
 
 #include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
 #include <vector>
 
 namespace {
@@ -847,6 +850,44 @@ efe_status efe_mlp_train(efe_mlp *mlp, float *theta, float *m, float *v, const f
     cudaStreamSynchronize(cs);
     cudaGraphExecDestroy(exec);
     return st;
+}
+
+// The file layout is defined little-endian; the hosts this builds for (x86-64,
+// AArch64) are little-endian, so the bytes are written as they are in memory.
+static const char kMlpTag[8] = {'E', 'F', 'E', 'M', 'L', 'P', '0', '1'};
+
+efe_status efe_mlp_save(efe_mlp *mlp, const float *theta, const char *path) {
+    if (!mlp) return EFE_ERR_ARG;
+    MLP_ARG(mlp, theta && path, "efe_mlp_save: null pointer");
+    std::vector<float> h(NPARAM);
+    MLP_CUDA(mlp, cudaMemcpyAsync(h.data(), theta, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, mlp->user));
+    MLP_CUDA(mlp, cudaStreamSynchronize(mlp->user));
+    FILE *f = std::fopen(path, "wb");
+    MLP_ARG(mlp, f != nullptr, std::string("efe_mlp_save: cannot open ") + path);
+    const int32_t cnt = NPARAM;
+    const bool ok = std::fwrite(kMlpTag, 1, 8, f) == 8 && std::fwrite(&cnt, 4, 1, f) == 1 &&
+                    std::fwrite(h.data(), sizeof(float), NPARAM, f) == (size_t)NPARAM;
+    const bool closed = std::fclose(f) == 0;
+    MLP_ARG(mlp, ok && closed, std::string("efe_mlp_save: write failed for ") + path);
+    return EFE_OK;
+}
+
+efe_status efe_mlp_load(efe_mlp *mlp, const char *path, float *theta) {
+    if (!mlp) return EFE_ERR_ARG;
+    MLP_ARG(mlp, theta && path, "efe_mlp_load: null pointer");
+    FILE *f = std::fopen(path, "rb");
+    MLP_ARG(mlp, f != nullptr, std::string("efe_mlp_load: cannot open ") + path);
+    char tag[8];
+    int32_t cnt = 0;
+    std::vector<float> h(NPARAM);
+    const bool ok = std::fread(tag, 1, 8, f) == 8 && std::memcmp(tag, kMlpTag, 8) == 0 &&
+                    std::fread(&cnt, 4, 1, f) == 1 && cnt == NPARAM &&
+                    std::fread(h.data(), sizeof(float), NPARAM, f) == (size_t)NPARAM;
+    std::fclose(f);
+    MLP_ARG(mlp, ok, std::string("efe_mlp_load: not a parameter file of this network: ") + path);
+    MLP_CUDA(mlp, cudaMemcpyAsync(theta, h.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice, mlp->user));
+    MLP_CUDA(mlp, cudaStreamSynchronize(mlp->user));
+    return EFE_OK;
 }
 
 efe_status efe_density_correction(efe_ctx *ctx, const double *c, double *drho_q) {

@@ -42,13 +42,14 @@ class efe_dims(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_longlong), ("n_fe_dof", ctypes.c_longlong),
                 ("n_rows", ctypes.c_longlong), ("n_quad", ctypes.c_longlong), ("n_enr", ctypes.c_int),
                 ("n_proj", ctypes.c_int), ("n_cells", ctypes.c_int), ("ne", ctypes.c_int),
-                ("nq", ctypes.c_int), ("grid", ctypes.c_int * 3)]
+                ("nq", ctypes.c_int), ("grid", ctypes.c_int * 3), ("n_support_nodes", ctypes.c_longlong)]
 
 
 class efe_stats(ctypes.Structure):
     _fields_ = [("ms_filter", ctypes.c_double), ("ms_rr", ctypes.c_double), ("ms_lanczos", ctypes.c_double),
                 ("ms_cell", ctypes.c_double), ("launches", ctypes.c_longlong),
-                ("cell_launches", ctypes.c_longlong), ("passes", ctypes.c_int)]
+                ("cell_launches", ctypes.c_longlong), ("passes", ctypes.c_int), ("ms_rec", ctypes.c_double),
+                ("rec_launches", ctypes.c_longlong)]
 
 
 SCF_LOG = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -108,6 +109,8 @@ SIGNATURES = {
     "efe_mlp_loss_grad": [_P, _P, _P, _P, _I, _P, _D],
     "efe_mlp_adam": [_P, _P, _P, _P, _P, _I, _P],
     "efe_mlp_train": [_P, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P],
+    "efe_mlp_save": [_P, _P, ctypes.c_char_p],
+    "efe_mlp_load": [_P, ctypes.c_char_p, _P],
     "efe_density_correction": [_P, _P, _P],
     "efe_fit_correction": [_P, _P, _P, ctypes.c_double, _P],
     "efe_warm_start": [_P, _P, _P, ctypes.c_double, _P, ctypes.POINTER(_I)],
@@ -399,6 +402,12 @@ class MLP:
         hp = efe_adam(lr, beta1, beta2, eps)
         self._check(self.lib.efe_mlp_adam(self.h, _ptr(theta), _ptr(m), _ptr(v), _ptr(grad), int(t),
                                           ctypes.byref(hp)))
+
+    def efe_mlp_save(self, theta, path):
+        self._check(self.lib.efe_mlp_save(self.h, _ptr(theta), os.fsencode(path)))
+
+    def efe_mlp_load(self, path, theta):
+        self._check(self.lib.efe_mlp_load(self.h, os.fsencode(path), _ptr(theta)))
 
     def efe_mlp_train(self, theta, m, v, D, T, steps, loss_hist, t0=0, lr=1e-3, beta1=0.9, beta2=0.999,
                       eps=1e-8):

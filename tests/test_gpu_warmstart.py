@@ -226,3 +226,25 @@ def test_learned_start_cuts_scf_iterations():
         assert abs(l["E"] - s["E"]) / 8 < 1e-6
         gains.append(s["iters"] - l["iters"])
     assert sum(gains) > 0, gains
+
+
+def test_parameter_file_round_trip_and_rejections(tmp_path):
+    mlp = _mlp()
+    th = _f32(W.mlp_init(6))
+    path = str(tmp_path / "ws.params")
+    mlp.efe_mlp_save(th, path)
+    back = torch.zeros_like(th)
+    mlp.efe_mlp_load(path, back)
+    assert torch.equal(th, back)
+    raw = open(path, "rb").read()
+    assert raw[:8] == b"EFEMLP01" and len(raw) == 12 + 4 * O.N_PARAMS
+    from paper_2607_06848_gb300 import EFEError
+    for bad in (raw[:100], b"EFEMLP02" + raw[8:]):
+        p2 = str(tmp_path / "bad.params")
+        open(p2, "wb").write(bad)
+        keep = torch.full_like(th, 7.0)
+        with pytest.raises(EFEError):
+            mlp.efe_mlp_load(p2, keep)
+        assert torch.all(keep == 7.0)
+    with pytest.raises(EFEError):
+        mlp.efe_mlp_load(str(tmp_path / "missing.params"), back)
