@@ -226,18 +226,25 @@ def fit_correction(mesh, atoms, drho, ridge=1e-3):
     return np.linalg.solve(A, r).reshape(len(atoms), N_OUT)
 
 
-def warm_start_density(mesh, atoms, Z, theta=None, rho_sup=None, kappa=2.4):
-    """rho_0 = max(rho_sup + drho, 0) scaled to N_e, or rho_sup when theta is None or
-    the corrected density is not usable (non-finite or without positive charge).
-    Returns (rho_0, used_fallback)."""
+def corrected_density(mesh, atoms, Z, c, rho_sup=None, kappa=2.4):
+    """max(rho_sup + drho(c), 0) scaled to N_e, or rho_sup when that density is not
+    usable (non-finite or without positive charge).  Returns (rho_0, used_fallback)."""
     from .scf import initial_density
     if rho_sup is None:
         rho_sup = initial_density(mesh, atoms, Z, kappa)
-    if theta is None:
-        return rho_sup, True
-    c = predict(theta, descriptors(atoms, Z))
     rho = np.maximum(rho_sup + density_correction(mesh, atoms, c), 0.0)
     tot = mesh.integrate(rho)
     if not np.all(np.isfinite(rho)) or not tot > 0.0:
         return rho_sup, True
     return rho * (float(np.sum(Z)) / tot), False
+
+
+def warm_start_density(mesh, atoms, Z, theta=None, rho_sup=None, kappa=2.4):
+    """The corrected density with the network's coefficients, or rho_sup when theta is
+    None.  Returns (rho_0, used_fallback)."""
+    from .scf import initial_density
+    if rho_sup is None:
+        rho_sup = initial_density(mesh, atoms, Z, kappa)
+    if theta is None:
+        return rho_sup, True
+    return corrected_density(mesh, atoms, Z, predict(theta, descriptors(atoms, Z)), rho_sup=rho_sup)
