@@ -175,7 +175,7 @@ def roofline_bf16(w, d, N, m, ms_cell_launch, ms_rec_launch, pk, pk_kind):
     (n_e^2 x 2 B), gathers X'_e (n_e N x 2 B) and writes Y_e (n_e N x 4 B):
     2 n_e^2 N flop against 2 n_e^2 + 6 n_e N bytes -> ~66 flop/B at N = 154,
     below the ridge (~292 flop/B), so HBM-bound.
-    k_gather_rec_f (node recurrence) reads, per interior node, its cell rows
+    k_gather_rec_w (node recurrence) reads, per interior node, its cell rows
     (one per cell containing the node) and Z_{k-1}, Z_{k-2}, G, writes Z_k, and
     writes HY at support nodes and zeros at Dirichlet nodes, 4 N bytes each."""
     p = w["p"]
@@ -188,7 +188,7 @@ def roofline_bf16(w, d, N, m, ms_cell_launch, ms_rec_launch, pk, pk_kind):
     hbm = pk["hbm_gbs"]
     out = []
     for name, bytes_, ms, traffic_key in (
-            ("k_gather_rec_f (FE-node recurrence: gather of cell products, coupling, Eq. residualapprox)",
+            ("k_gather_rec_w (FE-node recurrence: gather of cell products, coupling, Eq. residualapprox)",
              rec_bytes, ms_rec_launch, None),
             ("k_cell_mma (tcgen05 cell products, one launch per H apply)", cell_bytes, ms_cell_launch,
              "bytes_per_cell")):
@@ -338,12 +338,14 @@ def run_ours(args):
     lamh = torch.tensor(eig, dtype=torch.float64).contiguous()
     Vh.copy_(X.cpu())
     HVh.copy_(HX.cpu())
+    Oh = torch.empty((rows, N), dtype=torch.float64, pin_memory=True)   # pinned output
     e2e_steps = max(1, min(args.steps, 3))
-    g.efe_filter_host(Vh.numpy(), HVh.numpy(), lamh.numpy(), m, bounds, prec=precs[head])
+    g.efe_filter_host(Vh.numpy(), HVh.numpy(), lamh.numpy(), m, bounds, prec=precs[head], out=Oh.numpy())
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        out_h = g.efe_filter_host(Vh.numpy(), HVh.numpy(), lamh.numpy(), m, bounds, prec=precs[head])
+        out_h = g.efe_filter_host(Vh.numpy(), HVh.numpy(), lamh.numpy(), m, bounds, prec=precs[head],
+                                  out=Oh.numpy())
     barrier()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) / e2e_steps * 1e3, dist, dev)
     h2d = (2 * rows * N + N) * 8

@@ -200,7 +200,9 @@ efe_status efe_chfsi(efe_ctx *ctx, double *X, double *HX, int N, int m, const do
                      efe_precision prec, double *eig, double *resid, int *passes);
 
 /* Same filter with host buffers (V, HV, Vout: host rows x N; lam: host N):
- * copies in, filters, copies out on the library stream, returns when done. */
+ * copies in, filters, copies out on the library stream, returns when done.
+ * The device copies (3 rows x N + N doubles) stay allocated in the context
+ * for later calls; page-locked host buffers give the full copy bandwidth. */
 efe_status efe_filter_host(efe_ctx *ctx, const double *V, const double *HV, const double *lam,
                            int N, int m, const double bounds[3], efe_precision prec,
                            double *Vout);
@@ -408,6 +410,13 @@ efe_status efe_density_correction(efe_ctx *ctx, const double *c, double *drho_q)
  * Cholesky).  c: device natoms x 8 (out).  EFE_ERR_NOT_SPD if the system is
  * not positive definite (ridge = 0 with dependent functions). */
 efe_status efe_fit_correction(efe_ctx *ctx, const double *rho_q, const double *base_q, double ridge, double *c);
+
+/* The superposition (as efe_atomic_density with kappa) plus the correction
+ * with coefficients c (device natoms x 8), clipped at zero and scaled to N_e;
+ * the superposition alone when that density is not finite or has no charge.
+ * rho_q: device n_quad (out); fallback: host (may be NULL), 1 when rho_q is the
+ * superposition. */
+efe_status efe_corrected_density(efe_ctx *ctx, const double *c, double kappa, double *rho_q, int *fallback);
 
 /* Start density: the superposition (as efe_atomic_density with kappa) plus the
  * network's correction, clipped at zero and scaled to N_e.  theta: device

@@ -380,177 +380,352 @@ __device__ inline void fma4(float4 &a, float s, const float4 b) {
     a.x += s * b.x; a.y += s * b.y; a.z += s * b.z; a.w += s * b.w;
 }
 
-// Per-node row kernels of the bf16 filter.  A block holds npb nodes x ncg
-// float4 column groups (thread = one float4 of one node row), so no lane idles
-// when the row length is not a multiple of 128 floats; the per-node indices
-// (interior flag, cell rows, coupling range) are formed once per node in
-// shared memory.
-constexpr int kRowThreads = 512, kRowNodes = 64;
-inline int row_npb(int ncg) { return std::max(1, std::min(kRowNodes, kRowThreads / ncg)); }
-
 // Xb[n][4q..4q+3] = bf16( minv[n] Z[n] - sum_e C_e . Ye[atom(e)] ) (ldb >= ldz, padding zero)
-__global__ void __launch_bounds__(kRowThreads) k_pre_bf16_f(MeshDev m, int nn, int npb, const float *Z, int ldz,
-                                                          const float *Ye, int lde, int ldb, const double *minv,
-                                                          const long long *node_ptr, const int *node_ent,
-                                                          const int *ent_atom, const float *C, int use_c,
-                                                          __nv_bfloat16 *Xb) {
-    __shared__ float s_mi[kRowNodes];
-    __shared__ long long s_e0[kRowNodes];
-    __shared__ int s_cnt[kRowNodes];
-    const int ncg = ldb / 4;
-    const long long nbase = (long long)blockIdx.x * npb;
-    if (threadIdx.x < npb) {
-        const long long n = nbase + threadIdx.x;
-        float mi = 0.f;
-        long long e0 = 0;
-        int cnt = 0;
-        if (n < nn) {
-            int ix, iy, iz;
-            node_xyz(m, (int)n, ix, iy, iz);
-            if (node_interior(m, ix, iy, iz)) {
-                mi = (float)minv[n];
-                if (use_c) {
-                    e0 = node_ptr[n];
-                    cnt = (int)(node_ptr[n + 1] - e0);
+__global__ void __launch_bounds__(256) k_pre_bf16_v(MeshDev m, int nn, const float *Z, int ldz, const float *Ye,
+                                                    int lde, int ldb, const double *minv, const long long *node_ptr,
+                                                    const int *node_ent, const int *ent_atom, const float *C,
+                                                    int use_c, __nv_bfloat16 *Xb) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = blockIdx.x * 8 + warp;
+    if (n >= nn) return;
+    int ix, iy, iz;
+    node_xyz(m, n, ix, iy, iz);
+    const bool inter = node_interior(m, ix, iy, iz);
+    const float mi = inter ? (float)minv[n] : 0.f;
+    int ecount = 0;
+    long long e0 = 0;
+    if (inter && use_c) {
+        e0 = node_ptr[n];
+        ecount = (int)(node_ptr[n + 1] - e0);
+    }
+    // this node's coupling entries, one per lane (chunks of 32), broadcast by shuffles
+    const float *zr = Z + (size_t)n * ldz;
+    __nv_bfloat16 *out = Xb + (size_t)n * ldb;
+    float4 v[2];
+    for (int t = 0; t < 2; ++t) {
+        const int j = 4 * lane + 128 * t;
+        v[t] = (inter && j < ldz) ? f4(zr + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[t].x *= mi; v[t].y *= mi; v[t].z *= mi; v[t].w *= mi;
+    }
+    for (int c0 = 0; c0 < ecount; c0 += 32) {
+        int myI = 0;
+        float4 myc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c0 + lane < ecount) {
+            const int g = node_ent[e0 + c0 + lane];
+            myI = ent_atom[g];
+            myc = f4(C + 4 * (long long)g);
+        }
+        const int cnt = min(32, ecount - c0);
+        for (int k = 0; k < cnt; ++k) {
+            const int I = __shfl_sync(0xffffffffu, myI, k);
+            const float cx = __shfl_sync(0xffffffffu, myc.x, k), cy = __shfl_sync(0xffffffffu, myc.y, k);
+            const float cz = __shfl_sync(0xffffffffu, myc.z, k), cw = __shfl_sync(0xffffffffu, myc.w, k);
+            for (int t = 0; t < 2; ++t) {
+                const int j = 4 * lane + 128 * t;
+                if (j < ldz) {
+                    fma4(v[t], -cx, f4(Ye + (size_t)(4 * I + 0) * lde + j));
+                    fma4(v[t], -cy, f4(Ye + (size_t)(4 * I + 1) * lde + j));
+                    fma4(v[t], -cz, f4(Ye + (size_t)(4 * I + 2) * lde + j));
+                    fma4(v[t], -cw, f4(Ye + (size_t)(4 * I + 3) * lde + j));
                 }
             }
         }
-        s_mi[threadIdx.x] = mi;
-        s_e0[threadIdx.x] = e0;
-        s_cnt[threadIdx.x] = cnt;
     }
-    __syncthreads();
-    const int ln = threadIdx.x / ncg, cg = threadIdx.x - ln * ncg;
-    const long long n = nbase + ln;
-    if (ln >= npb || n >= nn) return;
-    const int j = 4 * cg;
-    const float mi = s_mi[ln];
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (j < ldz && mi != 0.f) {
-        v = f4(Z + (size_t)n * ldz + j);
-        v.x *= mi; v.y *= mi; v.z *= mi; v.w *= mi;
-        const long long e0 = s_e0[ln];
-        const int cnt = s_cnt[ln];
-        for (int k = 0; k < cnt; ++k) {
-            const int g = node_ent[e0 + k];
-            const int I = ent_atom[g];
-            const float4 cc = f4(C + 4 * (long long)g);
-            fma4(v, -cc.x, f4(Ye + (size_t)(4 * I + 0) * lde + j));
-            fma4(v, -cc.y, f4(Ye + (size_t)(4 * I + 1) * lde + j));
-            fma4(v, -cc.z, f4(Ye + (size_t)(4 * I + 2) * lde + j));
-            fma4(v, -cc.w, f4(Ye + (size_t)(4 * I + 3) * lde + j));
+    for (int t = 0; t < 2; ++t) {
+        const int j = 4 * lane + 128 * t;
+        if (j < ldb) {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(v[t].x, v[t].y), hi = __floats2bfloat162_rn(v[t].z, v[t].w);
+            uint2 pk;
+            pk.x = *reinterpret_cast<uint32_t *>(&lo);
+            pk.y = *reinterpret_cast<uint32_t *>(&hi);
+            *reinterpret_cast<uint2 *>(out + j) = pk;
         }
     }
-    __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
-    uint2 pk;
-    pk.x = *reinterpret_cast<uint32_t *>(&lo);
-    pk.y = *reinterpret_cast<uint32_t *>(&hi);
-    *reinterpret_cast<uint2 *>(Xb + (size_t)n * ldb + j) = pk;
 }
 
-// One recurrence step at the FE nodes, fused with the gather of the cell
-// products and the FE-enrichment coupling:
-//   HY[n] = sum over the cells of n of Y_cell[row(n)] + sum_e (Hca_e . Ye + Pc_e . W)
-//   Zn[n] = a (HY[n] - c Z1[n]) - b Z0[n] + a G[n] ck      (Eq. residualapprox)
-// HY is kept at support nodes (HYs) for the enrichment rows.  ldz = ncg * 4.
-__global__ void __launch_bounds__(kRowThreads) k_gather_rec_f(MeshDev m, int nn, int npb, int ldz, const float *Yc,
-                                                            int ldy, const long long *node_ptr, const int *node_ent,
-                                                            const int *ent_atom, const float *Hca, const float *Pc,
-                                                            const float *Ye, const float *W, int lde, int use_h,
-                                                            int use_p, const float *Z1, const float *Z0,
-                                                            const float *G, const float *ck, float a, float c, float b,
-                                                            float *Zn, float *HYs) {
-    __shared__ long long s_base[kRowNodes][8];
-    __shared__ long long s_e0[kRowNodes];
-    __shared__ int s_nb[kRowNodes], s_cnt[kRowNodes];
-    const int ncg = ldz / 4;
-    const long long nbase = (long long)blockIdx.x * npb;
-    if (threadIdx.x < npb) {
-        const long long n = nbase + threadIdx.x;
-        int nb = -1, cnt = 0;
-        long long e0 = 0;
-        if (n < nn) {
-            int ix, iy, iz;
-            node_xyz(m, (int)n, ix, iy, iz);
-            if (node_interior(m, ix, iy, iz)) {
-                int cv[3][2], av[3][2], cc[3];
-                const int ii[3] = {ix, iy, iz}, nc[3] = {m.nx, m.ny, m.nz};
-                for (int d = 0; d < 3; ++d) {
-                    const int q = ii[d] / m.p, r = ii[d] - q * m.p;
-                    cc[d] = 0;
-                    if (r == 0) {
-                        if (q - 1 >= 0) { cv[d][cc[d]] = q - 1; av[d][cc[d]] = m.p; ++cc[d]; }
-                        if (q < nc[d]) { cv[d][cc[d]] = q; av[d][cc[d]] = 0; ++cc[d]; }
-                    } else {
-                        cv[d][0] = q; av[d][0] = r; cc[d] = 1;
-                    }
+// Fused gather + coupling + FE-row recurrence on float4 columns (see k_gather_rec).
+__global__ void __launch_bounds__(256) k_gather_rec_v(MeshDev m, int nn, int ldz, const float *Yc, int ldy,
+                                                      const long long *node_ptr, const int *node_ent,
+                                                      const int *ent_atom, const float *Hca, const float *Pc,
+                                                      const float *Ye, const float *W, int lde, int use_h, int use_p,
+                                                      const float *Z1, const float *Z0, const float *G,
+                                                      const float *ck, float a, float c, float b, float *Zn,
+                                                      float *HYs) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = blockIdx.x * 8 + warp;
+    if (n >= nn) return;
+    int ix, iy, iz;
+    node_xyz(m, n, ix, iy, iz);
+    const size_t row = (size_t)n * ldz;
+    if (!node_interior(m, ix, iy, iz)) {
+        for (int j = 4 * lane; j < ldz; j += 128)
+            *reinterpret_cast<float4 *>(Zn + row + j) = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    // the (up to 8) cells holding this node, as scalars per axis so that the
+    // row offsets stay in registers: along each axis the node lies in cell k0
+    // at local index a0, and (on a cell face) also in cell k0 + 1 at index 0
+    int k0[3], a0[3], two[3];
+    {
+        const int ii[3] = {ix, iy, iz}, nc[3] = {m.nx, m.ny, m.nz};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int q = ii[d] / m.p, r = ii[d] - q * m.p;
+            if (r != 0) { k0[d] = q; a0[d] = r; two[d] = 0; }
+            else if (q > 0) { k0[d] = q - 1; a0[d] = m.p; two[d] = q < nc[d] ? 1 : 0; }
+            else { k0[d] = q; a0[d] = 0; two[d] = 0; }
+        }
+    }
+    long long base[8];
+    bool valid[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int sx = u & 1, sy = (u >> 1) & 1, sz = u >> 2;
+        valid[u] = (sx <= two[0]) && (sy <= two[1]) && (sz <= two[2]);
+        const int cx = k0[0] + sx, cy = k0[1] + sy, cz = k0[2] + sz;
+        const int lx = sx ? 0 : a0[0], ly = sy ? 0 : a0[1], lz = sz ? 0 : a0[2];
+        const long long cell = ((long long)cz * m.ny + cy) * m.nx + cx;
+        base[u] = valid[u] ? (cell * m.ne + (lz * m.np1 + ly) * m.np1 + lx) * ldy : 0;
+    }
+    int ecount = 0;
+    long long e0 = 0;
+    if (node_ptr) {
+        e0 = node_ptr[n];
+        ecount = (int)(node_ptr[n + 1] - e0);
+    }
+    float4 acc[2];
+    for (int t = 0; t < 2; ++t) {
+        const int j = 4 * lane + 128 * t;
+        acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < ldz) {
+            float4 y[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) y[u] = valid[u] ? f4(Yc + base[u] + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) { acc[t].x += y[u].x; acc[t].y += y[u].y; acc[t].z += y[u].z; acc[t].w += y[u].w; }
+        }
+    }
+    for (int c0 = 0; c0 < ecount; c0 += 32) {
+        int myI = 0;
+        float4 myh = make_float4(0.f, 0.f, 0.f, 0.f), myp = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c0 + lane < ecount) {
+            const int g = node_ent[e0 + c0 + lane];
+            myI = ent_atom[g];
+            if (use_h) myh = f4(Hca + 4 * (long long)g);
+            if (use_p) myp = f4(Pc + 4 * (long long)g);
+        }
+        const int cnt = min(32, ecount - c0);
+        for (int k = 0; k < cnt; ++k) {
+            const int I = __shfl_sync(0xffffffffu, myI, k);
+            const float h0 = __shfl_sync(0xffffffffu, myh.x, k), h1 = __shfl_sync(0xffffffffu, myh.y, k);
+            const float h2 = __shfl_sync(0xffffffffu, myh.z, k), h3 = __shfl_sync(0xffffffffu, myh.w, k);
+            const float p0 = __shfl_sync(0xffffffffu, myp.x, k), p1 = __shfl_sync(0xffffffffu, myp.y, k);
+            const float p2 = __shfl_sync(0xffffffffu, myp.z, k), p3 = __shfl_sync(0xffffffffu, myp.w, k);
+            for (int t = 0; t < 2; ++t) {
+                const int j = 4 * lane + 128 * t;
+                if (j >= ldz) continue;
+                if (use_h) {
+                    fma4(acc[t], h0, f4(Ye + (size_t)(4 * I + 0) * lde + j));
+                    fma4(acc[t], h1, f4(Ye + (size_t)(4 * I + 1) * lde + j));
+                    fma4(acc[t], h2, f4(Ye + (size_t)(4 * I + 2) * lde + j));
+                    fma4(acc[t], h3, f4(Ye + (size_t)(4 * I + 3) * lde + j));
                 }
-                nb = 0;
-                for (int a2 = 0; a2 < cc[2]; ++a2)
-                    for (int b2 = 0; b2 < cc[1]; ++b2)
-                        for (int c2 = 0; c2 < cc[0]; ++c2) {
-                            const long long cell = ((long long)cv[2][a2] * m.ny + cv[1][b2]) * m.nx + cv[0][c2];
-                            const int l = (av[2][a2] * m.np1 + av[1][b2]) * m.np1 + av[0][c2];
-                            s_base[threadIdx.x][nb++] = (cell * m.ne + l) * ldy;
-                        }
-                if (node_ptr) {
-                    e0 = node_ptr[n];
-                    cnt = (int)(node_ptr[n + 1] - e0);
+                if (use_p) {
+                    fma4(acc[t], p0, f4(W + (size_t)(4 * I + 0) * lde + j));
+                    fma4(acc[t], p1, f4(W + (size_t)(4 * I + 1) * lde + j));
+                    fma4(acc[t], p2, f4(W + (size_t)(4 * I + 2) * lde + j));
+                    fma4(acc[t], p3, f4(W + (size_t)(4 * I + 3) * lde + j));
                 }
             }
         }
-        s_nb[threadIdx.x] = nb;
-        s_e0[threadIdx.x] = e0;
-        s_cnt[threadIdx.x] = cnt;
     }
-    __syncthreads();
-    const int ln = threadIdx.x / ncg, cg = threadIdx.x - ln * ncg;
-    const long long n = nbase + ln;
-    if (ln >= npb || n >= nn) return;
-    const int j = 4 * cg;
-    const size_t row = (size_t)n * ldz;
-    const int nb = s_nb[ln];
-    if (nb < 0) {                       // Dirichlet node: held at zero
-        *reinterpret_cast<float4 *>(Zn + row + j) = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
+    for (int t = 0; t < 2; ++t) {
+        const int j = 4 * lane + 128 * t;
+        if (j >= ldz) continue;
+        const float4 z1 = f4(Z1 + row + j);
+        const float4 z0 = Z0 ? f4(Z0 + row + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 gg = f4(G + row + j);
+        const float4 kk = f4(ck + j);
+        float4 zn;
+        zn.x = a * (acc[t].x - c * z1.x) - b * z0.x + a * gg.x * kk.x;
+        zn.y = a * (acc[t].y - c * z1.y) - b * z0.y + a * gg.y * kk.y;
+        zn.z = a * (acc[t].z - c * z1.z) - b * z0.z + a * gg.z * kk.z;
+        zn.w = a * (acc[t].w - c * z1.w) - b * z0.w + a * gg.w * kk.w;
+        *reinterpret_cast<float4 *>(Zn + row + j) = zn;
+        if (ecount > 0) *reinterpret_cast<float4 *>(HYs + row + j) = acc[t];
     }
-    float4 y[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) y[u] = (u < nb) ? f4(Yc + s_base[ln][u] + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) { acc.x += y[u].x; acc.y += y[u].y; acc.z += y[u].z; acc.w += y[u].w; }
-    const long long e0 = s_e0[ln];
-    const int cnt = s_cnt[ln];
-    for (int k = 0; k < cnt; ++k) {
-        const int g = node_ent[e0 + k];
-        const int I = ent_atom[g];
-        if (use_h) {
-            const float4 h = f4(Hca + 4 * (long long)g);
-            fma4(acc, h.x, f4(Ye + (size_t)(4 * I + 0) * lde + j));
-            fma4(acc, h.y, f4(Ye + (size_t)(4 * I + 1) * lde + j));
-            fma4(acc, h.z, f4(Ye + (size_t)(4 * I + 2) * lde + j));
-            fma4(acc, h.w, f4(Ye + (size_t)(4 * I + 3) * lde + j));
+}
+
+// Warp-run forms of the two node kernels: a warp takes a run of kRun
+// consecutive nodes along x (same iy, iz), so the y/z part of the cell
+// indexing is formed once per warp, and walks the run's rows as one flat list
+// of float4 column groups (lane l takes groups l, l + 32, ...), so no lane
+// idles when the row length is not a multiple of 128 floats.
+constexpr int kRun = 8;
+
+struct AxisCells {
+    int k0, a0, two;   // the node lies in cell k0 at local index a0 (and in k0 + 1 at 0 if two)
+};
+__device__ __forceinline__ AxisCells axis_cells(int i, int p, int nc) {
+    const int q = i / p, r = i - q * p;
+    AxisCells a;
+    if (r != 0) { a.k0 = q; a.a0 = r; a.two = 0; }
+    else if (q > 0) { a.k0 = q - 1; a.a0 = p; a.two = q < nc ? 1 : 0; }
+    else { a.k0 = q; a.a0 = 0; a.two = 0; }
+    return a;
+}
+
+// Xb[n][4q..4q+3] = bf16( minv[n] Z[n] - sum_e C_e . Ye[atom(e)] ) (ldb >= ldz, padding zero)
+__global__ void __launch_bounds__(256) k_pre_bf16_w(MeshDev m, int nruns_x, const float *Z, int ldz, const float *Ye,
+                                                    int lde, int ldb, const double *minv, const long long *node_ptr,
+                                                    const int *node_ent, const int *ent_atom, const float *C,
+                                                    int use_c, __nv_bfloat16 *Xb) {
+    const int lane = threadIdx.x & 31;
+    const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nrows = (long long)m.Gy * m.Gz;
+    if (wid >= nrows * nruns_x) return;
+    const int xr = (int)(wid % nruns_x);
+    const long long yz = wid / nruns_x;
+    const int iy = (int)(yz % m.Gy), iz = (int)(yz / m.Gy);
+    const int x0 = xr * kRun;
+    const int nrun = min(kRun, m.Gx - x0);
+    const bool yz_in = iy > 0 && iz > 0 && iy < m.Gy - 1 && iz < m.Gz - 1;
+    const long long n0 = yz * m.Gx + x0;
+    const int ncg = ldb / 4;
+    int k = 0, cg = lane;
+    while (cg >= ncg) { cg -= ncg; ++k; }
+    for (; k < nrun;) {
+        const int ix = x0 + k;
+        const long long n = n0 + k;
+        const int j = 4 * cg;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (yz_in && ix > 0 && ix < m.Gx - 1 && j < ldz) {
+            const float mi = (float)minv[n];
+            v = f4(Z + (size_t)n * ldz + j);
+            v.x *= mi; v.y *= mi; v.z *= mi; v.w *= mi;
+            if (use_c) {
+                const long long e0 = node_ptr[n], e1 = node_ptr[n + 1];
+                for (long long e = e0; e < e1; ++e) {
+                    const int g = node_ent[e];
+                    const float4 cc = f4(C + 4 * (long long)g);
+                    const float *yb = Ye + (4 * ent_atom[g]) * lde + j;
+                    fma4(v, -cc.x, f4(yb));
+                    fma4(v, -cc.y, f4(yb + lde));
+                    fma4(v, -cc.z, f4(yb + 2 * lde));
+                    fma4(v, -cc.w, f4(yb + 3 * lde));
+                }
+            }
         }
-        if (use_p) {
-            const float4 pp = f4(Pc + 4 * (long long)g);
-            fma4(acc, pp.x, f4(W + (size_t)(4 * I + 0) * lde + j));
-            fma4(acc, pp.y, f4(W + (size_t)(4 * I + 1) * lde + j));
-            fma4(acc, pp.z, f4(W + (size_t)(4 * I + 2) * lde + j));
-            fma4(acc, pp.w, f4(W + (size_t)(4 * I + 3) * lde + j));
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+        uint2 pk;
+        pk.x = *reinterpret_cast<uint32_t *>(&lo);
+        pk.y = *reinterpret_cast<uint32_t *>(&hi);
+        *reinterpret_cast<uint2 *>(Xb + (size_t)n * ldb + j) = pk;
+        cg += 32;
+        while (cg >= ncg) { cg -= ncg; ++k; }
+    }
+}
+
+// The recurrence step at the FE nodes of a run (see k_gather_rec_v).
+__global__ void __launch_bounds__(256) k_gather_rec_w(MeshDev m, int nruns_x, int ldz, const float *Yc, int ldy,
+                                                      const long long *node_ptr, const int *node_ent,
+                                                      const int *ent_atom, const float *Hca, const float *Pc,
+                                                      const float *Ye, const float *W, int lde, int use_h, int use_p,
+                                                      const float *Z1, const float *Z0, const float *G,
+                                                      const float *ck, float a, float c, float b, float *Zn,
+                                                      float *HYs) {
+    const int lane = threadIdx.x & 31;
+    const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nrows = (long long)m.Gy * m.Gz;
+    if (wid >= nrows * nruns_x) return;
+    const int xr = (int)(wid % nruns_x);
+    const long long yz = wid / nruns_x;
+    const int iy = (int)(yz % m.Gy), iz = (int)(yz / m.Gy);
+    const int x0 = xr * kRun;
+    const int nrun = min(kRun, m.Gx - x0);
+    const bool yz_in = iy > 0 && iz > 0 && iy < m.Gy - 1 && iz < m.Gz - 1;
+    const long long n0 = yz * m.Gx + x0;
+    // y/z part of the cell rows: cell index (without x) and local offset (without x)
+    long long cyz[4];
+    int lyz[4];
+    bool vyz[4];
+    {
+        const AxisCells ay = axis_cells(iy, m.p, m.ny), az = axis_cells(iz, m.p, m.nz);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int sy = t & 1, sz = t >> 1;
+            vyz[t] = (sy <= ay.two) && (sz <= az.two);
+            const int cy = ay.k0 + sy, cz = az.k0 + sz;
+            const int ly = sy ? 0 : ay.a0, lz = sz ? 0 : az.a0;
+            cyz[t] = ((long long)cz * m.ny + cy) * m.nx;
+            lyz[t] = (lz * m.np1 + ly) * m.np1;
         }
     }
-    const float4 z1 = f4(Z1 + row + j);
-    const float4 z0 = Z0 ? f4(Z0 + row + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 gg = f4(G + row + j);
-    const float4 kk = f4(ck + j);
-    float4 zn;
-    zn.x = a * (acc.x - c * z1.x) - b * z0.x + a * gg.x * kk.x;
-    zn.y = a * (acc.y - c * z1.y) - b * z0.y + a * gg.y * kk.y;
-    zn.z = a * (acc.z - c * z1.z) - b * z0.z + a * gg.z * kk.z;
-    zn.w = a * (acc.w - c * z1.w) - b * z0.w + a * gg.w * kk.w;
-    *reinterpret_cast<float4 *>(Zn + row + j) = zn;
-    if (cnt > 0) *reinterpret_cast<float4 *>(HYs + row + j) = acc;
+    const int ncg = ldz / 4;
+    int k = 0, cg = lane;
+    while (cg >= ncg) { cg -= ncg; ++k; }
+    for (; k < nrun;) {
+        const int ix = x0 + k;
+        const long long n = n0 + k;
+        const int j = 4 * cg;
+        const size_t row = (size_t)n * ldz + j;
+        if (!(yz_in && ix > 0 && ix < m.Gx - 1)) {
+            *reinterpret_cast<float4 *>(Zn + row) = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            const AxisCells ax = axis_cells(ix, m.p, m.nx);
+            float4 y[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int sx = u & 1, t = u >> 1;
+                const bool ok = vyz[t] && (sx <= ax.two);
+                const long long cell = cyz[t] + ax.k0 + sx;
+                const int l = lyz[t] + (sx ? 0 : ax.a0);
+                y[u] = ok ? f4(Yc + (cell * m.ne + l) * ldy + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            const float4 z1 = f4(Z1 + row);
+            const float4 z0 = Z0 ? f4(Z0 + row) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 gg = f4(G + row);
+            const float4 kk = f4(ck + j);
+            // u = 4 sz + 2 sy + sx: the cells in the order z, y, x (outer to inner)
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) { acc.x += y[u].x; acc.y += y[u].y; acc.z += y[u].z; acc.w += y[u].w; }
+            int cnt = 0;
+            if (node_ptr) {
+                const long long e0 = node_ptr[n], e1 = node_ptr[n + 1];
+                cnt = (int)(e1 - e0);
+                for (long long e = e0; e < e1; ++e) {
+                    const int g = node_ent[e];
+                    const int rb = (4 * ent_atom[g]) * lde + j;
+                    if (use_h) {
+                        const float4 h = f4(Hca + 4 * (long long)g);
+                        const float *yb = Ye + rb;
+                        fma4(acc, h.x, f4(yb));
+                        fma4(acc, h.y, f4(yb + lde));
+                        fma4(acc, h.z, f4(yb + 2 * lde));
+                        fma4(acc, h.w, f4(yb + 3 * lde));
+                    }
+                    if (use_p) {
+                        const float4 pp = f4(Pc + 4 * (long long)g);
+                        const float *wb = W + rb;
+                        fma4(acc, pp.x, f4(wb));
+                        fma4(acc, pp.y, f4(wb + lde));
+                        fma4(acc, pp.z, f4(wb + 2 * lde));
+                        fma4(acc, pp.w, f4(wb + 3 * lde));
+                    }
+                }
+            }
+            float4 zn;
+            zn.x = a * (acc.x - c * z1.x) - b * z0.x + a * gg.x * kk.x;
+            zn.y = a * (acc.y - c * z1.y) - b * z0.y + a * gg.y * kk.y;
+            zn.z = a * (acc.z - c * z1.z) - b * z0.z + a * gg.z * kk.z;
+            zn.w = a * (acc.w - c * z1.w) - b * z0.w + a * gg.w * kk.w;
+            *reinterpret_cast<float4 *>(Zn + row) = zn;
+            if (cnt > 0) *reinterpret_cast<float4 *>(HYs + row) = acc;
+        }
+        cg += 32;
+        while (cg >= ncg) { cg -= ncg; ++k; }
+    }
 }
 
 // Support reduction: warps over positions (8 rows in flight per warp), lanes
@@ -584,10 +759,18 @@ __global__ void __launch_bounds__(256) k_support_reduce3(const long long *sup_of
     for (int i = 0; i < 8; ++i) r[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (pl < npl) {
         const int j = 4 * cg;
+        // the node indices of the next group are loaded one iteration ahead, so
+        // each iteration waits on one dependent load (the rows) instead of two
+        int nxt[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) nxt[u] = (beg + 4 * pl + u < end) ? sup_node[beg + 4 * pl + u] : -1;
         for (long long g0 = beg + 4 * pl; g0 < end; g0 += 4 * npl) {
             int nodes[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) nodes[u] = (g0 + u < end) ? sup_node[g0 + u] : -1;
+            for (int u = 0; u < 4; ++u) nodes[u] = nxt[u];
+            const long long g1 = g0 + 4 * npl;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) nxt[u] = (g1 + u < end) ? sup_node[g1 + u] : -1;
             float4 sv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -1339,8 +1522,8 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     HxScratch s{};
     if (cpl) EFE_TRY(hx_scratch(ctx, N, s));
     const unsigned rb_all = (unsigned)((rows + 7) / 8);
-    const int npb_b = row_npb(ldb / 4), npb_z = row_npb(ldz / 4);
-    const unsigned gpre = (unsigned)((nn + npb_b - 1) / npb_b), ggat = (unsigned)((nn + npb_z - 1) / npb_z);
+    const int nruns_x = (mh.Gx + kRun - 1) / kRun;                   // runs of kRun nodes along x
+    const unsigned rb_run = (unsigned)(((long long)mh.Gy * mh.Gz * nruns_x + 7) / 8);   // 8 warps per block
     ctx->cell_events_used = 0;
     ctx->rec_events_used = 0;
     ctx->cell_launches = 0;
@@ -1363,11 +1546,11 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
                                                                                 Zcur + nn * ldz, Ye, lde);
             ctx->launches++;
         }
-        k_pre_bf16_f<<<gpre, npb_b * (ldb / 4), 0, ctx->stream>>>(mh, (int)nn, npb_b, Zcur, ldz, Ye, lde, ldb,
-                                                                 ctx->d_minv, ctx->d_node_ptr, ctx->d_node_ent,
-                                                                 ctx->d_ent_atom, ctx->d_C32, ctx->enrich ? 1 : 0, Xb);
+        k_pre_bf16_w<<<rb_run, 256, 0, ctx->stream>>>(mh, nruns_x, Zcur, ldz, Ye, lde, ldb, ctx->d_minv,
+                                                      ctx->d_node_ptr, ctx->d_node_ent, ctx->d_ent_atom, ctx->d_C32,
+                                                      ctx->enrich ? 1 : 0, Xb);
         ctx->launches++;
-        EFE_TRY(efe_check_launch(ctx, "k_pre_bf16_f"));
+        EFE_TRY(efe_check_launch(ctx, "k_pre_bf16_w"));
         {
             auto *ev = cell_event_pair(ctx);
             if (ev) cudaEventRecord(ev->first, ctx->stream);
@@ -1399,13 +1582,14 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
         }
         auto *rev = rec_event_pair(ctx);
         if (rev) cudaEventRecord(rev->first, ctx->stream);
-        k_gather_rec_f<<<ggat, npb_z * (ldz / 4), 0, ctx->stream>>>(
-            mh, (int)nn, npb_z, ldz, Ycells, ldy, cpl ? ctx->d_node_ptr : nullptr, ctx->d_node_ent, ctx->d_ent_atom,
-            ctx->d_Hca32, ctx->d_Pc32, Ye, W32, lde, ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0, Zcur, Zprev, G,
-            fck + (size_t)(k - 1) * ldz, ak, cf, bk, Znext, HYs);
+        k_gather_rec_w<<<rb_run, 256, 0, ctx->stream>>>(mh, nruns_x, ldz, Ycells, ldy, cpl ? ctx->d_node_ptr : nullptr,
+                                                        ctx->d_node_ent, ctx->d_ent_atom, ctx->d_Hca32, ctx->d_Pc32,
+                                                        Ye, W32, lde, ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0,
+                                                        Zcur, Zprev, G, fck + (size_t)(k - 1) * ldz, ak, cf, bk,
+                                                        Znext, HYs);
         if (rev) cudaEventRecord(rev->second, ctx->stream);
         ctx->launches++;
-        EFE_TRY(efe_check_launch(ctx, "k_gather_rec_f"));
+        EFE_TRY(efe_check_launch(ctx, "k_gather_rec_w"));
         if (ne_) {
             k_support_reduce3<float><<<gred, 256, 0, ctx->stream>>>(ctx->d_sup_off, ctx->d_sup_node, ctx->d_C32,
                                                                     nullptr, HYs, N, ldz, s.chunk, s.nch, s.part);
@@ -1649,7 +1833,7 @@ void efe_destroy(efe_ctx *ctx) {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     efe_scf_free(ctx);
-    void *ptrs[] = {ctx->d_B1, ctx->d_D1, ctx->d_wq, ctx->d_Khat, ctx->d_mcc, ctx->d_minv, ctx->d_He, ctx->d_He32,
+    void *ptrs[] = {ctx->d_hostio, ctx->d_B1, ctx->d_D1, ctx->d_wq, ctx->d_Khat, ctx->d_mcc, ctx->d_minv, ctx->d_He, ctx->d_He32,
                     ctx->d_He16, ctx->d_atoms, ctx->d_hproj, ctx->d_sup_off, ctx->d_sup_node, ctx->d_C, ctx->d_B,
                     ctx->d_Kca, ctx->d_Hca, ctx->d_Pc, ctx->d_C32, ctx->d_Hca32, ctx->d_Pc32, ctx->d_node_ptr,
                     ctx->d_node_ent, ctx->d_ent_atom,
@@ -1982,18 +2166,18 @@ efe_status efe_filter_host(efe_ctx *ctx, const double *V, const double *HV, cons
     EFE_CHECK_CTX(ctx);
     EFE_ARG(ctx, V && HV && lam && bounds && Vout && N > 0 && m >= 1, "efe_filter_host: bad arguments");
     const long long n = ctx->n_rows * N;
-    double *dV = nullptr, *dHV = nullptr, *dO = nullptr, *dl = nullptr;
-    std::vector<void *> owned;
-    auto cleanup = [&]() {
-        cudaStreamSynchronize(ctx->stream);
-        for (void *p : owned) cudaFree(p);
-    };
-    for (double **p : {&dV, &dHV, &dO}) {
-        if (efe_alloc(ctx, (void **)p, sizeof(double) * n) != EFE_OK) { cleanup(); return EFE_ERR_OOM; }
-        owned.push_back(*p);
+    // device copies of V, HV, Vout and lam, kept by the context between calls
+    const size_t need = sizeof(double) * (3 * (size_t)n + (size_t)N) + 256;
+    if (need > ctx->hostio_bytes) {
+        EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (ctx->d_hostio) cudaFree(ctx->d_hostio);
+        ctx->d_hostio = nullptr;
+        ctx->hostio_bytes = 0;
+        EFE_TRY(efe_alloc(ctx, &ctx->d_hostio, need));
+        ctx->hostio_bytes = need;
     }
-    if (efe_alloc(ctx, (void **)&dl, sizeof(double) * N) != EFE_OK) { cleanup(); return EFE_ERR_OOM; }
-    owned.push_back(dl);
+    double *dV = static_cast<double *>(ctx->d_hostio), *dHV = dV + n, *dO = dHV + n, *dl = dO + n;
+    auto cleanup = [&]() { cudaStreamSynchronize(ctx->stream); };
     efe_status st = EFE_OK;
     if (cudaMemcpyAsync(dV, V, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
         cudaMemcpyAsync(dHV, HV, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||

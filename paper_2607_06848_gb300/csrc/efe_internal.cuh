@@ -108,6 +108,9 @@ struct efe_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> rec_events;
     size_t rec_events_used = 0;
     long long n_support_nodes = 0;
+    // device copies for the host-buffer filter (grown on demand, kept)
+    void *d_hostio = nullptr;
+    size_t hostio_bytes = 0;
     long long cell_launches = 0;
 };
 

@@ -113,17 +113,24 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-    uint32_t r[16];
+// TMEM -> registers, 16 consecutive columns of the warp's 32 lanes (rows)
+// (no wait: several are issued, then one tmem_wait_ld())
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t r[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
         "%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// ties the registers of a load to a point after tmem_wait_ld(), so that no use
+// of them is scheduled before the wait
+__device__ __forceinline__ void reg_after_wait(uint32_t r[16]) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]));
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -267,14 +274,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int row = mt * 128 + q * 32 + lane;
                 float *dst = Ycells + ((size_t)cell * P.ne + row) * P.ldy + P.col0;
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * P.Npad);
-                for (int c = 0; c < P.Npad; c += 16) {
-                    float v[16];
-                    tmem_ld16(tbase + (uint32_t)c, v);
-                    if (row < P.ne) {
+                // up to 64 columns per TMEM round trip: four loads, one wait
+                for (int c = 0; c < P.Npad; c += 64) {
+                    const int ng = min(4, (P.Npad - c) / 16);        // warp-uniform
+                    uint32_t r[4][16];
 #pragma unroll
-                        for (int i = 0; i < 16; i += 4)
-                            if (P.col0 + c + i + 3 < P.ldy)
-                                *reinterpret_cast<float4 *>(dst + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                    for (int g = 0; g < 4; ++g)
+                        if (g < ng) tmem_ld16_nw(tbase + (uint32_t)(c + 16 * g), r[g]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        if (g >= ng) continue;
+                        reg_after_wait(r[g]);
+                        if (row < P.ne) {
+                            const int cc = c + 16 * g;
+#pragma unroll
+                            for (int i = 0; i < 16; i += 4)
+                                if (P.col0 + cc + i + 3 < P.ldy)
+                                    *reinterpret_cast<float4 *>(dst + cc + i) =
+                                        make_float4(__uint_as_float(r[g][i]), __uint_as_float(r[g][i + 1]),
+                                                    __uint_as_float(r[g][i + 2]), __uint_as_float(r[g][i + 3]));
+                        }
                     }
                 }
                 fence_before();

@@ -976,6 +976,60 @@ efe_status efe_fit_correction(efe_ctx *ctx, const double *rho_q, const double *b
     return EFE_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// rho_q <- max(rho_sup + drho(c), 0) scaled to N_e, rho_sup already in rho_q;
+// c (natoms x 8, float or double) in the orthonormal basis.  *ok = false (rho_q
+// untouched) when the corrected density is not finite or has no charge.
+template <typename T>
+efe_status corrected_density(efe_ctx *ctx, const T *c, double *rho_q, bool *ok) {
+    *ok = false;
+    const int na = ctx->natoms;
+    const long long nq = ctx->n_quad;
+    Scratch sc(ctx->stream);
+    double *ceff = sc.get<double>((size_t)na * NO);
+    double *rho = sc.get<double>(nq);
+    if (!ceff || !rho) return EFE_ERR_OOM;
+    const Basis B = make_basis();
+    k_coeff_raw<T><<<nbl((long long)na * NO, 128), 128, 0, ctx->stream>>>(na, B, c, ceff);
+    EFE_TRY(efe_check_launch(ctx, "k_coeff_raw"));
+    const long long ncell = (long long)ctx->m.nx * ctx->m.ny * ctx->m.nz;
+    k_correction<<<(unsigned)ncell, kCorrThreads, 0, ctx->stream>>>(ctx->m, make_tables(ctx), B, na, ctx->d_atoms,
+                                                                  ceff, rho);
+    EFE_TRY(efe_check_launch(ctx, "k_correction"));
+    k_clip_sum<<<nbl(nq, 256), 256, 0, ctx->stream>>>(nq, rho_q, rho, rho);
+    double tot = 0.0;
+    EFE_TRY(efe_integrate(ctx, rho, nullptr, &tot));
+    double ne = 0.0;
+    for (double z : ctx->zval) ne += z;
+    if (!std::isfinite(tot) || !(tot > 0.0)) return EFE_OK;      // the superposition stays in rho_q
+    k_scale_into<<<nbl(nq, 256), 256, 0, ctx->stream>>>(nq, ne / tot, rho, rho_q);
+    EFE_TRY(efe_check_launch(ctx, "k_scale_into"));
+    EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *ok = true;
+    return EFE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+efe_status efe_corrected_density(efe_ctx *ctx, const double *c, double kappa, double *rho_q, int *fallback) {
+    if (!ctx) return EFE_ERR_ARG;
+    if (!c || !rho_q || !(kappa > 0.0)) {
+        ctx->err = "efe_corrected_density: null pointer or kappa <= 0";
+        return EFE_ERR_ARG;
+    }
+    if (fallback) *fallback = 1;
+    EFE_TRY(efe_atomic_density(ctx, kappa, rho_q));
+    bool ok = false;
+    EFE_TRY(corrected_density<double>(ctx, c, rho_q, &ok));
+    if (fallback) *fallback = ok ? 0 : 1;
+    return EFE_OK;
+}
+
 efe_status efe_warm_start(efe_ctx *ctx, efe_mlp *mlp, const float *theta, double kappa, double *rho_q,
                           int *fallback) {
     if (!ctx) return EFE_ERR_ARG;
@@ -987,42 +1041,24 @@ efe_status efe_warm_start(efe_ctx *ctx, efe_mlp *mlp, const float *theta, double
     EFE_TRY(efe_atomic_density(ctx, kappa, rho_q));
     if (!theta) return EFE_OK;
     const int na = ctx->natoms;
-    const long long nq = ctx->n_quad;
     Scratch sc(ctx->stream);
     double *dz = sc.get<double>(na);
     float *D = sc.get<float>((size_t)na * ND);
     float *C = sc.get<float>((size_t)na * NO);
-    double *ceff = sc.get<double>((size_t)na * NO);
-    double *rho = sc.get<double>(nq);
-    if (!dz || !D || !C || !ceff || !rho) return EFE_ERR_OOM;
+    if (!dz || !D || !C) return EFE_ERR_OOM;
     EFE_CUDA(ctx, cudaMemcpyAsync(dz, ctx->zval.data(), sizeof(double) * na, cudaMemcpyHostToDevice, ctx->stream));
     k_descriptors<<<na, ND, 0, ctx->stream>>>(na, ctx->d_atoms, dz, D);
     EFE_TRY(efe_check_launch(ctx, "k_descriptors"));
-    {
-        static bool attr = false;
-        if (!attr) {
-            EFE_CUDA(ctx, cudaFuncSetAttribute(k_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_BYTES));
-            attr = true;
-        }
-        k_mlp<<<nbl(na, MS), MT, SM_BYTES, ctx->stream>>>(theta, D, nullptr, na, C, nullptr, nullptr, nullptr);
-        EFE_TRY(efe_check_launch(ctx, "k_mlp"));
+    static bool attr = false;
+    if (!attr) {
+        EFE_CUDA(ctx, cudaFuncSetAttribute(k_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_BYTES));
+        attr = true;
     }
-    const Basis B = make_basis();
-    k_coeff_raw<float><<<nbl((long long)na * NO, 128), 128, 0, ctx->stream>>>(na, B, C, ceff);
-    EFE_TRY(efe_check_launch(ctx, "k_coeff_raw"));
-    const long long ncell = (long long)ctx->m.nx * ctx->m.ny * ctx->m.nz;
-    k_correction<<<(unsigned)ncell, kCorrThreads, 0, ctx->stream>>>(ctx->m, make_tables(ctx), B, na, ctx->d_atoms, ceff, rho);
-    EFE_TRY(efe_check_launch(ctx, "k_correction"));
-    k_clip_sum<<<nbl(nq, 256), 256, 0, ctx->stream>>>(nq, rho_q, rho, rho);
-    double tot = 0.0;
-    EFE_TRY(efe_integrate(ctx, rho, nullptr, &tot));
-    double ne = 0.0;
-    for (double z : ctx->zval) ne += z;
-    if (!std::isfinite(tot) || !(tot > 0.0)) return EFE_OK;      // the superposition stays in rho_q
-    k_scale_into<<<nbl(nq, 256), 256, 0, ctx->stream>>>(nq, ne / tot, rho, rho_q);
-    EFE_TRY(efe_check_launch(ctx, "k_scale_into"));
-    EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (fallback) *fallback = 0;
+    k_mlp<<<nbl(na, MS), MT, SM_BYTES, ctx->stream>>>(theta, D, nullptr, na, C, nullptr, nullptr, nullptr);
+    EFE_TRY(efe_check_launch(ctx, "k_mlp"));
+    bool ok = false;
+    EFE_TRY(corrected_density<float>(ctx, C, rho_q, &ok));
+    if (fallback) *fallback = ok ? 0 : 1;
     return EFE_OK;
 }
 

@@ -113,6 +113,7 @@ SIGNATURES = {
     "efe_mlp_load": [_P, ctypes.c_char_p, _P],
     "efe_density_correction": [_P, _P, _P],
     "efe_fit_correction": [_P, _P, _P, ctypes.c_double, _P],
+    "efe_corrected_density": [_P, _P, ctypes.c_double, _P, ctypes.POINTER(_I)],
     "efe_warm_start": [_P, _P, _P, ctypes.c_double, _P, ctypes.POINTER(_I)],
 }
 
@@ -259,12 +260,16 @@ class EFE:
             self._check(st)
         return np.array(eig[:]), np.array(res[:]), passes.value, st == 0
 
-    def efe_filter_host(self, V, HV, lam, m, bounds, prec=EFE_FP64):
-        """Host arrays in and out (the library copies on its stream)."""
+    def efe_filter_host(self, V, HV, lam, m, bounds, prec=EFE_FP64, out=None):
+        """Host arrays in and out (the library copies on its stream); out: an optional
+        caller-owned (e.g. pinned) host array for V_out."""
         V = np.ascontiguousarray(V, dtype=np.float64)
         HV = np.ascontiguousarray(HV, dtype=np.float64)
         lam = np.ascontiguousarray(lam, dtype=np.float64)
-        out = np.empty_like(V)
+        if out is None:
+            out = np.empty_like(V)
+        if out.shape != V.shape or out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a C-contiguous float64 array shaped like V")
         b = (ctypes.c_double * 3)(*[float(x) for x in bounds])
         self._check(self.lib.efe_filter_host(self.ctx, V.ctypes.data_as(_D), HV.ctypes.data_as(_D),
                                              lam.ctypes.data_as(_D), V.shape[1], int(m), b, int(prec),
@@ -344,6 +349,12 @@ class EFE:
 
     def efe_fit_correction(self, rho_q, c, base_q=None, ridge=1e-3):
         self._check(self.lib.efe_fit_correction(self.ctx, _ptr(rho_q), _ptr(base_q), float(ridge), _ptr(c)))
+
+    def efe_corrected_density(self, c, rho_q, kappa=2.4):
+        """Returns True when rho_q holds the superposition (fallback)."""
+        fb = ctypes.c_int(1)
+        self._check(self.lib.efe_corrected_density(self.ctx, _ptr(c), float(kappa), _ptr(rho_q), ctypes.byref(fb)))
+        return bool(fb.value)
 
     def efe_warm_start(self, mlp, theta, rho_q, kappa=2.4):
         """Returns True when rho_q holds the superposition (no network or fallback)."""

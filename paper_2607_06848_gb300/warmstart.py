@@ -2,8 +2,9 @@
 
 Orchestration only: every computation is a libefe call (efe_scf,
 efe_atomic_density, efe_fit_correction, efe_descriptors, efe_mlp_normalise,
-efe_mlp_train, efe_warm_start); this module loops over clusters and moves
-arrays between them.
+efe_mlp_train, efe_warm_start, efe_corrected_density); this module loops over
+clusters and moves arrays between them (the start-error diagnostics subtract
+two densities with torch).
 
   data      each training cluster is converged by the plain SCF (atomic
             superposition start); the least-squares coefficients of
@@ -12,8 +13,10 @@ arrays between them.
   train     full-batch Adam on all atoms of all training clusters
   evaluate  each held-out cluster is converged twice from the same start
             vectors -- from the superposition and from the learned density --
-            and, as a control, from the superposition plus the training set's
-            mean correction (the network with its output layer zeroed)
+            and, as controls, from the superposition plus the training set's
+            mean correction (the network with its output layer zeroed) and
+            from the best density this correction basis can give (coefficients
+            fitted to the converged density itself)
 
 Usage: python -m paper_2607_06848_gb300.warmstart [--train 40] [--train-atoms 8 16]
        [--heldout 6] [--heldout-atoms 24] [--steps 3000] [--precision fp64]
@@ -34,6 +37,7 @@ ENRICH = dict(alpha=1.2, r_end=5.0, t=0.33)
 # states stall near 1e-7 with one filter pass per iteration)
 TRAIN_SCF = dict(tol_rho=1e-6, tol_e=1e-7, max_iter=100)
 EVAL_SCF = dict(tol_rho=1e-7, tol_e=1e-7, max_iter=100)
+STARTS = ("superposition", "mean_correction", "learned", "best_fit")
 
 
 def _system(w):
@@ -53,7 +57,7 @@ def converge(w, rho0=None, precision="fp64", seed=1, g=None, **opts):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     r = g.efe_scf(X, u0, rho0_q=rho0, rho_out=rho, cheb_degree=w["cheb_degree"],
-                  precision=PRECISIONS[precision], **opts)
+                  precision=PRECISIONS[precision], log=lambda h: None, **opts)
     torch.cuda.synchronize()
     r["seconds"] = time.perf_counter() - t0
     r["rho"] = rho
@@ -100,22 +104,50 @@ def mean_only(theta):
     return t
 
 
+def iters_to_energy(history, E_final, natoms, tol):
+    """First iteration from which the energy stays within tol Ha/atom of E_final."""
+    k = len(history)
+    for i in range(len(history) - 1, -1, -1):
+        if abs(history[i]["E"] - E_final) / natoms >= tol:
+            break
+        k = i
+    return history[k]["it"] if k < len(history) else None
+
+
 def evaluate(w, mlp, theta, precision="fp64"):
     """SCF iterations and energies from the superposition, the mean correction and the
-    learned density, plus each start density's L2 distance to the converged one."""
+    learned density, plus each start density's L2 distance to the converged one and
+    the iterations after which the energy stays within 1e-5 / 1e-6 Ha/atom of its
+    converged value."""
     import torch
     g = _system(w)
-    starts = {"superposition": None, "mean_correction": mean_only(theta), "learned": theta}
-    out = dict(name=w["name"], atoms=len(w["atoms"]))
+    n = len(w["atoms"])
+    out = dict(name=w["name"], atoms=n)
     dens = {}
-    for key, th in starts.items():
-        rho0 = torch.empty(g.dims["n_quad"], dtype=torch.float64, device="cuda")
-        fb = g.efe_warm_start(mlp if th is not None else None, th, rho0)
+    ref = None
+
+    def run(key, rho0, fb):
         r, _ = converge(w, rho0=rho0, precision=precision, g=g, **EVAL_SCF)
         dens[key] = rho0
         out[key] = dict(iters=r["iters"], converged=r["converged"], E=r["E"], seconds=r["seconds"],
-                        fallback=fb)
-        ref = r["rho"]
+                        fallback=fb, iters_E_1e5=iters_to_energy(r["history"], r["E"], n, 1e-5),
+                        iters_E_1e6=iters_to_energy(r["history"], r["E"], n, 1e-6),
+                        drho=[h["drho"] for h in r["history"]])
+        return r["rho"]
+
+    for key, th in (("superposition", None), ("mean_correction", mean_only(theta)), ("learned", theta)):
+        rho0 = torch.empty(g.dims["n_quad"], dtype=torch.float64, device="cuda")
+        fb = g.efe_warm_start(mlp if th is not None else None, th, rho0)
+        rho_scf = run(key, rho0, fb)
+        ref = rho_scf if ref is None else ref
+    # the ceiling of this correction basis: coefficients fitted to the converged density itself
+    sup = torch.empty_like(ref)
+    g.efe_atomic_density(2.4, sup)
+    c = torch.empty((n, 8), dtype=torch.float64, device="cuda")
+    g.efe_fit_correction(ref, c, base_q=sup, ridge=1e-6)
+    rho0 = torch.empty_like(ref)
+    fb = g.efe_corrected_density(c, rho0)
+    run("best_fit", rho0, fb)
     for key, rho0 in dens.items():
         d = rho0 - ref
         out[key]["start_error_L2"] = float(np.sqrt(max(g.efe_integrate(d, d), 0.0)))
@@ -160,13 +192,16 @@ def main(argv=None):
         fit=dict(steps=args.steps, lr=args.lr, seconds=t_train, loss_first=float(hist[0]),
                  loss_last=float(hist[-1])),
         heldout=dict(clusters=len(evals), atoms=args.heldout_atoms,
-                     iters=dict((k, mean(k, "iters")) for k in ("superposition", "mean_correction", "learned")),
+                     iters=dict((k, mean(k, "iters")) for k in STARTS),
+                     iters_E_1e5=dict((k, mean(k, "iters_E_1e5"))
+                                      for k in STARTS),
+                     iters_E_1e6=dict((k, mean(k, "iters_E_1e6"))
+                                      for k in STARTS),
                      start_error_L2=dict((k, mean(k, "start_error_L2"))
-                                         for k in ("superposition", "mean_correction", "learned")),
+                                         for k in STARTS),
                      max_dE_learned_vs_superposition_Ha_per_atom=float(max(
                          abs(e["learned"]["E"] - e["superposition"]["E"]) / e["atoms"] for e in evals)),
-                     all_converged=all(e[k]["converged"] for e in evals
-                                       for k in ("superposition", "mean_correction", "learned"))),
+                     all_converged=all(e[k]["converged"] for e in evals for k in STARTS)),
         precision=args.precision, per_cluster=evals)
     it_s = summary["heldout"]["iters"]["superposition"]
     it_l = summary["heldout"]["iters"]["learned"]

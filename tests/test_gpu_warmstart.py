@@ -186,6 +186,12 @@ def test_warm_start_matches_oracle_and_falls_back():
     assert np.max(np.abs(r - ro)) < 1e-5 * np.max(ro)
     assert np.max(np.abs(ro - sup)) > 1e-3 * np.max(sup)          # the correction is visible
     assert abs(g.efe_integrate(rho) - 24.0) < 1e-10 and np.all(r >= 0)
+    # the same density from explicit coefficients
+    c = np.random.default_rng(5).standard_normal((6, 8)) * 0.02
+    fb = g.efe_corrected_density(torch.tensor(c, device=DEV), rho)
+    ro, fbo = O.corrected_density(m, w["atoms"], w["Z"], c, rho_sup=sup)
+    assert not fb and not fbo
+    assert np.max(np.abs(rho.cpu().numpy() - ro)) < 1e-12 * np.max(ro)
     # no network: the superposition itself
     fb = g.efe_warm_start(None, None, rho)
     s2 = torch.empty_like(rho)
