@@ -359,13 +359,6 @@ __global__ void k_gather(MeshDev m, long long n_nodes, int N, const float *Yc, i
 // coordinates and coupling lists are read once per row, lanes run over the
 // columns).  All arithmetic is FP32; the values feed bf16 products.
 // ---------------------------------------------------------------------------
-__device__ inline void node_xyz(const MeshDev &m, int n, int &ix, int &iy, int &iz) {
-    ix = n % m.Gx;
-    const int t = n / m.Gx;
-    iy = t % m.Gy;
-    iz = t / m.Gy;
-}
-
 __global__ void k_to_float_strided(int rows, int N, const double *x, float *y, int ldy) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= rows * N) return;
@@ -380,183 +373,7 @@ __device__ inline void fma4(float4 &a, float s, const float4 b) {
     a.x += s * b.x; a.y += s * b.y; a.z += s * b.z; a.w += s * b.w;
 }
 
-// Xb[n][4q..4q+3] = bf16( minv[n] Z[n] - sum_e C_e . Ye[atom(e)] ) (ldb >= ldz, padding zero)
-__global__ void __launch_bounds__(256) k_pre_bf16_v(MeshDev m, int nn, const float *Z, int ldz, const float *Ye,
-                                                    int lde, int ldb, const double *minv, const long long *node_ptr,
-                                                    const int *node_ent, const int *ent_atom, const float *C,
-                                                    int use_c, __nv_bfloat16 *Xb) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = blockIdx.x * 8 + warp;
-    if (n >= nn) return;
-    int ix, iy, iz;
-    node_xyz(m, n, ix, iy, iz);
-    const bool inter = node_interior(m, ix, iy, iz);
-    const float mi = inter ? (float)minv[n] : 0.f;
-    int ecount = 0;
-    long long e0 = 0;
-    if (inter && use_c) {
-        e0 = node_ptr[n];
-        ecount = (int)(node_ptr[n + 1] - e0);
-    }
-    // this node's coupling entries, one per lane (chunks of 32), broadcast by shuffles
-    const float *zr = Z + (size_t)n * ldz;
-    __nv_bfloat16 *out = Xb + (size_t)n * ldb;
-    float4 v[2];
-    for (int t = 0; t < 2; ++t) {
-        const int j = 4 * lane + 128 * t;
-        v[t] = (inter && j < ldz) ? f4(zr + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-        v[t].x *= mi; v[t].y *= mi; v[t].z *= mi; v[t].w *= mi;
-    }
-    for (int c0 = 0; c0 < ecount; c0 += 32) {
-        int myI = 0;
-        float4 myc = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c0 + lane < ecount) {
-            const int g = node_ent[e0 + c0 + lane];
-            myI = ent_atom[g];
-            myc = f4(C + 4 * (long long)g);
-        }
-        const int cnt = min(32, ecount - c0);
-        for (int k = 0; k < cnt; ++k) {
-            const int I = __shfl_sync(0xffffffffu, myI, k);
-            const float cx = __shfl_sync(0xffffffffu, myc.x, k), cy = __shfl_sync(0xffffffffu, myc.y, k);
-            const float cz = __shfl_sync(0xffffffffu, myc.z, k), cw = __shfl_sync(0xffffffffu, myc.w, k);
-            for (int t = 0; t < 2; ++t) {
-                const int j = 4 * lane + 128 * t;
-                if (j < ldz) {
-                    fma4(v[t], -cx, f4(Ye + (size_t)(4 * I + 0) * lde + j));
-                    fma4(v[t], -cy, f4(Ye + (size_t)(4 * I + 1) * lde + j));
-                    fma4(v[t], -cz, f4(Ye + (size_t)(4 * I + 2) * lde + j));
-                    fma4(v[t], -cw, f4(Ye + (size_t)(4 * I + 3) * lde + j));
-                }
-            }
-        }
-    }
-    for (int t = 0; t < 2; ++t) {
-        const int j = 4 * lane + 128 * t;
-        if (j < ldb) {
-            __nv_bfloat162 lo = __floats2bfloat162_rn(v[t].x, v[t].y), hi = __floats2bfloat162_rn(v[t].z, v[t].w);
-            uint2 pk;
-            pk.x = *reinterpret_cast<uint32_t *>(&lo);
-            pk.y = *reinterpret_cast<uint32_t *>(&hi);
-            *reinterpret_cast<uint2 *>(out + j) = pk;
-        }
-    }
-}
-
-// Fused gather + coupling + FE-row recurrence on float4 columns (see k_gather_rec).
-__global__ void __launch_bounds__(256) k_gather_rec_v(MeshDev m, int nn, int ldz, const float *Yc, int ldy,
-                                                      const long long *node_ptr, const int *node_ent,
-                                                      const int *ent_atom, const float *Hca, const float *Pc,
-                                                      const float *Ye, const float *W, int lde, int use_h, int use_p,
-                                                      const float *Z1, const float *Z0, const float *G,
-                                                      const float *ck, float a, float c, float b, float *Zn,
-                                                      float *HYs) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = blockIdx.x * 8 + warp;
-    if (n >= nn) return;
-    int ix, iy, iz;
-    node_xyz(m, n, ix, iy, iz);
-    const size_t row = (size_t)n * ldz;
-    if (!node_interior(m, ix, iy, iz)) {
-        for (int j = 4 * lane; j < ldz; j += 128)
-            *reinterpret_cast<float4 *>(Zn + row + j) = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
-    // the (up to 8) cells holding this node, as scalars per axis so that the
-    // row offsets stay in registers: along each axis the node lies in cell k0
-    // at local index a0, and (on a cell face) also in cell k0 + 1 at index 0
-    int k0[3], a0[3], two[3];
-    {
-        const int ii[3] = {ix, iy, iz}, nc[3] = {m.nx, m.ny, m.nz};
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const int q = ii[d] / m.p, r = ii[d] - q * m.p;
-            if (r != 0) { k0[d] = q; a0[d] = r; two[d] = 0; }
-            else if (q > 0) { k0[d] = q - 1; a0[d] = m.p; two[d] = q < nc[d] ? 1 : 0; }
-            else { k0[d] = q; a0[d] = 0; two[d] = 0; }
-        }
-    }
-    long long base[8];
-    bool valid[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const int sx = u & 1, sy = (u >> 1) & 1, sz = u >> 2;
-        valid[u] = (sx <= two[0]) && (sy <= two[1]) && (sz <= two[2]);
-        const int cx = k0[0] + sx, cy = k0[1] + sy, cz = k0[2] + sz;
-        const int lx = sx ? 0 : a0[0], ly = sy ? 0 : a0[1], lz = sz ? 0 : a0[2];
-        const long long cell = ((long long)cz * m.ny + cy) * m.nx + cx;
-        base[u] = valid[u] ? (cell * m.ne + (lz * m.np1 + ly) * m.np1 + lx) * ldy : 0;
-    }
-    int ecount = 0;
-    long long e0 = 0;
-    if (node_ptr) {
-        e0 = node_ptr[n];
-        ecount = (int)(node_ptr[n + 1] - e0);
-    }
-    float4 acc[2];
-    for (int t = 0; t < 2; ++t) {
-        const int j = 4 * lane + 128 * t;
-        acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (j < ldz) {
-            float4 y[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) y[u] = valid[u] ? f4(Yc + base[u] + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) { acc[t].x += y[u].x; acc[t].y += y[u].y; acc[t].z += y[u].z; acc[t].w += y[u].w; }
-        }
-    }
-    for (int c0 = 0; c0 < ecount; c0 += 32) {
-        int myI = 0;
-        float4 myh = make_float4(0.f, 0.f, 0.f, 0.f), myp = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c0 + lane < ecount) {
-            const int g = node_ent[e0 + c0 + lane];
-            myI = ent_atom[g];
-            if (use_h) myh = f4(Hca + 4 * (long long)g);
-            if (use_p) myp = f4(Pc + 4 * (long long)g);
-        }
-        const int cnt = min(32, ecount - c0);
-        for (int k = 0; k < cnt; ++k) {
-            const int I = __shfl_sync(0xffffffffu, myI, k);
-            const float h0 = __shfl_sync(0xffffffffu, myh.x, k), h1 = __shfl_sync(0xffffffffu, myh.y, k);
-            const float h2 = __shfl_sync(0xffffffffu, myh.z, k), h3 = __shfl_sync(0xffffffffu, myh.w, k);
-            const float p0 = __shfl_sync(0xffffffffu, myp.x, k), p1 = __shfl_sync(0xffffffffu, myp.y, k);
-            const float p2 = __shfl_sync(0xffffffffu, myp.z, k), p3 = __shfl_sync(0xffffffffu, myp.w, k);
-            for (int t = 0; t < 2; ++t) {
-                const int j = 4 * lane + 128 * t;
-                if (j >= ldz) continue;
-                if (use_h) {
-                    fma4(acc[t], h0, f4(Ye + (size_t)(4 * I + 0) * lde + j));
-                    fma4(acc[t], h1, f4(Ye + (size_t)(4 * I + 1) * lde + j));
-                    fma4(acc[t], h2, f4(Ye + (size_t)(4 * I + 2) * lde + j));
-                    fma4(acc[t], h3, f4(Ye + (size_t)(4 * I + 3) * lde + j));
-                }
-                if (use_p) {
-                    fma4(acc[t], p0, f4(W + (size_t)(4 * I + 0) * lde + j));
-                    fma4(acc[t], p1, f4(W + (size_t)(4 * I + 1) * lde + j));
-                    fma4(acc[t], p2, f4(W + (size_t)(4 * I + 2) * lde + j));
-                    fma4(acc[t], p3, f4(W + (size_t)(4 * I + 3) * lde + j));
-                }
-            }
-        }
-    }
-    for (int t = 0; t < 2; ++t) {
-        const int j = 4 * lane + 128 * t;
-        if (j >= ldz) continue;
-        const float4 z1 = f4(Z1 + row + j);
-        const float4 z0 = Z0 ? f4(Z0 + row + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 gg = f4(G + row + j);
-        const float4 kk = f4(ck + j);
-        float4 zn;
-        zn.x = a * (acc[t].x - c * z1.x) - b * z0.x + a * gg.x * kk.x;
-        zn.y = a * (acc[t].y - c * z1.y) - b * z0.y + a * gg.y * kk.y;
-        zn.z = a * (acc[t].z - c * z1.z) - b * z0.z + a * gg.z * kk.z;
-        zn.w = a * (acc[t].w - c * z1.w) - b * z0.w + a * gg.w * kk.w;
-        *reinterpret_cast<float4 *>(Zn + row + j) = zn;
-        if (ecount > 0) *reinterpret_cast<float4 *>(HYs + row + j) = acc[t];
-    }
-}
-
-// Warp-run forms of the two node kernels: a warp takes a run of kRun
+// The two per-node kernels of the bf16 filter.  A warp takes a run of kRun
 // consecutive nodes along x (same iy, iz), so the y/z part of the cell
 // indexing is formed once per warp, and walks the run's rows as one flat list
 // of float4 column groups (lane l takes groups l, l + 32, ...), so no lane
@@ -626,7 +443,11 @@ __global__ void __launch_bounds__(256) k_pre_bf16_w(MeshDev m, int nruns_x, cons
     }
 }
 
-// The recurrence step at the FE nodes of a run (see k_gather_rec_v).
+// One recurrence step at the FE nodes of a run, fused with the gather of the
+// cell products and the FE-enrichment coupling:
+//   HY[n] = sum over the cells of n of Y_cell[row(n)] + sum_e (Hca_e . Ye + Pc_e . W)
+//   Zn[n] = a (HY[n] - c Z1[n]) - b Z0[n] + a G[n] ck      (Eq. residualapprox)
+// HY is kept at support nodes (HYs) for the enrichment rows.
 __global__ void __launch_bounds__(256) k_gather_rec_w(MeshDev m, int nruns_x, int ldz, const float *Yc, int ldy,
                                                       const long long *node_ptr, const int *node_ent,
                                                       const int *ent_atom, const float *Hca, const float *Pc,
@@ -686,7 +507,7 @@ __global__ void __launch_bounds__(256) k_gather_rec_w(MeshDev m, int nruns_x, in
             const float4 z0 = Z0 ? f4(Z0 + row) : make_float4(0.f, 0.f, 0.f, 0.f);
             const float4 gg = f4(G + row);
             const float4 kk = f4(ck + j);
-            // u = 4 sz + 2 sy + sx: the cells in the order z, y, x (outer to inner)
+            // u = 4 sz + 2 sy + sx: the cells summed in the order z, y, x (outer to inner)
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int u = 0; u < 8; ++u) { acc.x += y[u].x; acc.y += y[u].y; acc.z += y[u].z; acc.w += y[u].w; }
