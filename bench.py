@@ -334,7 +334,7 @@ def run_ours(args):
 
     # end to end through the public call with host buffers (pinned)
     Vh = torch.empty((rows, N), dtype=torch.float64, pin_memory=True)
-    HVh = torch.empty_like(Vh)
+    HVh = torch.empty((rows, N), dtype=torch.float64, pin_memory=True)
     lamh = torch.tensor(eig, dtype=torch.float64).contiguous()
     Vh.copy_(X.cpu())
     HVh.copy_(HX.cpu())

@@ -580,18 +580,10 @@ __global__ void __launch_bounds__(256) k_support_reduce3(const long long *sup_of
     for (int i = 0; i < 8; ++i) r[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (pl < npl) {
         const int j = 4 * cg;
-        // the node indices of the next group are loaded one iteration ahead, so
-        // each iteration waits on one dependent load (the rows) instead of two
-        int nxt[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) nxt[u] = (beg + 4 * pl + u < end) ? sup_node[beg + 4 * pl + u] : -1;
         for (long long g0 = beg + 4 * pl; g0 < end; g0 += 4 * npl) {
             int nodes[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) nodes[u] = nxt[u];
-            const long long g1 = g0 + 4 * npl;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) nxt[u] = (g1 + u < end) ? sup_node[g1 + u] : -1;
+            for (int u = 0; u < 4; ++u) nodes[u] = (g0 + u < end) ? sup_node[g0 + u] : -1;
             float4 sv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
