@@ -393,10 +393,12 @@ __device__ __forceinline__ AxisCells axis_cells(int i, int p, int nc) {
 }
 
 // Xb[n][4q..4q+3] = bf16( minv[n] Z[n] - sum_e C_e . Ye[atom(e)] ) (ldb >= ldz, padding zero)
-__global__ void __launch_bounds__(256) k_pre_bf16_w(MeshDev m, int nruns_x, const float *Z, int ldz, const float *Ye,
-                                                    int lde, int ldb, const double *minv, const long long *node_ptr,
-                                                    const int *node_ent, const int *ent_atom, const float *C,
-                                                    int use_c, __nv_bfloat16 *Xb) {
+__global__ void __launch_bounds__(256) k_pre_bf16_w(MeshDev m, int nruns_x, const float *__restrict__ Z, int ldz,
+                                                    const float *__restrict__ Ye, int lde, int ldb,
+                                                    const double *__restrict__ minv,
+                                                    const long long *__restrict__ node_ptr,
+                                                    const int *__restrict__ nm_atom, const float *__restrict__ nm_C,
+                                                    int use_c, __nv_bfloat16 *__restrict__ Xb) {
     const int lane = threadIdx.x & 31;
     const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nrows = (long long)m.Gy * m.Gz;
@@ -417,15 +419,18 @@ __global__ void __launch_bounds__(256) k_pre_bf16_w(MeshDev m, int nruns_x, cons
         const int j = 4 * cg;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (yz_in && ix > 0 && ix < m.Gx - 1 && j < ldz) {
+            long long e0 = 0, e1 = 0;
+            if (use_c) {
+                e0 = node_ptr[n];
+                e1 = node_ptr[n + 1];
+            }
             const float mi = (float)minv[n];
             v = f4(Z + (size_t)n * ldz + j);
             v.x *= mi; v.y *= mi; v.z *= mi; v.w *= mi;
-            if (use_c) {
-                const long long e0 = node_ptr[n], e1 = node_ptr[n + 1];
+            {
                 for (long long e = e0; e < e1; ++e) {
-                    const int g = node_ent[e];
-                    const float4 cc = f4(C + 4 * (long long)g);
-                    const float *yb = Ye + (4 * ent_atom[g]) * lde + j;
+                    const float4 cc = f4(nm_C + 4 * e);
+                    const float *yb = Ye + (4 * nm_atom[e]) * lde + j;
                     fma4(v, -cc.x, f4(yb));
                     fma4(v, -cc.y, f4(yb + lde));
                     fma4(v, -cc.z, f4(yb + 2 * lde));
@@ -448,13 +453,15 @@ __global__ void __launch_bounds__(256) k_pre_bf16_w(MeshDev m, int nruns_x, cons
 //   HY[n] = sum over the cells of n of Y_cell[row(n)] + sum_e (Hca_e . Ye + Pc_e . W)
 //   Zn[n] = a (HY[n] - c Z1[n]) - b Z0[n] + a G[n] ck      (Eq. residualapprox)
 // HY is kept at support nodes (HYs) for the enrichment rows.
-__global__ void __launch_bounds__(256) k_gather_rec_w(MeshDev m, int nruns_x, int ldz, const float *Yc, int ldy,
-                                                      const long long *node_ptr, const int *node_ent,
-                                                      const int *ent_atom, const float *Hca, const float *Pc,
-                                                      const float *Ye, const float *W, int lde, int use_h, int use_p,
-                                                      const float *Z1, const float *Z0, const float *G,
-                                                      const float *ck, float a, float c, float b, float *Zn,
-                                                      float *HYs) {
+__global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x, int ldz, const float *__restrict__ Yc,
+                                                      int ldy, const long long *__restrict__ node_ptr,
+                                                      const int *__restrict__ nm_atom, const float *__restrict__ Hca,
+                                                      const float *__restrict__ Pc, const float *__restrict__ Ye,
+                                                      const float *__restrict__ W, int lde, int use_h, int use_p,
+                                                      const float *__restrict__ Z1, const float *__restrict__ Z0,
+                                                      const float *__restrict__ G, const float *__restrict__ ck,
+                                                      float a, float c, float b, float *__restrict__ Zn,
+                                                      float *__restrict__ HYs) {
     const int lane = threadIdx.x & 31;
     const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nrows = (long long)m.Gy * m.Gz;
@@ -493,6 +500,12 @@ __global__ void __launch_bounds__(256) k_gather_rec_w(MeshDev m, int nruns_x, in
         if (!(yz_in && ix > 0 && ix < m.Gx - 1)) {
             *reinterpret_cast<float4 *>(Zn + row) = make_float4(0.f, 0.f, 0.f, 0.f);
         } else {
+            // coupling range first, so that its loads overlap the row loads below
+            long long e0 = 0, e1 = 0;
+            if (node_ptr) {
+                e0 = node_ptr[n];
+                e1 = node_ptr[n + 1];
+            }
             const AxisCells ax = axis_cells(ix, m.p, m.nx);
             float4 y[8];
 #pragma unroll
@@ -511,15 +524,12 @@ __global__ void __launch_bounds__(256) k_gather_rec_w(MeshDev m, int nruns_x, in
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int u = 0; u < 8; ++u) { acc.x += y[u].x; acc.y += y[u].y; acc.z += y[u].z; acc.w += y[u].w; }
-            int cnt = 0;
-            if (node_ptr) {
-                const long long e0 = node_ptr[n], e1 = node_ptr[n + 1];
-                cnt = (int)(e1 - e0);
+            const int cnt = (int)(e1 - e0);
+            {
                 for (long long e = e0; e < e1; ++e) {
-                    const int g = node_ent[e];
-                    const int rb = (4 * ent_atom[g]) * lde + j;
+                    const int rb = (4 * nm_atom[e]) * lde + j;
                     if (use_h) {
-                        const float4 h = f4(Hca + 4 * (long long)g);
+                        const float4 h = f4(Hca + 4 * e);
                         const float *yb = Ye + rb;
                         fma4(acc, h.x, f4(yb));
                         fma4(acc, h.y, f4(yb + lde));
@@ -527,7 +537,7 @@ __global__ void __launch_bounds__(256) k_gather_rec_w(MeshDev m, int nruns_x, in
                         fma4(acc, h.w, f4(yb + 3 * lde));
                     }
                     if (use_p) {
-                        const float4 pp = f4(Pc + 4 * (long long)g);
+                        const float4 pp = f4(Pc + 4 * e);
                         const float *wb = W + rb;
                         fma4(acc, pp.x, f4(wb));
                         fma4(acc, pp.y, f4(wb + lde));
@@ -1360,7 +1370,7 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
             ctx->launches++;
         }
         k_pre_bf16_w<<<rb_run, 256, 0, ctx->stream>>>(mh, nruns_x, Zcur, ldz, Ye, lde, ldb, ctx->d_minv,
-                                                      ctx->d_node_ptr, ctx->d_node_ent, ctx->d_ent_atom, ctx->d_C32,
+                                                      ctx->d_node_ptr, ctx->d_nm_atom, ctx->d_nm_C32,
                                                       ctx->enrich ? 1 : 0, Xb);
         ctx->launches++;
         EFE_TRY(efe_check_launch(ctx, "k_pre_bf16_w"));
@@ -1396,7 +1406,7 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
         auto *rev = rec_event_pair(ctx);
         if (rev) cudaEventRecord(rev->first, ctx->stream);
         k_gather_rec_w<<<rb_run, 256, 0, ctx->stream>>>(mh, nruns_x, ldz, Ycells, ldy, cpl ? ctx->d_node_ptr : nullptr,
-                                                        ctx->d_node_ent, ctx->d_ent_atom, ctx->d_Hca32, ctx->d_Pc32,
+                                                        ctx->d_nm_atom, ctx->d_nm_H32, ctx->d_nm_P32,
                                                         Ye, W32, lde, ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0,
                                                         Zcur, Zprev, G, fck + (size_t)(k - 1) * ldz, ak, cf, bk,
                                                         Znext, HYs);
@@ -1646,7 +1656,7 @@ void efe_destroy(efe_ctx *ctx) {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     efe_scf_free(ctx);
-    void *ptrs[] = {ctx->d_hostio, ctx->d_B1, ctx->d_D1, ctx->d_wq, ctx->d_Khat, ctx->d_mcc, ctx->d_minv, ctx->d_He, ctx->d_He32,
+    void *ptrs[] = {ctx->d_nm_atom, ctx->d_nm_C32, ctx->d_nm_H32, ctx->d_nm_P32, ctx->d_hostio, ctx->d_B1, ctx->d_D1, ctx->d_wq, ctx->d_Khat, ctx->d_mcc, ctx->d_minv, ctx->d_He, ctx->d_He32,
                     ctx->d_He16, ctx->d_atoms, ctx->d_hproj, ctx->d_sup_off, ctx->d_sup_node, ctx->d_C, ctx->d_B,
                     ctx->d_Kca, ctx->d_Hca, ctx->d_Pc, ctx->d_C32, ctx->d_Hca32, ctx->d_Pc32, ctx->d_node_ptr,
                     ctx->d_node_ent, ctx->d_ent_atom,

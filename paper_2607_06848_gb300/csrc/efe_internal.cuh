@@ -68,6 +68,9 @@ struct efe_ctx {
     double *d_Hca = nullptr;                  // sup_total x 4 (Kca + Vca)
     double *d_Pc = nullptr;                   // sup_total x 4 (<beta_f, N_j>)
     float *d_C32 = nullptr, *d_Hca32 = nullptr, *d_Pc32 = nullptr;   // FP32 copies for the mixed filter
+    // the same in node-major (CSR) order, with the atom of each entry, for the node kernels
+    int *d_nm_atom = nullptr;
+    float *d_nm_C32 = nullptr, *d_nm_H32 = nullptr, *d_nm_P32 = nullptr;
     // node -> (atom, pos) CSR over all nodes
     long long *d_node_ptr = nullptr;          // n_nodes + 1
     int *d_node_ent = nullptr;                // entries: global support index (sup_off[I] + pos)

@@ -160,6 +160,21 @@ __global__ void k_static_pairs(MeshDev m, Tables1D T, FuncParams fp, const PairI
 }
 
 // Potential coupling for one pair: Hca[l][f] += int v a_f N_l.
+// node-major copies of the coupling tables (statics on the first call, H^ca always)
+__global__ void k_node_major(long long n, const int *node_ent, const int *ent_atom, const float *C32,
+                             const float *H32, const float *P32, int statics, int *nm_atom, float *nm_C,
+                             float *nm_H, float *nm_P) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int g = node_ent[e];
+    reinterpret_cast<float4 *>(nm_H)[e] = reinterpret_cast<const float4 *>(H32)[g];
+    if (statics) {
+        nm_atom[e] = ent_atom[g];
+        reinterpret_cast<float4 *>(nm_C)[e] = reinterpret_cast<const float4 *>(C32)[g];
+        reinterpret_cast<float4 *>(nm_P)[e] = reinterpret_cast<const float4 *>(P32)[g];
+    }
+}
+
 __global__ void k_potential_pairs(MeshDev m, Tables1D T, FuncParams fp, const PairInfo *pairs,
                                   int p0, const int *pair_pos, const long long *sup_off,
                                   const double *atoms, const double *vq, double *dH) {
@@ -719,6 +734,21 @@ efe_status efe_potential_assembly(efe_ctx *ctx, const double *veff_q) {
         }
         k_to_float<<<nblk(S4, 256), 256, 0, ctx->stream>>>(S4, ctx->d_Hca, ctx->d_Hca32);
         EFE_TRY(efe_check_launch(ctx, "k_to_float"));
+        // node-major copies: entry e of the node CSR carries its atom and coefficients
+        const long long ns = std::max<long long>(ctx->sup_total, 1);
+        const bool first = ctx->d_nm_atom == nullptr;
+        if (first) {
+            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_nm_atom, sizeof(int) * ns));
+            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_nm_C32, sizeof(float) * 4 * ns));
+            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_nm_H32, sizeof(float) * 4 * ns));
+            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_nm_P32, sizeof(float) * 4 * ns));
+        }
+        if (ctx->sup_total > 0) {
+            k_node_major<<<nblk(ctx->sup_total, 256), 256, 0, ctx->stream>>>(
+                ctx->sup_total, ctx->d_node_ent, ctx->d_ent_atom, ctx->d_C32, ctx->d_Hca32, ctx->d_Pc32, first ? 1 : 0,
+                ctx->d_nm_atom, ctx->d_nm_C32, ctx->d_nm_H32, ctx->d_nm_P32);
+            EFE_TRY(efe_check_launch(ctx, "k_node_major"));
+        }
     }
     ctx->have_potential = true;
     return EFE_OK;
