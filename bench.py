@@ -194,9 +194,13 @@ def roofline_bf16(w, d, N, m, ms_cell_launch, ms_rec_launch, pk, pk_kind):
              "bytes_per_cell")):
         achieved = bytes_ / (ms / 1e3) / 1e9 if ms and ms > 0 else None
         traffic = None
-        if traffic_key and d["ne"] == 343 and N == 154:   # counters taken on this kernel at this shape
-            per = _traffic_per_unit("k_cell_mma_traffic.txt", traffic_key)
-            traffic = per * d["n_cells"] if per else None
+        if d["ne"] == 343 and N == 154:      # counters taken on these kernels at this shape (p = 6, N = 154)
+            if traffic_key:
+                per = _traffic_per_unit("k_cell_mma_traffic.txt", traffic_key)
+                traffic = per * d["n_cells"] if per else None
+            else:
+                ratio = _traffic_per_unit("k_gather_rec_w_traffic.txt", "traffic_over_algorithmic")
+                traffic = ratio * bytes_ if ratio else None
         out.append({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm if achieved else None, "traffic": traffic,
                     "algorithmic_bytes": bytes_, "peak_kind": pk_kind + " (burst copy)", "kernel": name,

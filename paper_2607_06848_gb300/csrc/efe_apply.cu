@@ -571,7 +571,7 @@ __device__ inline float4 ld4(const __nv_bfloat16 *p) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_support_reduce3(const long long *sup_off, const int *sup_node,
+__global__ void __launch_bounds__(256, 4) k_support_reduce3(const long long *sup_off, const int *sup_node,
                                                          const float *coefA, const float *coefB, const T *S,
                                                          int N, int ld, int chunk, int nch, double *part) {
     // thread t: float4 column group cg = t % ncg, position lane pl = t / ncg
