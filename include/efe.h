@@ -184,7 +184,8 @@ efe_status efe_filter(efe_ctx *ctx, const double *V, const double *HV, const dou
  * X <- X D, HX <- H^E X D with D^T (X^T M X) D = I, ascending eigenvalues.
  * X, HX: device rows x N (HX is computed here); eig, resid: host N doubles
  * (resid_i = ||H psi_i - eps_i M psi_i||_2).  EFE_ERR_NOT_SPD if X^T M X is
- * not positive definite (dependent columns). */
+ * not positive definite (dependent columns) or the generalized eigensolve
+ * fails. */
 efe_status efe_rayleigh_ritz(efe_ctx *ctx, double *X, double *HX, int N,
                              double *eig, double *resid);
 
@@ -194,7 +195,9 @@ efe_status efe_rayleigh_ritz(efe_ctx *ctx, double *X, double *HX, int N,
  * with a0 = theta_min, a = a0 + 0.3 (b - a0); later passes a = max Ritz value,
  * a0 = min Ritz value.  X, HX: device rows x N, in/out (HX may be NULL).
  * eig, resid: host N.  passes: host, may be NULL.  EFE_ERR_NO_CONVERGE when
- * max_pass is reached (results are still written). */
+ * max_pass is reached (results are still written).  With prec = EFE_BF16 the
+ * passes run in bf16 while each reduces max(resid[0:nconv]); after one that
+ * does not, the remaining passes run in FP32. */
 efe_status efe_chfsi(efe_ctx *ctx, double *X, double *HX, int N, int m, const double *bounds,
                      const double *u0, int max_pass, double tol, int nconv,
                      efe_precision prec, double *eig, double *resid, int *passes);

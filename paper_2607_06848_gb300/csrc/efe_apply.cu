@@ -987,11 +987,13 @@ efe_status hx_scratch(efe_ctx *ctx, int N, HxScratch &s) {
     for (int I = 0; I < ctx->natoms; ++I) maxsup = std::max(maxsup, ctx->sup_off[I + 1] - ctx->sup_off[I]);
     s.chunk = 1024;
     s.nch = (int)std::max<long long>(1, (maxsup + s.chunk - 1) / s.chunk);
-    size_t need = (size_t)s.nch * std::max(ctx->natoms, 1) * 8 * N + (size_t)(3 * ctx->n_enr + 2 * ctx->n_proj) * N + 64;
+    // partial sums: 8 rows per (atom, chunk)
+    const size_t npart = (size_t)s.nch * std::max(ctx->natoms, 1) * 8 * N;
+    size_t need = npart + (size_t)(3 * ctx->n_enr + 2 * ctx->n_proj) * N + 64;
     EFE_TRY(efe_partials(ctx, need));
     double *p = ctx->d_part;
     s.part = p;
-    p += (size_t)s.nch * std::max(ctx->natoms, 1) * 8 * N;
+    p += npart;
     s.Rh = p; p += (size_t)ctx->n_enr * N;
     s.Wc = p; p += (size_t)ctx->n_proj * N;
     s.W = p; p += (size_t)ctx->n_proj * N;
@@ -1518,8 +1520,9 @@ efe_status efe_rr_impl(efe_ctx *ctx, double *X, double *HX, int N, double *eig, 
     EFE_CUDA(ctx, cudaMemcpyAsync(&info, ctx->d_info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (info != 0) {
-        ctx->err = "Rayleigh-Ritz: X^T M X is not positive definite (sygvd info " + std::to_string(info) + ")";
-        return info > N ? EFE_ERR_NOT_SPD : EFE_ERR_NO_CONVERGE;
+        ctx->err = "Rayleigh-Ritz: generalized eigensolve failed (sygvd info " + std::to_string(info) +
+                   (info > N ? ": X^T M X is not positive definite)" : ": eigenvalues did not converge)");
+        return EFE_ERR_NOT_SPD;
     }
     k_rr_unscale<<<nblk(N2, 256), 256, 0, ctx->stream>>>(N, Hs, d, Qr);
     const size_t shm = sizeof(double) * 16 * N;
@@ -1956,12 +1959,19 @@ efe_status efe_chfsi(efe_ctx *ctx, double *X, double *HX, int N, int m, const do
     double ms_filter = 0.0, ms_rr = 0.0;
     int pass = 0;
     bool conv = false;
+    // bf16 passes only while they contract the largest wanted residual: the
+    // rounding error of a pass scales with the residual, and from a poor
+    // subspace of a large problem it can outgrow the filter's damping; after a
+    // bf16 pass that does not reduce the residual, the remaining passes are FP32
+    efe_precision pp = prec;
+    double prev_mx = 0.0;
+    for (int j = 0; j < nconv; ++j) prev_mx = std::max(prev_mx, resid[j]);
     while (pass < max_pass) {
         if (cudaMemcpyAsync(dlam, eig, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
             cleanup();
             return EFE_ERR_CUDA;
         }
-        if ((st = efe_filter_dispatch(ctx, X, dHX, dlam, N, m, bd, prec, dVout)) != EFE_OK) { cleanup(); return st; }
+        if ((st = efe_filter_dispatch(ctx, X, dHX, dlam, N, m, bd, pp, dVout)) != EFE_OK) { cleanup(); return st; }
         ms_filter += ctx->stats.ms_filter;
         if ((st = efe_rr_impl(ctx, dVout, dHX, N, eig, resid)) != EFE_OK) { cleanup(); return st; }
         ms_rr += ctx->stats.ms_rr;
@@ -1972,6 +1982,8 @@ efe_status efe_chfsi(efe_ctx *ctx, double *X, double *HX, int N, int m, const do
         ++pass;
         double mx = 0.0;
         for (int j = 0; j < nconv; ++j) mx = std::max(mx, resid[j]);
+        if (pp == EFE_BF16 && !(mx < prev_mx)) pp = EFE_FP32;
+        prev_mx = mx;
         bd[0] = eig[0];
         bd[1] = eig[N - 1];
         if (mx < tol) { conv = true; break; }

@@ -3,19 +3,26 @@
 //
 // Layout choices (all produced by this library, so chosen for the MMA):
 //   A = H_e (ne x ne, bf16) is stored per cell pre-tiled in the canonical
-//       K-major no-swizzle layout: for M-tile mt (128 rows) and k-step s (16
-//       columns) a 4 KB block of 8x8 core matrices, core (rg, kg) at byte
-//       (rg*2 + kg)*128.  It is streamed through shared memory with 1-D bulk
-//       copies (LBO = 128 B along K, SBO = 256 B along M).
+//       K-major no-swizzle layout, k-step by k-step: for k-step s (16
+//       columns) and M-tile mt (128 rows) a 4 KB block of 8x8 core matrices,
+//       core (rg, kg) at byte (rg*2 + kg)*128, blocks ordered [s][mt].  One
+//       A stage (all M-tiles of one k-step) is a single 1-D bulk copy
+//       (LBO = 128 B along K, SBO = 256 B along M).
 //   B = X'_e (K x Npad, bf16) is gathered by TMA straight from the node grid:
 //       a 4-D tile {8 columns, xpad, p+1, 1} per z-plane and column block
-//       lands as rows of 16 B, i.e. the canonical MN-major no-swizzle layout
-//       (LBO = 128 B between 8-row K groups, SBO = Kpad*16 B between
-//       8-column blocks).  No index list: the cell's nodes are a box.  The
-//       x extent is padded to xpad = 8 so that every plane is a multiple of
-//       128 B (TMA destinations must be 128-byte aligned); the padding node
-//       meets zero columns of the pre-tiled H_e.  K index k = (z*(p+1) + y)*xpad + x.
+//       lands as rows of 16 B, i.e. the canonical MN-major no-swizzle layout.
+//       Planes are grouped in pairs; a pair is 2 (p+1) xpad rows = (p+1)
+//       whole k-steps, held in one of two ring slots (LBO = 128 B between
+//       8-row K groups, SBO = 2 (p+1) xpad 16 B between 8-column blocks).  No
+//       index list: the cell's nodes are a box.  The x extent is padded to
+//       xpad = 8 so that every plane is a multiple of 128 B (TMA destinations
+//       must be 128-byte aligned); the padding node meets zero columns of the
+//       pre-tiled H_e.  K index k = (z*(p+1) + y)*xpad + x.
 //   D = accumulator, M-tile mt at TMEM columns [mt*Npad, (mt+1)*Npad).
+// The MMAs run k-step-major (all M-tiles of a k-step, then the next k-step),
+// so each plane pair is released as soon as its k-steps are done and the
+// freed shared memory deepens the A ring; the epilogue of a cell overlaps the
+// loads of the next.
 // Per-cell results go to Ycells[cell][row][ldy] (FP32); a gather kernel sums
 // the up-to-8 contributions of each node, so no colouring or atomics are
 // needed and every cell of the mesh runs in one persistent launch.
@@ -31,14 +38,18 @@
 namespace {
 
 constexpr int TC_THREADS = 256;      // w0 TMA producer, w1 MMA issuer, w2 TMEM owner, w4-7 epilogue
-constexpr int KS = 2;                // k-steps per A stage (2 x 4 KB)
-constexpr int A_STAGES = 12;
-constexpr int MAX_PLANES = EFE_MAXP + 1;
+constexpr int MAX_A_STAGES = 24;     // A ring depth limit (one stage = one k-step of all M-tiles)
+constexpr int B_SLOTS = 2;           // plane-pair ring
+constexpr int SMEM_LIMIT = 232448;   // dynamic shared memory per block (227 KB)
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz before a wait gives up
 
 struct TcParams {
     int ncells, nx, ny, p, np1, ne, xpad, Kpad, ksteps, MT, Npad, ncb, col0, ldy;
-    int nsmem_b;                        // bytes of the B region
+    int plane_rows;                     // (p+1) xpad rows per z-plane
+    int kpg;                            // k-steps per plane pair: 2 plane_rows / 16
+    int ngroups;                        // plane pairs per cell: ceil((p+1) / 2)
+    int a_stages;                       // A ring depth
+    int slot_bytes;                     // one B slot: ncb x 2 plane_rows x 16 B
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -140,29 +151,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // every TMA destination below is a multiple of 128 B from this base
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    unsigned char *sB = smem;
-    unsigned char *sA = smem + P.nsmem_b;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sA + A_STAGES * KS * 4096);
-    uint64_t *full_a = bars, *empty_a = bars + A_STAGES;
-    uint64_t *full_b = bars + 2 * A_STAGES, *empty_b = full_b + MAX_PLANES;
-    uint64_t *acc_full = empty_b + MAX_PLANES, *acc_empty = acc_full + 4;
+    const int stage_bytes = P.MT * 4096;
+    unsigned char *sA = smem;
+    unsigned char *sB = smem + (size_t)P.a_stages * stage_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + (size_t)B_SLOTS * P.slot_bytes);
+    uint64_t *full_a = bars, *empty_a = bars + MAX_A_STAGES;
+    uint64_t *full_b = bars + 2 * MAX_A_STAGES, *empty_b = full_b + B_SLOTS;
+    uint64_t *acc_full = empty_b + B_SLOTS, *acc_empty = acc_full + 4;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int plane_rows = P.np1 * P.xpad;
-    const int krows = P.np1 * plane_rows;      // rows written by TMA
+    const int pair_stride = 2 * P.plane_rows * 16;   // bytes between column blocks in a slot
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < A_STAGES; ++i) { mbar_init(&full_a[i], 1); mbar_init(&empty_a[i], 1); }
-        for (int z = 0; z < MAX_PLANES; ++z) { mbar_init(&full_b[z], 1); mbar_init(&empty_b[z], 1); }
+        for (int i = 0; i < P.a_stages; ++i) { mbar_init(&full_a[i], 1); mbar_init(&empty_a[i], 1); }
+        for (int i = 0; i < B_SLOTS; ++i) { mbar_init(&full_b[i], 1); mbar_init(&empty_b[i], 1); }
         for (int t = 0; t < 4; ++t) { mbar_init(&acc_full[t], 1); mbar_init(&acc_empty[t], 128); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // zero the rows [krows, Kpad) of every column block of B once (never written by TMA)
-    for (int i = threadIdx.x; i < P.ncb * (P.Kpad - krows) * 4; i += blockDim.x) {
-        int cb = i / ((P.Kpad - krows) * 4), rem = i % ((P.Kpad - krows) * 4);
-        reinterpret_cast<uint32_t *>(sB + (size_t)cb * P.Kpad * 16 + (size_t)krows * 16)[rem] = 0u;
-    }
+    // zero both B slots once: rows a lone last plane leaves unwritten meet zero
+    // columns of H_e, and must hold finite values
+    for (int i = threadIdx.x; i < B_SLOTS * P.slot_bytes / 4; i += blockDim.x)
+        reinterpret_cast<uint32_t *>(sB)[i] = 0u;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
@@ -175,89 +185,85 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     if (warp == 0 && lane == 0) {
         // ---------------- producer ----------------
-        int slot = 0;
-        uint32_t ph = 0;
-        int it = 0;
+        int sa = 0, sb = 0;
+        uint32_t pha = 0, phb = 0;
         bool ok = true;
-        uint32_t used = 0, par = 0;       // per A slot: issued at least once, parity of its last phase
-        uint32_t bused = 0, bpar = 0;     // the same per B plane
-        for (int cell = blockIdx.x; cell < P.ncells && ok; cell += gridDim.x, ++it) {
+        uint32_t aused = 0, apar = 0;      // per A slot: issued at least once, parity of its last phase
+        uint32_t bused = 0, bpar = 0;      // the same per B slot
+        for (int cell = blockIdx.x; cell < P.ncells && ok; cell += gridDim.x) {
             const int cx = cell % P.nx, cy = (cell / P.nx) % P.ny, cz = cell / (P.nx * P.ny);
-            for (int z = 0; z < P.np1 && ok; ++z) {
-                if (!mbar_wait(&empty_b[z], (it & 1) ^ 1)) { ok = false; break; }
-                mbar_expect_tx(&full_b[z], (uint32_t)(plane_rows * 16 * P.ncb));
-                for (int cb = 0; cb < P.ncb; ++cb)
-                    tma_load_4d(sB + (size_t)cb * P.Kpad * 16 + (size_t)z * plane_rows * 16, &xmap, P.col0 + 8 * cb,
-                                cx * P.p, cy * P.p, cz * P.p + z, &full_b[z]);   // {cols, x, y, z}
-                bused |= 1u << z;
-                bpar = (bpar & ~(1u << z)) | ((uint32_t)(it & 1) << z);
-            }
-            const __nv_bfloat16 *Ac = He16 + (size_t)cell * P.MT * P.ksteps * 2048;
-            for (int mt = 0; mt < P.MT && ok; ++mt)
-                for (int s0 = 0; s0 < P.ksteps; s0 += KS) {
-                    if (!mbar_wait(&empty_a[slot], ph ^ 1)) { ok = false; break; }
-                    const int nks = min(KS, P.ksteps - s0);
-                    mbar_expect_tx(&full_a[slot], (uint32_t)(nks * 4096));
-                    bulk_load(sA + (size_t)slot * KS * 4096, Ac + ((size_t)mt * P.ksteps + s0) * 2048,
-                              (uint32_t)(nks * 4096), &full_a[slot]);
-                    used |= 1u << slot;
-                    par = (par & ~(1u << slot)) | (ph << slot);
-                    if (++slot == A_STAGES) { slot = 0; ph ^= 1; }
+            const __nv_bfloat16 *Ac = He16 + (size_t)cell * P.ksteps * P.MT * 2048;
+            int s = 0;
+            for (int g = 0; g < P.ngroups && ok; ++g) {
+                // plane pair g -> B slot sb
+                if (!mbar_wait(&empty_b[sb], phb ^ 1)) { ok = false; break; }
+                const int np = min(2, P.np1 - 2 * g);
+                mbar_expect_tx(&full_b[sb], (uint32_t)(np * P.plane_rows * 16 * P.ncb));
+                unsigned char *slot = sB + (size_t)sb * P.slot_bytes;
+                for (int zz = 0; zz < np; ++zz)
+                    for (int cb = 0; cb < P.ncb; ++cb)
+                        tma_load_4d(slot + (size_t)cb * pair_stride + (size_t)zz * P.plane_rows * 16, &xmap,
+                                    P.col0 + 8 * cb, cx * P.p, cy * P.p, cz * P.p + 2 * g + zz,
+                                    &full_b[sb]);   // {cols, x, y, z}
+                bused |= 1u << sb;
+                bpar = (bpar & ~(1u << sb)) | (phb << sb);
+                if (++sb == B_SLOTS) { sb = 0; phb ^= 1; }
+                // the A stages of this pair's k-steps
+                const int s_end = min(P.ksteps, (g + 1) * P.kpg);
+                for (; s < s_end; ++s) {
+                    if (!mbar_wait(&empty_a[sa], pha ^ 1)) { ok = false; break; }
+                    mbar_expect_tx(&full_a[sa], (uint32_t)stage_bytes);
+                    bulk_load(sA + (size_t)sa * stage_bytes, Ac + (size_t)s * P.MT * 2048, (uint32_t)stage_bytes,
+                              &full_a[sa]);
+                    aused |= 1u << sa;
+                    apar = (apar & ~(1u << sa)) | (pha << sa);
+                    if (++sa == P.a_stages) { sa = 0; pha ^= 1; }
                 }
+            }
         }
         if (!ok) atomicExch(err, 1);
         // drain: every copy this thread issued has landed before the block exits
-        for (int z = 0; z < P.np1; ++z)
-            if (bused & (1u << z)) mbar_wait(&full_b[z], (bpar >> z) & 1u);
-        for (int i = 0; i < A_STAGES; ++i)
-            if (used & (1u << i)) mbar_wait(&full_a[i], (par >> i) & 1u);
+        for (int i = 0; i < B_SLOTS; ++i)
+            if (bused & (1u << i)) mbar_wait(&full_b[i], (bpar >> i) & 1u);
+        for (int i = 0; i < P.a_stages; ++i)
+            if (aused & (1u << i)) mbar_wait(&full_a[i], (apar >> i) & 1u);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (0u << 15) | (1u << 16) |
                                ((uint32_t)(P.Npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-        int slot = 0;
-        uint32_t ph = 0;
+        int sa = 0, sb = 0;
+        uint32_t pha = 0, phb = 0;
         int it = 0;
         bool ok = true;
         const uint32_t sB_addr = smem_u32(sB), sA_addr = smem_u32(sA);
         for (int cell = blockIdx.x; cell < P.ncells && ok; cell += gridDim.x, ++it) {
-            int zdone = -1;
-            int zrel = 0;
-            for (int mt = 0; mt < P.MT && ok; ++mt) {
-                if (!mbar_wait(&acc_empty[mt], (it & 1) ^ 1)) { ok = false; break; }
-                fence_after();
-                for (int s = 0; s < P.ksteps; ++s) {
-                    if (s % KS == 0) {
-                        if (!mbar_wait(&full_a[slot], ph)) { ok = false; break; }
-                        fence_after();
-                    }
-                    if (mt == 0) {
-                        int zneed = min(P.np1 - 1, (16 * s + 15) / plane_rows);
-                        while (zdone < zneed) {
-                            ++zdone;
-                            if (!mbar_wait(&full_b[zdone], it & 1)) { ok = false; break; }
-                        }
-                        if (!ok) break;
-                        fence_after();
-                    }
-                    const uint64_t ad = smem_desc(sA_addr + slot * KS * 4096 + (s % KS) * 4096, 128, 256);
-                    const uint64_t bd = smem_desc(sB_addr + s * 256, 128, (uint32_t)(P.Kpad * 16));
-                    mma_bf16(tmem + (uint32_t)(mt * P.Npad), ad, bd, idesc, s > 0 ? 1u : 0u);
-                    if (s % KS == KS - 1 || s == P.ksteps - 1) {
-                        mma_commit(&empty_a[slot]);
-                        if (++slot == A_STAGES) { slot = 0; ph ^= 1; }
-                    }
-                    if (mt == P.MT - 1) {
-                        // release the B planes whose last row is consumed by this k-step
-                        while (zrel < P.np1 && ((plane_rows * (zrel + 1) - 1) / 16 <= s || s == P.ksteps - 1)) {
-                            mma_commit(&empty_b[zrel]);
-                            ++zrel;
-                        }
-                    }
+            // every M-tile accumulates over the whole cell: all of them must be drained
+            for (int mt = 0; mt < P.MT && ok; ++mt)
+                if (!mbar_wait(&acc_empty[mt], (it & 1) ^ 1)) ok = false;
+            if (!ok) break;
+            fence_after();
+            for (int s = 0; s < P.ksteps; ++s) {
+                const int g = s / P.kpg, j = s - g * P.kpg;
+                if (j == 0) {
+                    if (!mbar_wait(&full_b[sb], phb)) { ok = false; break; }
+                    fence_after();
                 }
-                if (!ok) break;
-                mma_commit(&acc_full[mt]);
+                if (!mbar_wait(&full_a[sa], pha)) { ok = false; break; }
+                fence_after();
+                const uint64_t bd = smem_desc(sB_addr + sb * P.slot_bytes + j * 256, 128, (uint32_t)pair_stride);
+                for (int mt = 0; mt < P.MT; ++mt) {
+                    const uint64_t ad = smem_desc(sA_addr + sa * stage_bytes + mt * 4096, 128, 256);
+                    mma_bf16(tmem + (uint32_t)(mt * P.Npad), ad, bd, idesc, s > 0 ? 1u : 0u);
+                }
+                mma_commit(&empty_a[sa]);
+                if (++sa == P.a_stages) { sa = 0; pha ^= 1; }
+                if (j == P.kpg - 1 || s == P.ksteps - 1) {
+                    mma_commit(&empty_b[sb]);
+                    if (++sb == B_SLOTS) { sb = 0; phb ^= 1; }
+                }
             }
+            if (!ok) break;
+            for (int mt = 0; mt < P.MT; ++mt) mma_commit(&acc_full[mt]);
         }
         if (!ok) atomicExch(err, 2);
     } else if (warp >= 4) {
@@ -311,7 +317,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // Pre-tile H_e (FP32, ne x ne per cell) into bf16 MMA blocks:
-// [cell][mt][s][rg 16][kg 2][ri 8][ki 8].  Row R is the cell-local node
+// [cell][s][mt][rg 16][kg 2][ri 8][ki 8].  Row R is the cell-local node
 // (az*(p+1) + ay)*(p+1) + ax; column K = (z*(p+1) + y)*xpad + x follows the B
 // rows, with zeros for the padding nodes x >= p+1 and outside ne x ne.
 __global__ void k_tile_he16(int ncells, int np1, int xpad, int MT, int ksteps, const float *He32,
@@ -323,8 +329,8 @@ __global__ void k_tile_he16(int ncells, int np1, int xpad, int MT, int ksteps, c
          i += (long long)gridDim.x * blockDim.x) {
         int e = (int)(i % 2048);
         long long blk = i / 2048;
-        int s = (int)(blk % ksteps);
-        int mt = (int)((blk / ksteps) % MT);
+        int mt = (int)(blk % MT);
+        int s = (int)((blk / MT) % ksteps);
         long long cell = blk / ((long long)ksteps * MT);
         int core = e / 64, within = e % 64;
         int rg = core / 2, kg = core % 2, ri = within / 8, ki = within % 8;
@@ -359,8 +365,15 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode(efe_ctx *ctx) {
 
 // Geometry of the tensor-core cell product for this mesh and N columns.
 struct TcShape {
-    int xpad, Kpad, ksteps, MT, Npad, nchunks;
+    int xpad, Kpad, ksteps, MT, Npad, nchunks, plane_rows, kpg, ngroups, a_stages, slot_bytes;
+    size_t smem;
 };
+
+// shared memory: A ring + two B slots + barriers (+ alignment slack) within 227 KB
+static size_t tc_smem(const TcShape &s) {
+    return (size_t)s.a_stages * s.MT * 4096 + (size_t)B_SLOTS * s.slot_bytes +
+           (2 * MAX_A_STAGES + 2 * B_SLOTS + 8) * 8 + 64 + 1024;
+}
 
 static TcShape tc_shape(const efe_ctx *ctx, int N, int ldb) {
     TcShape s{};
@@ -369,13 +382,23 @@ static TcShape tc_shape(const efe_ctx *ctx, int N, int ldb) {
     s.Kpad = (np1 * np1 * s.xpad + 15) / 16 * 16;
     s.ksteps = s.Kpad / 16;
     s.MT = (ne + 127) / 128;
+    s.plane_rows = np1 * s.xpad;
+    s.kpg = 2 * s.plane_rows / 16;
+    s.ngroups = (np1 + 1) / 2;
+    const int stage = s.MT * 4096;
+    const size_t fixed = (2 * MAX_A_STAGES + 2 * B_SLOTS + 8) * 8 + 64 + 1024;
     int maxN = std::min(256, (512 / s.MT) / 16 * 16);
-    // shared memory: B (Kpad x Npad bf16) + A ring + barriers within 227 KB
-    const int budget = 227 * 1024 - A_STAGES * KS * 4096 - 2048;
-    while (maxN > 16 && (long long)s.Kpad * maxN * 2 > budget) maxN -= 16;
+    // keep at least 4 A stages
+    while (maxN > 16 && fixed + 4 * (size_t)stage + (size_t)B_SLOTS * (maxN / 8) * 2 * s.plane_rows * 16 >
+                            (size_t)SMEM_LIMIT)
+        maxN -= 16;
     int Nn = std::min(ldb, ((N + 15) / 16) * 16);
     s.nchunks = (Nn + maxN - 1) / maxN;
     s.Npad = ((Nn + s.nchunks - 1) / s.nchunks + 15) / 16 * 16;
+    s.slot_bytes = (s.Npad / 8) * 2 * s.plane_rows * 16;
+    const size_t left = (size_t)SMEM_LIMIT - fixed - (size_t)B_SLOTS * s.slot_bytes;
+    s.a_stages = (int)std::min<size_t>(MAX_A_STAGES, left / stage);
+    s.smem = tc_smem(s);
     return s;
 }
 
@@ -441,8 +464,16 @@ efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, float
         P.ncb = sh.Npad / 8;
         P.col0 = ch * sh.Npad;
         P.ldy = ldy;
-        P.nsmem_b = sh.Kpad * 16 * P.ncb;
-        const size_t shm = (size_t)P.nsmem_b + A_STAGES * KS * 4096 + 64 * 8 + 64 + 1024;
+        P.plane_rows = sh.plane_rows;
+        P.kpg = sh.kpg;
+        P.ngroups = sh.ngroups;
+        P.a_stages = sh.a_stages;
+        P.slot_bytes = sh.slot_bytes;
+        if (sh.a_stages < 4 || sh.smem > (size_t)SMEM_LIMIT) {
+            ctx->err = "tensor-core cell product: shared-memory plan does not fit";
+            return EFE_ERR_ARG;
+        }
+        const size_t shm = sh.smem;
         EFE_CUDA(ctx, cudaFuncSetAttribute(k_cell_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         const int grid = std::min(nsm > 0 ? nsm : 148, ncells);
         k_cell_mma<<<grid, TC_THREADS, shm, ctx->stream>>>(map, reinterpret_cast<const __nv_bfloat16 *>(ctx->d_He16),
