@@ -48,6 +48,15 @@ def _case(name):
     if name == "p5_enriched":
         return dict(h=2.0, ncell=(5, 5, 6), p=5, atoms=np.array([[5.0, 5.0, 6.1]]),
                     hproj=np.array([[-0.4, 1.1]]), enrich=True, nl=True)
+    if name == "p7_cfe":
+        return dict(h=1.5, ncell=(2, 3, 2), p=7, atoms=np.array([[1.5, 2.2, 1.4]]), hproj=np.zeros((1, 2)),
+                    enrich=False, nl=False)
+    if name == "p1_enriched":
+        return dict(h=1.0, ncell=(13, 13, 13), p=1, atoms=np.array([[6.5, 6.4, 6.6]]),
+                    hproj=np.array([[0.9, -0.7]]), enrich=True, nl=True)
+    if name == "p8_cfe":
+        return dict(h=2.0, ncell=(2, 2, 2), p=8, atoms=np.array([[2.0, 2.0, 2.0]]), hproj=np.zeros((1, 2)),
+                    enrich=False, nl=False)
     if name == "single_atom":
         return dict(h=2.0, ncell=(6, 6, 6), p=4, atoms=np.array([[6.3, 5.8, 6.1]]), hproj=np.array([[-1.2, 0.7]]),
                     enrich=True, nl=True)

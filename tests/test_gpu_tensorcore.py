@@ -37,6 +37,32 @@ def test_apply_h_bf16(name, N):
     assert rel < 1e-2, rel
 
 
+@pytest.mark.parametrize("name,N", [("p7_cfe", 37), ("p1_enriched", 13), ("p6_cfe", 200), ("p6_enriched", 256)])
+def test_apply_h_bf16_shapes(name, N):
+    # p = 7: four M-tiles (Npad <= 128, two column chunks at N = 200 would not fit
+    # otherwise); p = 1: the smallest box; N = 200 and 256 at p = 6: more columns
+    # than one launch holds (three M-tiles -> 160 per chunk), so two chunks
+    o, g = TP._systems(name)
+    X = TP._rand(o, N, 500 + N)
+    Xd = torch.tensor(X, device="cuda")
+    Y = torch.empty_like(Xd)
+    g.efe_apply_h(Xd, Y, prec=2)
+    rel = TP._rel(Y.cpu().numpy(), o.apply_H(X))
+    assert rel < 1e-2, rel
+
+
+def test_tensor_path_rejects_p8():
+    # (p+1)^3 = 729 rows need more than four 128-row M-tiles of tensor memory
+    from paper_2607_06848_gb300 import EFEError
+    o, g = TP._systems("p8_cfe")
+    X = torch.tensor(TP._rand(o, 8, 9), device="cuda")
+    Y = torch.empty_like(X)
+    with pytest.raises(EFEError):
+        g.efe_apply_h(X, Y, prec=2)
+    g.efe_apply_h(X, Y)                      # the FP64 path still works
+    assert TP._rel(Y.cpu().numpy(), o.apply_H(TP._rand(o, 8, 9))) < 1e-12
+
+
 @pytest.mark.parametrize("name", ["dimer", "ragged"])
 def test_chfsi_bf16_reaches_fp64_eigenvalues(name):
     o, g = TP._systems(name)
