@@ -202,6 +202,30 @@ efe_status efe_chfsi(efe_ctx *ctx, double *X, double *HX, int N, int m, const do
                      const double *u0, int max_pass, double tol, int nconv,
                      efe_precision prec, double *eig, double *resid, int *passes);
 
+/* The standard Chebyshev filter with the approximate inverse (Eq. ChebyRecur
+ * applied to A = M~^-1 H^E, the method the residual filter replaces; Sec. III.B,
+ * Fig. 1): Vout = C_m(M~^-1 H^E) V by
+ *   Y_0 = V;  Y_1 = (s1/e)(M~^-1 H V - c V);
+ *   Y_k = (2 s_k/e)(M~^-1 H Y_{k-1} - c Y_{k-1}) - s_{k-1} s_k Y_{k-2},
+ * run in the variables Z_k = M~ Y_k so that it shares every kernel of the
+ * residual filter (no forcing term, Z_0 = M~ V, Vout = M~^-1 Z_m).  Its fixed
+ * points are eigenvectors of M~^-1 H^E, not of (H^E, M^E), and its rounding
+ * error scales with V rather than with the residual.  Arguments as for
+ * efe_filter (no Ritz values). */
+efe_status efe_filter_standard(efe_ctx *ctx, const double *V, const double *HV, int N, int m,
+                               const double bounds[3], efe_precision prec, double *Vout);
+
+/* efe_chfsi with a choice of filter and a per-pass record:
+ * kind = EFE_FILTER_RESIDUAL or EFE_FILTER_STANDARD, optionally or-ed with
+ * EFE_FILTER_KEEP_PRECISION (bf16 passes stay bf16: no switch to FP32 after
+ * a pass that does not reduce the residual).  history: host max_pass doubles
+ * or NULL; entry j is max(resid[0:nconv]) after pass j + 1.  Other arguments
+ * and errors as for efe_chfsi (EFE_ERR_ARG for unknown kind bits). */
+enum { EFE_FILTER_RESIDUAL = 0, EFE_FILTER_STANDARD = 1, EFE_FILTER_KEEP_PRECISION = 2 };
+efe_status efe_chfsi_kind(efe_ctx *ctx, double *X, double *HX, int N, int m, const double *bounds,
+                          const double *u0, int max_pass, double tol, int nconv, efe_precision prec,
+                          int kind, double *eig, double *resid, int *passes, double *history);
+
 /* Same filter with host buffers (V, HV, Vout: host rows x N; lam: host N):
  * copies in, filters, copies out on the library stream, returns when done.
  * The device copies (3 rows x N + N doubles) stay allocated in the context

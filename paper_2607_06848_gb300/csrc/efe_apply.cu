@@ -359,8 +359,8 @@ __global__ void k_gather(MeshDev m, long long n_nodes, int N, const float *Yc, i
 // coordinates and coupling lists are read once per row, lanes run over the
 // columns).  All arithmetic is FP32; the values feed bf16 products.
 // ---------------------------------------------------------------------------
-__global__ void k_to_float_strided(int rows, int N, const double *x, float *y, int ldy) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_to_float_strided(long long rows, int N, const double *x, float *y, int ldy) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= rows * N) return;
     y[(size_t)(idx / N) * ldy + idx % N] = (float)x[idx];
 }
@@ -392,13 +392,11 @@ __device__ __forceinline__ AxisCells axis_cells(int i, int p, int nc) {
     return a;
 }
 
-// Xb[n][4q..4q+3] = bf16( minv[n] Z[n] - sum_e C_e . Ye[atom(e)] ) (ldb >= ldz, padding zero)
+// Xb[n][4q..4q+3] = bf16( minv[n] Z[n] ) at interior nodes, zero at the
+// Dirichlet nodes and in the padding columns (ldb >= ldz)
 __global__ void __launch_bounds__(256) k_pre_bf16_w(MeshDev m, int nruns_x, const float *__restrict__ Z, int ldz,
-                                                    const float *__restrict__ Ye, int lde, int ldb,
-                                                    const double *__restrict__ minv,
-                                                    const long long *__restrict__ node_ptr,
-                                                    const int *__restrict__ nm_atom, const float *__restrict__ nm_C,
-                                                    int use_c, __nv_bfloat16 *__restrict__ Xb) {
+                                                    int ldb, const double *__restrict__ minv,
+                                                    __nv_bfloat16 *__restrict__ Xb) {
     const int lane = threadIdx.x & 31;
     const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nrows = (long long)m.Gy * m.Gz;
@@ -419,24 +417,9 @@ __global__ void __launch_bounds__(256) k_pre_bf16_w(MeshDev m, int nruns_x, cons
         const int j = 4 * cg;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (yz_in && ix > 0 && ix < m.Gx - 1 && j < ldz) {
-            long long e0 = 0, e1 = 0;
-            if (use_c) {
-                e0 = node_ptr[n];
-                e1 = node_ptr[n + 1];
-            }
             const float mi = (float)minv[n];
             v = f4(Z + (size_t)n * ldz + j);
             v.x *= mi; v.y *= mi; v.z *= mi; v.w *= mi;
-            {
-                for (long long e = e0; e < e1; ++e) {
-                    const float4 cc = f4(nm_C + 4 * e);
-                    const float *yb = Ye + (4 * nm_atom[e]) * lde + j;
-                    fma4(v, -cc.x, f4(yb));
-                    fma4(v, -cc.y, f4(yb + lde));
-                    fma4(v, -cc.z, f4(yb + 2 * lde));
-                    fma4(v, -cc.w, f4(yb + 3 * lde));
-                }
-            }
         }
         __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
         uint2 pk;
@@ -450,18 +433,18 @@ __global__ void __launch_bounds__(256) k_pre_bf16_w(MeshDev m, int nruns_x, cons
 
 // One recurrence step at the FE nodes of a run, fused with the gather of the
 // cell products and the FE-enrichment coupling:
-//   HY[n] = sum over the cells of n of Y_cell[row(n)] + sum_e (Hca_e . Ye + Pc_e . W)
+//   HY[n] = sum over the cells of n of Y_cell[row(n)] + sum_e (E_e . Ye + Pc_e . W)
 //   Zn[n] = a (HY[n] - c Z1[n]) - b Z0[n] + a G[n] ck      (Eq. residualapprox)
-// HY is kept at support nodes (HYs) for the enrichment rows.
+// with E the FE-enrichment block of H^E (E^T Ye is the enrichment's part of
+// the FE rows).
 __global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x, int ldz, const float *__restrict__ Yc,
                                                       int ldy, const long long *__restrict__ node_ptr,
-                                                      const int *__restrict__ nm_atom, const float *__restrict__ Hca,
+                                                      const int *__restrict__ nm_atom, const float *__restrict__ Ec,
                                                       const float *__restrict__ Pc, const float *__restrict__ Ye,
                                                       const float *__restrict__ W, int lde, int use_h, int use_p,
                                                       const float *__restrict__ Z1, const float *__restrict__ Z0,
                                                       const float *__restrict__ G, const float *__restrict__ ck,
-                                                      float a, float c, float b, float *__restrict__ Zn,
-                                                      float *__restrict__ HYs) {
+                                                      float a, float c, float b, float *__restrict__ Zn) {
     const int lane = threadIdx.x & 31;
     const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nrows = (long long)m.Gy * m.Gz;
@@ -524,12 +507,11 @@ __global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x,
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int u = 0; u < 8; ++u) { acc.x += y[u].x; acc.y += y[u].y; acc.z += y[u].z; acc.w += y[u].w; }
-            const int cnt = (int)(e1 - e0);
             {
                 for (long long e = e0; e < e1; ++e) {
                     const int rb = (4 * nm_atom[e]) * lde + j;
                     if (use_h) {
-                        const float4 h = f4(Hca + 4 * e);
+                        const float4 h = f4(Ec + 4 * e);
                         const float *yb = Ye + rb;
                         fma4(acc, h.x, f4(yb));
                         fma4(acc, h.y, f4(yb + lde));
@@ -552,7 +534,6 @@ __global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x,
             zn.z = a * (acc.z - c * z1.z) - b * z0.z + a * gg.z * kk.z;
             zn.w = a * (acc.w - c * z1.w) - b * z0.w + a * gg.w * kk.w;
             *reinterpret_cast<float4 *>(Zn + row) = zn;
-            if (cnt > 0) *reinterpret_cast<float4 *>(HYs + row) = acc;
         }
         cg += 32;
         while (cg >= ncg) { cg -= ncg; ++k; }
@@ -562,18 +543,12 @@ __global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x,
 // Support reduction: warps over positions (8 rows in flight per warp), lanes
 // over 4-column vectors (two 128-column slots), one block per (chunk, atom).
 __device__ inline float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-__device__ inline float4 ld4(const __nv_bfloat16 *p) {
-    const uint2 u = *reinterpret_cast<const uint2 *>(p);
-    const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162 *>(&u.x);
-    const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162 *>(&u.y);
-    const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
-    return make_float4(a.x, a.y, b.x, b.y);
-}
 
 template <typename T>
 __global__ void __launch_bounds__(256, 4) k_support_reduce3(const long long *sup_off, const int *sup_node,
                                                          const float *coefA, const float *coefB, const T *S,
-                                                         int N, int ld, int chunk, int nch, double *part) {
+                                                         const double *scale, int N, int ld, int chunk, int nch,
+                                                         double *part) {
     // thread t: float4 column group cg = t % ncg, position lane pl = t / ncg
     __shared__ float acc[8][256];
     const int I = blockIdx.y;
@@ -596,8 +571,13 @@ __global__ void __launch_bounds__(256, 4) k_support_reduce3(const long long *sup
             for (int u = 0; u < 4; ++u) nodes[u] = (g0 + u < end) ? sup_node[g0 + u] : -1;
             float4 sv[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u) {
                 sv[u] = nodes[u] >= 0 ? ld4(S + (long long)nodes[u] * ld + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (scale && nodes[u] >= 0) {
+                    const float sc = (float)scale[nodes[u]];
+                    sv[u].x *= sc; sv[u].y *= sc; sv[u].z *= sc; sv[u].w *= sc;
+                }
+            }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 if (nodes[u] < 0) continue;
@@ -661,7 +641,7 @@ __global__ void k_enr_rec_v(int n_enr, int N, int ldz, const double *Yraw, const
     const int k = idx / ldz, j = idx % ldz;
     const size_t o = (size_t)k * ldz + j;
     if (j >= N) { Zn[o] = 0.f; return; }
-    const float hy = (float)(Yraw[(size_t)k * N + j] - Q[(size_t)k * N + j]);
+    const float hy = (float)(Yraw[(size_t)k * N + j] - (Q ? Q[(size_t)k * N + j] : 0.0));
     const float z0 = Z0 ? Z0[o] : 0.f;
     Zn[o] = a * (hy - c * Z1[o]) - b * z0 + a * G[o] * ck[j];
 }
@@ -742,6 +722,18 @@ template <typename T>
 __global__ void k_scale_to(long long n, double s, const double *G, T *Z) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx < n) Z[idx] = (T)(s * G[idx]);
+}
+// Standard filter start, written in the residual variables Z = M~ Y:
+// Z_0 = M~ V, Z_1 = (s1/e)(H V - c M~ V); G holds H V - c M~ V
+template <typename T>
+__global__ void k_std_start(long long n, double c, double s1e, const double *HV, const double *MtV, double *G,
+                            T *Z0, T *Z1) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const double g = HV[idx] - c * MtV[idx];
+    G[idx] = g;
+    Z0[idx] = (T)MtV[idx];
+    Z1[idx] = (T)(s1e * g);
 }
 // Vout = Y + V diag(cm)   (Y = M~^-1 Z_m)
 template <typename T>
@@ -1209,7 +1201,7 @@ struct Carver {
 
 template <typename T>
 efe_status filter_impl(efe_ctx *ctx, const double *V, const double *HV, const double *lam_dev, int N, int m,
-                       const double bounds[3], double *Vout, bool tensor = false) {
+                       const double bounds[3], double *Vout, bool tensor = false, bool standard = false) {
     const long long rows = ctx->n_rows, nn = ctx->n_nodes;
     const long long n = rows * N;
     const double a0 = bounds[0], a = bounds[1], b = bounds[2];
@@ -1217,11 +1209,15 @@ efe_status filter_impl(efe_ctx *ctx, const double *V, const double *HV, const do
         ctx->err = "filter bounds must satisfy a0 < a < b";
         return EFE_ERR_ARG;
     }
-    std::vector<double> lam(N);
-    EFE_CUDA(ctx, cudaMemcpyAsync(lam.data(), lam_dev, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
-    EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<double> lam(N, 0.0);   // the standard filter passes no Ritz values
+    if (lam_dev) {
+        EFE_CUDA(ctx, cudaMemcpyAsync(lam.data(), lam_dev, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
+        EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
     std::vector<double> ck, sig;
     cheb_table(m, N, lam.data(), a, b, a0, ck, sig);
+    // the standard filter has no forcing term and no V diag(C_m) part
+    if (standard) std::fill(ck.begin(), ck.end(), 0.0);
     const double e = 0.5 * (b - a), c = 0.5 * (b + a);
     const int ldb = (N + 7) / 8 * 8, ldy = (N + 3) / 4 * 4;
     const long long ncells = (long long)ctx->m.nx * ctx->m.ny * ctx->m.nz;
@@ -1244,11 +1240,18 @@ efe_status filter_impl(efe_ctx *ctx, const double *V, const double *HV, const do
     ctx->cell_launches = 0;
     Timer tm(ctx->stream);
     const long long l0 = ctx->launches;
-    EFE_TRY(m_apply(ctx, V, MV, N, true));
-    k_eig_residual<<<nblk(n, 256), 256, 0, ctx->stream>>>(rows, N, HV, MV, lam_dev, G);
-    k_scale_to<T><<<nblk(n, 256), 256, 0, ctx->stream>>>(n, sig[1] / e, G, Z1);
-    ctx->launches += 2;
     T *Zprev = nullptr, *Zcur = Z1, *Znext = Z2, *Zspare = Z0;
+    if (standard) {
+        EFE_TRY(m_apply(ctx, V, MV, N, false));
+        k_std_start<T><<<nblk(n, 256), 256, 0, ctx->stream>>>(n, c, sig[1] / e, HV, MV, G, Z0, Z1);
+        ctx->launches++;
+        Zprev = Z0;
+    } else {
+        EFE_TRY(m_apply(ctx, V, MV, N, true));
+        k_eig_residual<<<nblk(n, 256), 256, 0, ctx->stream>>>(rows, N, HV, MV, lam_dev, G);
+        k_scale_to<T><<<nblk(n, 256), 256, 0, ctx->stream>>>(n, sig[1] / e, G, Z1);
+        ctx->launches += 2;
+    }
     const T *He = std::is_same<T, double>::value ? (const T *)ctx->d_He : (const T *)ctx->d_He32;
     for (int k = 2; k <= m; ++k) {
         EFE_TRY(mtilde_inv<T>(ctx, Zcur, Y, N));
@@ -1298,7 +1301,7 @@ efe_status filter_impl(efe_ctx *ctx, const double *V, const double *HV, const do
 // bf16 producer of T M~^-1 Z, the tensor-core cell products, the coupling
 // reductions, and the fused gather + recurrence.
 static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV, const double *lam_dev, int N,
-                                int m, const double bounds[3], double *Vout) {
+                                int m, const double bounds[3], double *Vout, bool standard) {
     const MeshDev &mh = ctx->m;
     const long long rows = ctx->n_rows, nn = ctx->n_nodes;
     const int ne_ = ctx->n_enr;
@@ -1312,34 +1315,45 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
         return EFE_ERR_ARG;
     }
     if (!ctx->he16_valid) EFE_TRY(efe_tc_prepare(ctx));
-    std::vector<double> lam(N);
-    EFE_CUDA(ctx, cudaMemcpyAsync(lam.data(), lam_dev, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
-    EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<double> lam(N, 0.0);   // the standard filter passes no Ritz values
+    if (lam_dev) {
+        EFE_CUDA(ctx, cudaMemcpyAsync(lam.data(), lam_dev, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
+        EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
     std::vector<double> ck, sig;
     cheb_table(m, N, lam.data(), a, b, a0, ck, sig);
     const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+    // the standard filter: no forcing term, no V diag(C_m) part, and the start
+    // residual formed with the constant c in place of the Ritz values
+    std::vector<double> cvec;
+    if (standard) {
+        std::fill(ck.begin(), ck.end(), 0.0);
+        cvec.assign(N, c);
+    }
     const int ldz = (N + 3) / 4 * 4, ldb = (N + 7) / 8 * 8, ldy = ldz, lde = ldz;
     std::vector<float> ckf((size_t)(m + 1) * ldz, 0.f);
     for (int k = 0; k <= m; ++k)
         for (int j = 0; j < N; ++j) ckf[(size_t)k * ldz + j] = (float)ck[(size_t)k * N + j];
     const long long ncells = (long long)mh.nx * mh.ny * mh.nz;
     const size_t nz = (size_t)rows * ldz;
-    size_t need = 16384 + sizeof(double) * (size_t)rows * N + sizeof(double) * (size_t)(m + 1) * N +
-                  sizeof(float) * ckf.size() + sizeof(float) * (4 * nz + (size_t)nn * ldz) +
+    size_t need = 16384 + sizeof(double) * (size_t)rows * N + sizeof(double) * (size_t)(m + 2) * N +
+                  sizeof(float) * ckf.size() + sizeof(float) * 4 * nz +
                   sizeof(float) * 2 * ((size_t)std::max(ne_, ctx->n_proj) * lde + 4) + 2 * (size_t)nn * ldb +
                   4 * (size_t)ncells * mh.ne * ldy;
     EFE_TRY(efe_workspace(ctx, need));
     Carver cv{(char *)ctx->d_ws, ctx->ws_bytes};
     double *MV = cv.take<double>((size_t)rows * N), *dck = cv.take<double>((size_t)(m + 1) * N);
+    double *dc = cv.take<double>((size_t)N);
     float *fck = cv.take<float>(ckf.size());
     float *G = cv.take<float>(nz), *Z0 = cv.take<float>(nz), *Z1 = cv.take<float>(nz), *Z2 = cv.take<float>(nz);
-    float *HYs = cv.take<float>((size_t)nn * ldz);
     float *Ye = cv.take<float>((size_t)std::max(ne_, 1) * lde + 4);
     float *W32 = cv.take<float>((size_t)std::max(ctx->n_proj, 1) * lde + 4);
     __nv_bfloat16 *Xb = cv.take<__nv_bfloat16>((size_t)nn * ldb);
     float *Ycells = cv.take<float>((size_t)ncells * mh.ne * ldy);
     EFE_CUDA(ctx, cudaMemcpyAsync(dck, ck.data(), sizeof(double) * ck.size(), cudaMemcpyHostToDevice, ctx->stream));
     EFE_CUDA(ctx, cudaMemcpyAsync(fck, ckf.data(), sizeof(float) * ckf.size(), cudaMemcpyHostToDevice, ctx->stream));
+    if (standard)
+        EFE_CUDA(ctx, cudaMemcpyAsync(dc, cvec.data(), sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
     EFE_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
     EFE_CUDA(ctx, cudaMemsetAsync(Ye, 0, sizeof(float) * ((size_t)std::max(ne_, 1) * lde + 4), ctx->stream));
     EFE_CUDA(ctx, cudaMemsetAsync(W32, 0, sizeof(float) * ((size_t)std::max(ctx->n_proj, 1) * lde + 4), ctx->stream));
@@ -1354,10 +1368,18 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     ctx->cell_launches = 0;
     Timer tm(ctx->stream);
     const long long l0 = ctx->launches;
-    EFE_TRY(m_apply(ctx, V, MV, N, true));
-    k_rows_residual_f<<<rb_all, 256, 0, ctx->stream>>>(rows, N, ldz, HV, MV, lam_dev, (float)(sig[1] / e), G, Z1);
+    EFE_TRY(m_apply(ctx, V, MV, N, !standard));
+    k_rows_residual_f<<<rb_all, 256, 0, ctx->stream>>>(rows, N, ldz, HV, MV, standard ? dc : lam_dev,
+                                                       (float)(sig[1] / e), G, Z1);
     ctx->launches++;
     float *Zprev = nullptr, *Zcur = Z1, *Znext = Z2, *Zspare = Z0;
+    if (standard) {
+        // Z_0 = M~ V in FP32 (padding columns zero)
+        EFE_CUDA(ctx, cudaMemsetAsync(Z0, 0, sizeof(float) * nz, ctx->stream));
+        k_to_float_strided<<<nblk(rows * N, 256), 256, 0, ctx->stream>>>(rows, N, MV, Z0, ldz);
+        ctx->launches++;
+        Zprev = Z0;
+    }
     const dim3 gred(s.nch, std::max(ctx->natoms, 1), 1);
     if (N > 256) {
         ctx->err = "the tensor-core filter takes at most 256 columns per call";
@@ -1371,9 +1393,9 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
                                                                                 Zcur + nn * ldz, Ye, lde);
             ctx->launches++;
         }
-        k_pre_bf16_w<<<rb_run, 256, 0, ctx->stream>>>(mh, nruns_x, Zcur, ldz, Ye, lde, ldb, ctx->d_minv,
-                                                      ctx->d_node_ptr, ctx->d_nm_atom, ctx->d_nm_C32,
-                                                      ctx->enrich ? 1 : 0, Xb);
+        // cell operand: the FE part of Y = M~^-1 Z in bf16 (no T transform: the
+        // enrichment enters through the blocks E and H^E_ee of H^E)
+        k_pre_bf16_w<<<rb_run, 256, 0, ctx->stream>>>(mh, nruns_x, Zcur, ldz, ldb, ctx->d_minv, Xb);
         ctx->launches++;
         EFE_TRY(efe_check_launch(ctx, "k_pre_bf16_w"));
         {
@@ -1383,24 +1405,27 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
             if (ev) cudaEventRecord(ev->second, ctx->stream);
         }
         if (cpl) {
-            k_support_reduce3<__nv_bfloat16><<<gred, 256, 0, ctx->stream>>>(
-                ctx->d_sup_off, ctx->d_sup_node, ctx->enrich ? ctx->d_Hca32 : ctx->d_Pc32,
-                (ctx->enrich && ctx->nonlocal) ? ctx->d_Pc32 : nullptr, Xb, N, ldb, s.chunk, s.nch, s.part);
+            // E Y_c and P_c Y_c over the supports, from the FP32 Z scaled by M^cc^-1
+            k_support_reduce3<float><<<gred, 256, 0, ctx->stream>>>(
+                ctx->d_sup_off, ctx->d_sup_node, ctx->enrich ? ctx->d_E32 : ctx->d_Pc32,
+                (ctx->enrich && ctx->nonlocal) ? ctx->d_Pc32 : nullptr, Zcur, ctx->d_minv, N, ldz, s.chunk, s.nch,
+                s.part);
             const long long n8 = (long long)ctx->natoms * 8 * N;
             k_support_sum<<<nblk(n8, 256), 256, 0, ctx->stream>>>(ctx->natoms, s.nch, N, s.part,
                                                                   ctx->enrich ? s.Rh : s.Wc,
                                                                   (ctx->enrich && ctx->nonlocal) ? s.Wc : nullptr);
             ctx->launches += 2;
+            // W = D (P_c Y_c + P^E Y_e); enriched rows E Y_c + H^E_ee Y_e + P^E^T W
             if (ctx->nonlocal) {
                 k_proj_w<float><<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
-                    ctx->n_proj, ne_, s.Wc, ctx->enrich ? ctx->d_Pa : nullptr, Ye, lde, ctx->d_hproj, N, s.W);
+                    ctx->n_proj, ne_, s.Wc, ctx->enrich ? ctx->d_PE : nullptr, Ye, lde, ctx->d_hproj, N, s.W);
                 k_to_float_strided<<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
                     ctx->n_proj, N, s.W, W32, lde);
                 ctx->launches += 2;
             }
             if (ctx->enrich) {
                 k_enr_raw<float><<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(
-                    ne_, ctx->n_proj, s.Rh, ctx->d_Haa, ctx->nonlocal ? ctx->d_Pa : nullptr, s.W, Ye, lde, N,
+                    ne_, ctx->n_proj, s.Rh, ctx->d_HEee, ctx->nonlocal ? ctx->d_PE : nullptr, s.W, Ye, lde, N,
                     s.Yraw);
                 ctx->launches++;
             }
@@ -1408,22 +1433,18 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
         auto *rev = rec_event_pair(ctx);
         if (rev) cudaEventRecord(rev->first, ctx->stream);
         k_gather_rec_w<<<rb_run, 256, 0, ctx->stream>>>(mh, nruns_x, ldz, Ycells, ldy, cpl ? ctx->d_node_ptr : nullptr,
-                                                        ctx->d_nm_atom, ctx->d_nm_H32, ctx->d_nm_P32,
+                                                        ctx->d_nm_atom, ctx->d_nm_E32, ctx->d_nm_P32,
                                                         Ye, W32, lde, ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0,
                                                         Zcur, Zprev, G, fck + (size_t)(k - 1) * ldz, ak, cf, bk,
-                                                        Znext, HYs);
+                                                        Znext);
         if (rev) cudaEventRecord(rev->second, ctx->stream);
         ctx->launches++;
         EFE_TRY(efe_check_launch(ctx, "k_gather_rec_w"));
         if (ne_) {
-            k_support_reduce3<float><<<gred, 256, 0, ctx->stream>>>(ctx->d_sup_off, ctx->d_sup_node, ctx->d_C32,
-                                                                    nullptr, HYs, N, ldz, s.chunk, s.nch, s.part);
-            const long long n8 = (long long)ctx->natoms * 8 * N;
-            k_support_sum<<<nblk(n8, 256), 256, 0, ctx->stream>>>(ctx->natoms, s.nch, N, s.part, s.Q, nullptr);
             k_enr_rec_v<<<nblk((long long)ne_ * ldz, 256), 256, 0, ctx->stream>>>(
-                ne_, N, ldz, s.Yraw, s.Q, Zcur + nn * ldz, Zprev ? Zprev + nn * ldz : nullptr, G + nn * ldz,
+                ne_, N, ldz, s.Yraw, nullptr, Zcur + nn * ldz, Zprev ? Zprev + nn * ldz : nullptr, G + nn * ldz,
                 fck + (size_t)(k - 1) * ldz, ak, cf, bk, Znext + nn * ldz);
-            ctx->launches += 3;
+            ctx->launches++;
         }
         float *old_prev = Zprev ? Zprev : Zspare;
         Zprev = Zcur;
@@ -1456,10 +1477,10 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
 }
 
 efe_status efe_filter_dispatch(efe_ctx *ctx, const double *V, const double *HV, const double *lam, int N, int m,
-                               const double bounds[3], efe_precision prec, double *Vout) {
-    if (prec == EFE_FP64) return filter_impl<double>(ctx, V, HV, lam, N, m, bounds, Vout);
-    if (prec == EFE_FP32) return filter_impl<float>(ctx, V, HV, lam, N, m, bounds, Vout);
-    if (prec == EFE_BF16) return filter_tensor(ctx, V, HV, lam, N, m, bounds, Vout);
+                               const double bounds[3], efe_precision prec, double *Vout, bool standard = false) {
+    if (prec == EFE_FP64) return filter_impl<double>(ctx, V, HV, lam, N, m, bounds, Vout, false, standard);
+    if (prec == EFE_FP32) return filter_impl<float>(ctx, V, HV, lam, N, m, bounds, Vout, false, standard);
+    if (prec == EFE_BF16) return filter_tensor(ctx, V, HV, lam, N, m, bounds, Vout, standard);
     ctx->err = "unknown precision";
     return EFE_ERR_ARG;
 }
@@ -1659,9 +1680,9 @@ void efe_destroy(efe_ctx *ctx) {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     efe_scf_free(ctx);
-    void *ptrs[] = {ctx->d_nm_atom, ctx->d_nm_C32, ctx->d_nm_H32, ctx->d_nm_P32, ctx->d_hostio, ctx->d_B1, ctx->d_D1, ctx->d_wq, ctx->d_Khat, ctx->d_mcc, ctx->d_minv, ctx->d_He, ctx->d_He32,
+    void *ptrs[] = {ctx->d_nm_atom, ctx->d_nm_E32, ctx->d_nm_P32, ctx->d_E, ctx->d_PE, ctx->d_HEee, ctx->d_hostio, ctx->d_B1, ctx->d_D1, ctx->d_wq, ctx->d_Khat, ctx->d_mcc, ctx->d_minv, ctx->d_He, ctx->d_He32,
                     ctx->d_He16, ctx->d_atoms, ctx->d_hproj, ctx->d_sup_off, ctx->d_sup_node, ctx->d_C, ctx->d_B,
-                    ctx->d_Kca, ctx->d_Hca, ctx->d_Pc, ctx->d_C32, ctx->d_Hca32, ctx->d_Pc32, ctx->d_node_ptr,
+                    ctx->d_Kca, ctx->d_Hca, ctx->d_Pc, ctx->d_E32, ctx->d_Pc32, ctx->d_node_ptr,
                     ctx->d_node_ent, ctx->d_ent_atom,
                     ctx->d_pairs, ctx->d_pair_pos, ctx->d_cell_atom_ptr, ctx->d_cell_atoms, ctx->d_Aee, ctx->d_Kaa,
                     ctx->d_Haa, ctx->d_Mee, ctx->d_Pa, ctx->d_Mblk_inv, ctx->d_Mblk, ctx->d_ws, ctx->d_part,
@@ -1905,6 +1926,18 @@ efe_status efe_filter(efe_ctx *ctx, const double *V, const double *HV, const dou
     return efe_filter_dispatch(ctx, V, HV, lam, N, m, bounds, prec, Vout);
 }
 
+efe_status efe_filter_standard(efe_ctx *ctx, const double *V, const double *HV, int N, int m,
+                               const double bounds[3], efe_precision prec, double *Vout) {
+    EFE_CHECK_CTX(ctx);
+    EFE_ARG(ctx, V && HV && bounds && Vout && N > 0 && m >= 1 && Vout != V && Vout != HV,
+            "efe_filter_standard: bad arguments");
+    if (!ctx->have_potential) {
+        ctx->err = "efe_filter_standard: no potential set";
+        return EFE_ERR_STATE;
+    }
+    return efe_filter_dispatch(ctx, V, HV, nullptr, N, m, bounds, prec, Vout, true);
+}
+
 efe_status efe_rayleigh_ritz(efe_ctx *ctx, double *X, double *HX, int N, double *eig, double *resid) {
     EFE_CHECK_CTX(ctx);
     EFE_ARG(ctx, X && HX && eig && N > 0 && X != HX, "efe_rayleigh_ritz: bad arguments");
@@ -1918,9 +1951,18 @@ efe_status efe_rayleigh_ritz(efe_ctx *ctx, double *X, double *HX, int N, double 
 efe_status efe_chfsi(efe_ctx *ctx, double *X, double *HX, int N, int m, const double *bounds, const double *u0,
                      int max_pass, double tol, int nconv, efe_precision prec, double *eig, double *resid,
                      int *passes) {
+    return efe_chfsi_kind(ctx, X, HX, N, m, bounds, u0, max_pass, tol, nconv, prec, EFE_FILTER_RESIDUAL, eig,
+                          resid, passes, nullptr);
+}
+
+efe_status efe_chfsi_kind(efe_ctx *ctx, double *X, double *HX, int N, int m, const double *bounds,
+                          const double *u0, int max_pass, double tol, int nconv, efe_precision prec, int kind,
+                          double *eig, double *resid, int *passes, double *history) {
     EFE_CHECK_CTX(ctx);
-    EFE_ARG(ctx, X && eig && resid && N > 0 && m >= 1 && max_pass >= 0 && (bounds || u0),
+    EFE_ARG(ctx, X && eig && resid && N > 0 && m >= 1 && max_pass >= 0 && (bounds || u0) &&
+                     (kind & ~(EFE_FILTER_STANDARD | EFE_FILTER_KEEP_PRECISION)) == 0,
             "efe_chfsi: bad arguments");
+    const bool standard = (kind & EFE_FILTER_STANDARD) != 0;
     if (!ctx->have_potential) {
         ctx->err = "efe_chfsi: no potential set";
         return EFE_ERR_STATE;
@@ -1971,7 +2013,10 @@ efe_status efe_chfsi(efe_ctx *ctx, double *X, double *HX, int N, int m, const do
             cleanup();
             return EFE_ERR_CUDA;
         }
-        if ((st = efe_filter_dispatch(ctx, X, dHX, dlam, N, m, bd, pp, dVout)) != EFE_OK) { cleanup(); return st; }
+        if ((st = efe_filter_dispatch(ctx, X, dHX, dlam, N, m, bd, pp, dVout, standard)) != EFE_OK) {
+            cleanup();
+            return st;
+        }
         ms_filter += ctx->stats.ms_filter;
         if ((st = efe_rr_impl(ctx, dVout, dHX, N, eig, resid)) != EFE_OK) { cleanup(); return st; }
         ms_rr += ctx->stats.ms_rr;
@@ -1982,7 +2027,8 @@ efe_status efe_chfsi(efe_ctx *ctx, double *X, double *HX, int N, int m, const do
         ++pass;
         double mx = 0.0;
         for (int j = 0; j < nconv; ++j) mx = std::max(mx, resid[j]);
-        if (pp == EFE_BF16 && !(mx < prev_mx)) pp = EFE_FP32;
+        if (history) history[pass - 1] = mx;
+        if (pp == EFE_BF16 && !(mx < prev_mx) && !(kind & EFE_FILTER_KEEP_PRECISION)) pp = EFE_FP32;
         prev_mx = mx;
         bd[0] = eig[0];
         bd[1] = eig[N - 1];

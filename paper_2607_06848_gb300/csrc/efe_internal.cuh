@@ -67,10 +67,15 @@ struct efe_ctx {
     double *d_Kca = nullptr;                  // sup_total x 4 (1/2 grad N . grad a)
     double *d_Hca = nullptr;                  // sup_total x 4 (Kca + Vca)
     double *d_Pc = nullptr;                   // sup_total x 4 (<beta_f, N_j>)
-    float *d_C32 = nullptr, *d_Hca32 = nullptr, *d_Pc32 = nullptr;   // FP32 copies for the mixed filter
+    // the FE-enrichment block of H^E itself, E = H^ac - C H^cc (sup_total x 4, per
+    // potential): the mixed filter applies H^E through E instead of T^T H_raw T,
+    // whose two large terms cancel when the enrichment is nearly representable
+    // by the FE space
+    double *d_E = nullptr;
+    float *d_E32 = nullptr, *d_Pc32 = nullptr;   // FP32 copies for the mixed filter
     // the same in node-major (CSR) order, with the atom of each entry, for the node kernels
     int *d_nm_atom = nullptr;
-    float *d_nm_C32 = nullptr, *d_nm_H32 = nullptr, *d_nm_P32 = nullptr;
+    float *d_nm_E32 = nullptr, *d_nm_P32 = nullptr;
     // node -> (atom, pos) CSR over all nodes
     long long *d_node_ptr = nullptr;          // n_nodes + 1
     int *d_node_ent = nullptr;                // entries: global support index (sup_off[I] + pos)
@@ -85,6 +90,8 @@ struct efe_ctx {
     // dense enriched blocks (n_enr x n_enr), projector blocks
     double *d_Aee = nullptr, *d_Kaa = nullptr, *d_Haa = nullptr, *d_Mee = nullptr;
     double *d_Pa = nullptr;                   // n_proj x n_enr
+    double *d_PE = nullptr;                   // n_proj x n_enr: <beta_p, N^E_k> = Pa - Pc C^T
+    double *d_HEee = nullptr;                 // n_enr x n_enr: H^E_ee (local part), per potential
     double *d_Mblk_inv = nullptr;             // natoms x 16
     double *d_Mblk = nullptr;                 // natoms x 16
 

@@ -161,16 +161,14 @@ __global__ void k_static_pairs(MeshDev m, Tables1D T, FuncParams fp, const PairI
 
 // Potential coupling for one pair: Hca[l][f] += int v a_f N_l.
 // node-major copies of the coupling tables (statics on the first call, H^ca always)
-__global__ void k_node_major(long long n, const int *node_ent, const int *ent_atom, const float *C32,
-                             const float *H32, const float *P32, int statics, int *nm_atom, float *nm_C,
-                             float *nm_H, float *nm_P) {
+__global__ void k_node_major(long long n, const int *node_ent, const int *ent_atom, const float *E32,
+                             const float *P32, int statics, int *nm_atom, float *nm_E, float *nm_P) {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= n) return;
     const int g = node_ent[e];
-    reinterpret_cast<float4 *>(nm_H)[e] = reinterpret_cast<const float4 *>(H32)[g];
+    if (E32) reinterpret_cast<float4 *>(nm_E)[e] = reinterpret_cast<const float4 *>(E32)[g];
     if (statics) {
         nm_atom[e] = ent_atom[g];
-        reinterpret_cast<float4 *>(nm_C)[e] = reinterpret_cast<const float4 *>(C32)[g];
         reinterpret_cast<float4 *>(nm_P)[e] = reinterpret_cast<const float4 *>(P32)[g];
     }
 }
@@ -308,6 +306,89 @@ __global__ void k_btmb(long long chunk, const long long *sup_off, const int *sup
     for (int i = threadIdx.x; i < 4 * n_enr; i += blockDim.x) {
         double v = acc[i];
         if (v != 0.0) atomicAdd(&out[(size_t)(4 * I + i / n_enr) * n_enr + (i % n_enr)], v);
+    }
+}
+
+// Products of two support tables summed over shared nodes: for atom I
+// (blockIdx.y) and a chunk of its support,
+//   out[4I+f][4J+h] += sum_j A1[g][f] B1[g'][h] + A2[g][f] B2[g'][h]
+// with g the entry of atom I at node j and g' every entry (atom J) at j.
+// Used for C H^ca + E C^T (the enriched block of H^E) and P_c C^T.
+__global__ void k_support_pair_products(long long chunk, const long long *sup_off, const int *sup_node,
+                                        const long long *node_ptr, const int *node_ent, const int *ent_atom,
+                                        int n_enr, const double *A1, const double *B1, const double *A2,
+                                        const double *B2, double *out) {
+    extern __shared__ double acc[];      // 4 x n_enr
+    const int I = blockIdx.y;
+    for (int i = threadIdx.x; i < 4 * n_enr; i += blockDim.x) acc[i] = 0.0;
+    __syncthreads();
+    const long long beg = sup_off[I] + blockIdx.x * chunk;
+    const long long end = min(sup_off[I + 1], beg + chunk);
+    for (long long g = beg + threadIdx.x; g < end; g += blockDim.x) {
+        const int node = sup_node[g];
+        for (long long e = node_ptr[node]; e < node_ptr[node + 1]; ++e) {
+            const int gj = node_ent[e];
+            const int J = ent_atom[gj];
+            for (int f = 0; f < 4; ++f)
+                for (int h = 0; h < 4; ++h) {
+                    double v = A1[4 * g + f] * B1[4 * (size_t)gj + h];
+                    if (A2) v += A2[4 * g + f] * B2[4 * (size_t)gj + h];
+                    atomicAdd(&acc[f * n_enr + 4 * J + h], v);
+                }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * n_enr; i += blockDim.x) {
+        const double v = acc[i];
+        if (v != 0.0) atomicAdd(&out[(size_t)(4 * I + i / n_enr) * n_enr + (i % n_enr)], v);
+    }
+}
+
+// out = A - 0.5 (X + X^T) for n x n (A symmetric): H^E_ee = H^aa - sym(C H^ca + E C^T)
+__global__ void k_sub_sym(int n, const double *A, const double *X, double *out) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * n) return;
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    out[idx] = A[idx] - 0.5 * (X[idx] + X[(size_t)j * n + i]);
+}
+// out = A - X (n_proj x n_enr)
+__global__ void k_sub(long long n, const double *A, const double *X, double *out) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx < n) out[idx] = A[idx] - X[idx];
+}
+
+// The FE-enrichment block of H^E (Eq. Discrete_Eig_Gen_H with T):
+// E = H^ac - C H^cc on the support entries.  For one (atom, cell) pair,
+// subtract H_e C_cell^T from the entries of the cell's nodes; E starts as a
+// copy of H^ac, and the pairs of one colour share no node.
+__global__ void k_orth_coupling(MeshDev m, const PairInfo *pairs, int p0, const int *pair_pos,
+                                const long long *sup_off, const double *He, const double *C, double *E) {
+    extern __shared__ double Cc[];       // ne x 4
+    const PairInfo pr = pairs[p0 + blockIdx.x];
+    const int *pp = pair_pos + (size_t)(p0 + blockIdx.x) * m.ne;
+    const long long gbase = sup_off[pr.atom];
+    for (int l = threadIdx.x; l < m.ne; l += blockDim.x) {
+        const int pos = pp[l];
+        for (int f = 0; f < 4; ++f) Cc[4 * l + f] = pos >= 0 ? C[4 * (gbase + pos) + f] : 0.0;
+    }
+    __syncthreads();
+    const double *H = He + (size_t)pr.cell * m.ne * m.ne;
+    for (int l = threadIdx.x; l < m.ne; l += blockDim.x) {
+        const int pos = pp[l];
+        if (pos < 0) continue;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        for (int l2 = 0; l2 < m.ne; ++l2) {
+            const double h = H[(size_t)l2 * m.ne + l];   // H_e is symmetric: coalesced over l
+            a0 += h * Cc[4 * l2];
+            a1 += h * Cc[4 * l2 + 1];
+            a2 += h * Cc[4 * l2 + 2];
+            a3 += h * Cc[4 * l2 + 3];
+        }
+        double *e = E + 4 * (gbase + pos);
+        e[0] -= a0;
+        e[1] -= a1;
+        e[2] -= a2;
+        e[3] -= a3;
     }
 }
 
@@ -449,9 +530,15 @@ efe_status efe_static_integrals(efe_ctx *ctx) {
     ctx->sup_off.assign(na + 1, 0);
     ctx->pair_colour_off.assign(9, 0);
     if (!any || na == 0) return EFE_OK;
-    double R = 0.0;
-    if (ctx->enrich) R = std::max(R, ctx->r0 * (1.0 + 1.0 / ctx->t));
-    if (ctx->nonlocal) R = std::max(R, ctx->rtrunc);
+    // Support cells of an atom: the cells that meet the projector ball
+    // (r <= rtrunc) and, with enrichment, the cells that meet the enrichment
+    // ball (r <= r_end) together with every cell sharing a node with one of
+    // them.  C is nonzero only at nodes of the first kind of cell, so the
+    // FE-enrichment block of H^E, E = H^ac - C H^cc, is nonzero only at nodes of
+    // the cells around them: the support lists carry every nonzero of E.
+    const double Re = ctx->enrich ? ctx->r0 * (1.0 + 1.0 / ctx->t) : -1.0;
+    const double Rp = ctx->nonlocal ? ctx->rtrunc : -1.0;
+    const double Rmax = std::max(Re, Rp);
     std::vector<std::vector<int>> atom_cells(na);
     std::vector<int> mark(ctx->n_nodes, -1);
     std::vector<int> sup_node;
@@ -460,20 +547,32 @@ efe_status efe_static_integrals(efe_ctx *ctx) {
         const double *X = &ctx->xyz[3 * I];
         int lo[3], hi[3], nc[3] = {m.nx, m.ny, m.nz};
         for (int d = 0; d < 3; ++d) {
-            lo[d] = std::max(0, (int)std::floor((X[d] - R) / m.h) - 1);
-            hi[d] = std::min(nc[d] - 1, (int)std::floor((X[d] + R) / m.h) + 1);
+            lo[d] = std::max(0, (int)std::floor((X[d] - Rmax) / m.h) - 2);
+            hi[d] = std::min(nc[d] - 1, (int)std::floor((X[d] + Rmax) / m.h) + 2);
         }
+        auto meets = [&](int cx, int cy, int cz, double R) {
+            if (R < 0.0) return false;
+            double d2 = 0.0;
+            const int cc[3] = {cx, cy, cz};
+            for (int d = 0; d < 3; ++d) {
+                double a = cc[d] * m.h, b = a + m.h;
+                double qd = std::min(std::max(X[d], a), b) - X[d];
+                d2 += qd * qd;
+            }
+            return d2 <= R * R;
+        };
         for (int cz = lo[2]; cz <= hi[2]; ++cz)
             for (int cy = lo[1]; cy <= hi[1]; ++cy)
                 for (int cx = lo[0]; cx <= hi[0]; ++cx) {
-                    double d2 = 0.0;
-                    int cc[3] = {cx, cy, cz};
-                    for (int d = 0; d < 3; ++d) {
-                        double a = cc[d] * m.h, b = a + m.h;
-                        double qd = std::min(std::max(X[d], a), b) - X[d];
-                        d2 += qd * qd;
-                    }
-                    if (d2 <= R * R) {
+                    bool in = meets(cx, cy, cz, Rp);
+                    for (int dz = -1; dz <= 1 && !in; ++dz)
+                        for (int dy = -1; dy <= 1 && !in; ++dy)
+                            for (int dx = -1; dx <= 1 && !in; ++dx) {
+                                const int ax = cx + dx, ay = cy + dy, az = cz + dz;
+                                if (ax < 0 || ay < 0 || az < 0 || ax >= m.nx || ay >= m.ny || az >= m.nz) continue;
+                                in = meets(ax, ay, az, Re);
+                            }
+                    if (in) {
                         int c = (cz * m.ny + cy) * m.nx + cx;
                         atom_cells[I].push_back(c);
                         cell_atoms[c].push_back(I);
@@ -681,6 +780,24 @@ efe_status efe_static_integrals(efe_ctx *ctx) {
         EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_Mblk_inv, sizeof(double) * 16 * na));
         EFE_CUDA(ctx, cudaMemcpy(ctx->d_Mblk, blk.data(), sizeof(double) * 16 * na, cudaMemcpyHostToDevice));
         EFE_CUDA(ctx, cudaMemcpy(ctx->d_Mblk_inv, binv.data(), sizeof(double) * 16 * na, cudaMemcpyHostToDevice));
+        if (ctx->nonlocal) {
+            // projector overlaps of the orthogonalized functions: P^E = P_a - P_c C^T
+            const size_t PE = (size_t)ctx->n_proj * ne_;
+            double *d_pct = nullptr;
+            EFE_TRY(efe_alloc(ctx, (void **)&d_pct, sizeof(double) * PE));
+            EFE_CUDA(ctx, cudaMemset(d_pct, 0, sizeof(double) * PE));
+            EFE_CUDA(ctx, cudaFuncSetAttribute(k_support_pair_products, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)shb));
+            k_support_pair_products<<<g, 256, shb, ctx->stream>>>(chunk, d_supoff, ctx->d_sup_node, ctx->d_node_ptr,
+                                                                  ctx->d_node_ent, ctx->d_ent_atom, ne_, ctx->d_Pc,
+                                                                  ctx->d_C, nullptr, nullptr, d_pct);
+            EFE_TRY(efe_check_launch(ctx, "k_support_pair_products(PcC)"));
+            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_PE, sizeof(double) * PE));
+            k_sub<<<nblk((long long)PE, 256), 256, 0, ctx->stream>>>((long long)PE, ctx->d_Pa, d_pct, ctx->d_PE);
+            EFE_TRY(efe_check_launch(ctx, "k_sub(PE)"));
+            EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            cudaFree(d_pct);
+        }
     }
     return EFE_OK;
 }
@@ -722,31 +839,59 @@ efe_status efe_potential_assembly(efe_ctx *ctx, const double *veff_q) {
             m, T, fp, ctx->d_cell_atom_ptr, ctx->d_cell_atoms, ctx->d_atoms, veff_q, ctx->n_enr, nullptr,
             nullptr, nullptr, ctx->d_Haa);
         EFE_TRY(efe_check_launch(ctx, "k_enriched_pairs(v)"));
+        // the blocks of H^E that touch the enriched rows, in FP64:
+        //   E = H^ac - C H^cc (support entries), H^E_ee = H^aa - C H^ca - E C^T
+        if (!ctx->d_E) {
+            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_E, sizeof(double) * S4));
+            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_HEee, sizeof(double) * 2 * E2));
+        }
+        EFE_CUDA(ctx, cudaMemcpyAsync(ctx->d_E, ctx->d_Hca, sizeof(double) * S4, cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
+        const size_t sho = sizeof(double) * 4 * m.ne;
+        for (int k = 0; k < 8; ++k) {
+            int n = ctx->pair_colour_off[k + 1] - ctx->pair_colour_off[k];
+            if (!n) continue;
+            k_orth_coupling<<<n, 256, sho, ctx->stream>>>(m, ctx->d_pairs, ctx->pair_colour_off[k], ctx->d_pair_pos,
+                                                          d_supoff, ctx->d_He, ctx->d_C, ctx->d_E);
+            EFE_TRY(efe_check_launch(ctx, "k_orth_coupling"));
+        }
+        double *acc = ctx->d_HEee + E2;       // second half: the products, summed
+        EFE_CUDA(ctx, cudaMemsetAsync(acc, 0, sizeof(double) * E2, ctx->stream));
+        long long maxsup = 0;
+        for (int I = 0; I < ctx->natoms; ++I) maxsup = std::max(maxsup, ctx->sup_off[I + 1] - ctx->sup_off[I]);
+        const long long chunk = 4096;
+        const size_t shb = sizeof(double) * 4 * ctx->n_enr;
+        EFE_CUDA(ctx, cudaFuncSetAttribute(k_support_pair_products, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)shb));
+        dim3 gp((unsigned)std::max<long long>(1, (maxsup + chunk - 1) / chunk), ctx->natoms);
+        k_support_pair_products<<<gp, 256, shb, ctx->stream>>>(chunk, d_supoff, ctx->d_sup_node, ctx->d_node_ptr,
+                                                               ctx->d_node_ent, ctx->d_ent_atom, ctx->n_enr, ctx->d_C,
+                                                               ctx->d_Hca, ctx->d_E, ctx->d_C, acc);
+        EFE_TRY(efe_check_launch(ctx, "k_support_pair_products(HEee)"));
+        k_sub_sym<<<nblk((long long)E2, 256), 256, 0, ctx->stream>>>(ctx->n_enr, ctx->d_Haa, acc, ctx->d_HEee);
+        EFE_TRY(efe_check_launch(ctx, "k_sub_sym"));
     }
     if ((ctx->enrich || ctx->nonlocal) && ctx->natoms) {
         const long long S4 = 4 * std::max<long long>(ctx->sup_total, 1);
-        if (!ctx->d_Hca32) {
-            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_Hca32, sizeof(float) * S4));
-            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_C32, sizeof(float) * S4));
+        const bool first = ctx->d_Pc32 == nullptr;
+        if (first) {
+            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_E32, sizeof(float) * S4));
             EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_Pc32, sizeof(float) * S4));
-            k_to_float<<<nblk(S4, 256), 256, 0, ctx->stream>>>(S4, ctx->d_C, ctx->d_C32);
             k_to_float<<<nblk(S4, 256), 256, 0, ctx->stream>>>(S4, ctx->d_Pc, ctx->d_Pc32);
         }
-        k_to_float<<<nblk(S4, 256), 256, 0, ctx->stream>>>(S4, ctx->d_Hca, ctx->d_Hca32);
+        if (ctx->enrich) k_to_float<<<nblk(S4, 256), 256, 0, ctx->stream>>>(S4, ctx->d_E, ctx->d_E32);
         EFE_TRY(efe_check_launch(ctx, "k_to_float"));
         // node-major copies: entry e of the node CSR carries its atom and coefficients
         const long long ns = std::max<long long>(ctx->sup_total, 1);
-        const bool first = ctx->d_nm_atom == nullptr;
         if (first) {
             EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_nm_atom, sizeof(int) * ns));
-            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_nm_C32, sizeof(float) * 4 * ns));
-            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_nm_H32, sizeof(float) * 4 * ns));
+            EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_nm_E32, sizeof(float) * 4 * ns));
             EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_nm_P32, sizeof(float) * 4 * ns));
         }
         if (ctx->sup_total > 0) {
             k_node_major<<<nblk(ctx->sup_total, 256), 256, 0, ctx->stream>>>(
-                ctx->sup_total, ctx->d_node_ent, ctx->d_ent_atom, ctx->d_C32, ctx->d_Hca32, ctx->d_Pc32, first ? 1 : 0,
-                ctx->d_nm_atom, ctx->d_nm_C32, ctx->d_nm_H32, ctx->d_nm_P32);
+                ctx->sup_total, ctx->d_node_ent, ctx->d_ent_atom, ctx->enrich ? ctx->d_E32 : nullptr, ctx->d_Pc32,
+                first ? 1 : 0, ctx->d_nm_atom, ctx->d_nm_E32, ctx->d_nm_P32);
             EFE_TRY(efe_check_launch(ctx, "k_node_major"));
         }
     }

@@ -13,6 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libefe.so")
 
 EFE_FP64, EFE_FP32, EFE_BF16 = 0, 1, 2
+EFE_FILTER_RESIDUAL, EFE_FILTER_STANDARD, EFE_FILTER_KEEP_PRECISION = 0, 1, 2
 PRECISIONS = {"fp64": EFE_FP64, "fp32": EFE_FP32, "bf16": EFE_BF16}
 STATUS = {0: "EFE_OK", 1: "EFE_ERR_ARG", 2: "EFE_ERR_CUDA", 3: "EFE_ERR_NOT_SPD",
           4: "EFE_ERR_NO_CONVERGE", 5: "EFE_ERR_TIMEOUT", 6: "EFE_ERR_OOM", 7: "EFE_ERR_STATE"}
@@ -91,6 +92,9 @@ SIGNATURES = {
     "efe_rayleigh_ritz": [_P, _P, _P, _I, _D, _D],
     "efe_chfsi": [_P, _P, _P, _I, _I, _D, _P, _I, ctypes.c_double, _I, _I, _D, _D, ctypes.POINTER(_I)],
     "efe_filter_host": [_P, _D, _D, _D, _I, _I, _D, _I, _D],
+    "efe_filter_standard": [_P, _P, _P, _I, _I, _D, _I, _P],
+    "efe_chfsi_kind": [_P, _P, _P, _I, _I, _D, _P, _I, ctypes.c_double, _I, _I, _I, _D, _D,
+                       ctypes.POINTER(_I), _D],
     "efe_smeared_charge": [_P, _P],
     "efe_atomic_density": [_P, ctypes.c_double, _P],
     "efe_density": [_P, _P, _I, _D, _P],
@@ -241,6 +245,11 @@ class EFE:
         self._check(self.lib.efe_filter(self.ctx, _ptr(V), _ptr(HV), _ptr(lam), V.shape[1], int(m), b,
                                         int(prec), _ptr(Vout)))
 
+    def efe_filter_standard(self, V, HV, m, bounds, Vout, prec=EFE_FP64):
+        b = (ctypes.c_double * 3)(*[float(x) for x in bounds])
+        self._check(self.lib.efe_filter_standard(self.ctx, _ptr(V), _ptr(HV), V.shape[1], int(m), b,
+                                                 int(prec), _ptr(Vout)))
+
     def efe_rayleigh_ritz(self, X, HX):
         N = X.shape[1]
         eig = (ctypes.c_double * N)()
@@ -259,6 +268,23 @@ class EFE:
         if st not in (0, 4):
             self._check(st)
         return np.array(eig[:]), np.array(res[:]), passes.value, st == 0
+
+    def efe_chfsi_kind(self, X, m, kind=EFE_FILTER_RESIDUAL, bounds=None, u0=None, max_pass=20, tol=1e-8,
+                       nconv=0, prec=EFE_FP64, HX=None):
+        """efe_chfsi with a choice of filter; also returns the per-pass max residual."""
+        N = X.shape[1]
+        eig = (ctypes.c_double * N)()
+        res = (ctypes.c_double * N)()
+        hist = (ctypes.c_double * max(int(max_pass), 1))()
+        passes = ctypes.c_int(0)
+        b = None if bounds is None else (ctypes.c_double * 3)(*[float(x) for x in bounds])
+        st = self.lib.efe_chfsi_kind(self.ctx, _ptr(X), _ptr(HX), N, int(m), b, _ptr(u0), int(max_pass),
+                                     float(tol), int(nconv), int(prec), int(kind), eig, res,
+                                     ctypes.byref(passes), hist)
+        if st not in (0, 4):
+            self._check(st)
+        return (np.array(eig[:]), np.array(res[:]), passes.value, st == 0,
+                np.array(hist[:passes.value]))
 
     def efe_filter_host(self, V, HV, lam, m, bounds, prec=EFE_FP64, out=None):
         """Host arrays in and out (the library copies on its stream); out: an optional

@@ -99,6 +99,34 @@ def test_filter_pass_bf16_vs_oracle():
     assert rel < bound, (rel, bound)
 
 
+def test_filter_pass_bf16_near_redundant_enrichment():
+    # At p = 6, h = 40/24 the Gaussian enrichment is almost in the FE space
+    # (M^ee ~ 1e-5 A_ee), so the enriched coordinates are large and the
+    # T^T H_raw T form of H^E cancels two large terms.  The bf16 filter applies
+    # H^E through its blocks E = H^ac - C H^cc and H^E_ee (FP64-assembled);
+    # its error must still scale with the residual.
+    o, g = TP._systems("p6_enriched")
+    ratio = np.linalg.eigvalsh(o.Mee).min() / np.linalg.eigvalsh(o.Aee).min()
+    assert ratio < 1e-4, ratio
+    m = 12
+    # the four lowest states converge quickly; the next ones form a slow cluster
+    X = TP._rand(o, 12, 181)
+    conv = OC.chfsi(o, X, m, 1e-5, 30, TP._rand(o, 1, 182), nconv=4)
+    V, lam, HV = (np.ascontiguousarray(conv["V"][:, :4]), conv["lam"][:4],
+                  np.ascontiguousarray(conv["HV"][:, :4]))
+    a0, a, b = conv["bounds"]
+    ref = OC.residual_filter(o, V, lam, m, a, b, a0, HV=HV)
+    Vd = torch.tensor(V, device="cuda")
+    out = torch.empty_like(Vd)
+    g.efe_filter(Vd, torch.tensor(HV, device="cuda"), torch.tensor(lam, device="cuda"), m, (a0, a, b), out,
+                 prec=2)
+    resid = float(np.max(conv["resid"][:4]))
+    assert resid < 1e-5
+    rel = TP._rel(out.cpu().numpy(), ref)
+    # each of the m steps rounds Z ~ G once (x4 margin)
+    assert rel < 4 * m * 2.0 ** -8 * resid, (rel, resid)
+
+
 _C64 = {}
 
 
@@ -200,3 +228,27 @@ def test_cluster64_sampled_rows_against_oracle():
         scale = np.abs(row).max()
         assert np.max(np.abs(Yg64[node] - row)) < 1e-12 * max(scale, 1.0), node
         assert np.max(np.abs(Yg16[node] - row)) < 1e-2 * max(scale, 1.0), node
+
+
+def test_cluster64_filter_bf16_vs_fp32():
+    # the benchmark's configuration: 64 atoms, 24^3 cells of degree 6, 154
+    # vectors, degree 30; the bf16 filter against the FP32 one (whose parity
+    # with the oracle is tested on the small meshes) from the Ritz vectors of
+    # a random block
+    g, w, v = _cluster64()
+    rows, N, m = g.dims["n_rows"], w["nstates"], w["cheb_degree"]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(123)
+    X = torch.randn((rows, N), generator=gen, dtype=torch.float64, device="cuda")
+    u0 = torch.randn((rows, 1), generator=gen, dtype=torch.float64, device="cuda")
+    HX = torch.empty_like(X)
+    eig, _ = g.efe_rayleigh_ritz(X, HX)
+    b = g.efe_lanczos(u0, 10)[2]
+    lam = torch.tensor(eig, device="cuda")
+    out32, out16 = torch.empty_like(X), torch.empty_like(X)
+    g.efe_filter(X, HX, lam, m, (eig[0], eig[-1], b), out32, prec=1)
+    g.efe_filter(X, HX, lam, m, (eig[0], eig[-1], b), out16, prec=2)
+    assert bool(torch.isfinite(out16).all())
+    rel = float((out16 - out32).abs().max() / out32.abs().max())
+    # one bf16 rounding of the cell operand per step, errors adding over m steps
+    assert rel < m * 2.0 ** -8, rel
