@@ -177,13 +177,14 @@ def roofline_bf16(w, d, N, m, ms_cell_launch, ms_rec_launch, pk, pk_kind):
     below the ridge (~292 flop/B), so HBM-bound.
     k_gather_rec_w (node recurrence) reads, per interior node, its cell rows
     (one per cell containing the node) and Z_{k-1}, Z_{k-2}, G, writes Z_k, and
-    writes HY at support nodes and zeros at Dirichlet nodes, 4 N bytes each."""
+    writes zeros at Dirichlet nodes, 4 N bytes each (the coupling reads 16 bytes
+    of E and P_c per support entry and the small enriched rows, which stay in
+    cache: not counted)."""
     p = w["p"]
     nx, ny, nz = w["ncell"]
     inc = (nx * (p + 1) - 2) * (ny * (p + 1) - 2) * (nz * (p + 1) - 2)   # interior (cell, node) pairs
     z0 = (m - 2) / (m - 1)                       # the first recurrence step has no Z_{k-2}
-    rec_bytes = 4.0 * N * (inc + (2 + z0 + 1) * d["n_fe_dof"] + d["n_support_nodes"]
-                           + (d["n_nodes"] - d["n_fe_dof"]))
+    rec_bytes = 4.0 * N * (inc + (2 + z0 + 1) * d["n_fe_dof"] + (d["n_nodes"] - d["n_fe_dof"]))
     cell_bytes = d["n_cells"] * (2.0 * d["ne"] ** 2 + 6.0 * d["ne"] * N)
     hbm = pk["hbm_gbs"]
     out = []
