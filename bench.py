@@ -224,8 +224,8 @@ def roofline_simt(head, d, N, ms_sweep, pk):
 
 
 def scf_time_to_solution(torch, dev):
-    """SCF time-to-solution, FP64 and mixed (bf16 passes in the first iteration, FP32
-    after), from the same start vectors, with |dE| per atom of mixed against FP64:
+    """SCF time-to-solution, FP64 and mixed (every filter pass in bf16), from the
+    same start vectors, with |dE| per atom of mixed against FP64:
     the 2-atom workload (8^3 cells, p = 4, 8 states, degree 20) and an 8-atom cluster
     at the same resolution (12x13x11 cells, 20 states)."""
     from paper_2607_06848_gb300 import EFE, workloads as W, EFE_FP64, EFE_BF16

@@ -310,9 +310,16 @@ typedef struct {
                              run in bf16; a later pass runs in bf16 while the largest
                              residual of the occupied states after the last
                              Rayleigh-Ritz exceeds this, in FP32 below it (0: every
-                             pass in bf16) */
+                             pass in bf16, the binding's default) */
     int profile;          /* nonzero: synchronise at phase ends and report the
                              phase times in efe_scf_result.ms_phase */
+    int passes;           /* filter passes (each followed by Rayleigh-Ritz) per
+                             iteration after the first; values below 1 mean 1 */
+    double precond_k2;    /* > 0: Kerker preconditioning of the Anderson step (not in
+                             the paper, whose mixing is plain Anderson): the mixed
+                             residual Rbar enters as Rbar - k2 (-Lap + k2)^-1 Rbar,
+                             the inverse by CG on the FE mesh (lumped mass, phi = 0
+                             on the box); bohr^-2.  0: plain Anderson. */
 } efe_scf_opts;
 
 typedef struct {

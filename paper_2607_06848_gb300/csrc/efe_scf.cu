@@ -258,6 +258,16 @@ __global__ void k_axpy_n(long long n, double a, const double *x, double b, const
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) out[i] = a * x[i] + b * y[i];
 }
+// Y += s M^cc X (lumped mass, zero on the Dirichlet rows)
+__global__ void k_add_mass(long long n, double s, const double *mcc, const double *X, double *Y) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) Y[i] += s * mcc[i] * X[i];
+}
+// Jacobi of (1/4pi) K + s M^cc from that of (1/4pi) K (rows with dinv = 0 stay 0)
+__global__ void k_shift_jacobi(long long n, double s, const double *mcc, const double *dinv, double *out) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = dinv[i] != 0.0 ? 1.0 / (1.0 / dinv[i] + s * mcc[i]) : 0.0;
+}
 __global__ void k_add3(long long n, const double *a, const double *b, double *out) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) out[i] = a[i] + b[i];
@@ -510,7 +520,9 @@ struct MixCoef {
 };
 
 // rho = x_mm + beta R_mm - sum_j gamma_j ((x_{j+1} - x_j) + beta (R_{j+1} - R_j))
-__global__ void k_mix_update(long long n, MixRing ring, int mm, MixCoef gc, double beta, double *rho) {
+// rho = xbar + beta Rbar; Rbar also written when Rbar_out is given (preconditioned update)
+__global__ void k_mix_update(long long n, MixRing ring, int mm, MixCoef gc, double beta, double *rho,
+                             double *Rbar_out) {
     const double *xk = ring.x[0], *Rk = ring.R[0];
 #pragma unroll
     for (int j = 1; j <= kMixMax; ++j)
@@ -519,12 +531,15 @@ __global__ void k_mix_update(long long n, MixRing ring, int mm, MixCoef gc, doub
             Rk = ring.R[j];
         }
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double v = xk[i] + beta * Rk[i];
+        double xb = xk[i], rb = Rk[i];
 #pragma unroll
         for (int j = 0; j < kMixMax; ++j)
-            if (j < mm)
-                v -= gc.g[j] * ((ring.x[j + 1][i] - ring.x[j][i]) + beta * (ring.R[j + 1][i] - ring.R[j][i]));
-        rho[i] = v;
+            if (j < mm) {
+                xb -= gc.g[j] * (ring.x[j + 1][i] - ring.x[j][i]);
+                rb -= gc.g[j] * (ring.R[j + 1][i] - ring.R[j][i]);
+            }
+        rho[i] = xb + beta * rb;
+        if (Rbar_out) Rbar_out[i] = rb;
     }
 }
 
@@ -540,6 +555,8 @@ struct ScfState {
     int *d_cell_pair_ptr = nullptr, *d_cell_pair_idx = nullptr, *d_pair_atom = nullptr;
     double *d_Kpois = nullptr;      // (1/4pi) K_e shared cell matrix
     double *d_dinv = nullptr;       // Jacobi preconditioner of the Poisson matrix
+    double *d_dinv_shift = nullptr; // the same for (1/4pi)(K + k^2 M^cc), at shift_k2
+    double shift_k2 = 0.0;
     double *d_part = nullptr;       // reduction partials
     double *d_Z = nullptr;          // valence charges
     // conjugate-gradient work vectors (n_nodes), scalars and partials
@@ -557,7 +574,7 @@ void efe_scf_free(efe_ctx *ctx) {
     if (!ctx->scf) return;
     ScfState *S = static_cast<ScfState *>(ctx->scf);
     void *ptrs[] = {S->d_b, S->d_avals, S->d_cell_pair_ptr, S->d_cell_pair_idx, S->d_pair_atom, S->d_Kpois,
-                    S->d_dinv, S->d_part, S->d_Z, S->cg_F, S->cg_r, S->cg_z, S->cg_p, S->cg_Ap, S->cg_sc,
+                    S->d_dinv, S->d_dinv_shift, S->d_part, S->d_Z, S->cg_F, S->cg_r, S->cg_z, S->cg_p, S->cg_Ap, S->cg_sc,
                     S->cg_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -683,8 +700,8 @@ static efe_status cell_values(efe_ctx *ctx, const double *U, const double *Ue, i
     return efe_check_launch(ctx, "k_cell_values");
 }
 
-// Y = (1/4 pi) K X for one nodal vector (Dirichlet rows left at zero)
-static efe_status lap_apply(efe_ctx *ctx, const double *X, double *Y) {
+// Y = (1/4 pi) K X + shift M^cc X for one nodal vector (Dirichlet rows left at zero)
+static efe_status lap_apply(efe_ctx *ctx, const double *X, double *Y, double shift = 0.0) {
     ScfState &S = scf_state(ctx);
     const MeshDev &m = ctx->m;
     EFE_CUDA(ctx, cudaMemsetAsync(Y, 0, sizeof(double) * ctx->n_nodes, ctx->stream));
@@ -693,17 +710,32 @@ static efe_status lap_apply(efe_ctx *ctx, const double *X, double *Y) {
         const int ncol = ((m.nx - ox + 1) / 2) * ((m.ny - oy + 1) / 2) * ((m.nz - oz + 1) / 2);
         if (ncol) k_lap_colour<<<ncol, 256, 0, ctx->stream>>>(m, S.lap, colour, X, Y);
     }
+    if (shift != 0.0)
+        k_add_mass<<<nb(ctx->n_nodes, 256), 256, 0, ctx->stream>>>(ctx->n_nodes, shift, ctx->d_mcc, X, Y);
     return efe_check_launch(ctx, "k_lap_colour");
 }
 
-// FE solution of -1/(4 pi) Lap phi = f, phi = 0 on the box: Jacobi-preconditioned
-// CG to ||r|| < tol ||F||.  warm: start from the phi passed in (else from 0).
+// FE solution of -1/(4 pi) Lap phi + k2/(4 pi) phi = f (k2 = 0: Poisson), phi = 0
+// on the box, with the lumped mass for the k2 term: Jacobi-preconditioned CG to
+// ||r|| < tol ||F||.  warm: start from the phi passed in (else from 0).
 // The scalars stay on the device; the host reads the convergence flag once
 // every kCgBlock iterations, and iterations after convergence change nothing.
 constexpr int kCgBlock = 16;
 static efe_status poisson(efe_ctx *ctx, const double *fq, double *phi, double *phi_q, double tol, int max_it,
-                          int *iters, double *rel_res, bool warm = false) {
+                          int *iters, double *rel_res, bool warm = false, double k2 = 0.0) {
     ScfState &S = scf_state(ctx);
+    const double shift = k2 / (4.0 * kPi);
+    const double *dinv = S.d_dinv;
+    if (shift != 0.0) {
+        if (!S.d_dinv_shift) EFE_TRY(efe_alloc(ctx, (void **)&S.d_dinv_shift, sizeof(double) * ctx->n_nodes));
+        if (S.shift_k2 != k2) {
+            k_shift_jacobi<<<nb(ctx->n_nodes, 256), 256, 0, ctx->stream>>>(ctx->n_nodes, shift, ctx->d_mcc, S.d_dinv,
+                                                                           S.d_dinv_shift);
+            EFE_TRY(efe_check_launch(ctx, "k_shift_jacobi"));
+            S.shift_k2 = k2;
+        }
+        dinv = S.d_dinv_shift;
+    }
     const MeshDev &m = ctx->m;
     const long long n = ctx->n_nodes;
     Tables1D T = make_tables(ctx);
@@ -733,7 +765,7 @@ static efe_status poisson(efe_ctx *ctx, const double *fq, double *phi, double *p
     } else {
         // r = F - K phi0 (warm) or F (cold, phi0 = 0); z = D^-1 r; p = z
         if (warm) {
-            EFE_TRY(lap_apply(ctx, phi, Ap));
+            EFE_TRY(lap_apply(ctx, phi, Ap, shift));
             k_axpy_n<<<nb(n, 256), 256, 0, ctx->stream>>>(n, 1.0, F, -1.0, Ap, r);
         } else {
             EFE_CUDA(ctx, cudaMemsetAsync(phi, 0, sizeof(double) * n, ctx->stream));
@@ -743,7 +775,7 @@ static efe_status poisson(efe_ctx *ctx, const double *fq, double *phi, double *p
         k_set_scalar<<<1, 1, 0, ctx->stream>>>(sc, CG_ALPHA, 0.0);
         // with alpha = 0 the update only forms z = D^-1 r and the partials of r.r, r.z
         // (p and Ap are not read)
-        k_cg_update<<<NRED, 256, 0, ctx->stream>>>(n, sc, phi, r, p, Ap, S.d_dinv, z, S.cg_part);
+        k_cg_update<<<NRED, 256, 0, ctx->stream>>>(n, sc, phi, r, p, Ap, dinv, z, S.cg_part);
         k_cg_beta<<<1, 32, 0, ctx->stream>>>(S.cg_part, sc, 1);
         EFE_CUDA(ctx, cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
         EFE_TRY(efe_check_launch(ctx, "poisson start"));
@@ -756,10 +788,10 @@ static efe_status poisson(efe_ctx *ctx, const double *fq, double *phi, double *p
         while (!done && issued < max_it) {
             const int blk = std::min(kCgBlock, max_it - issued);
             for (int k = 0; k < blk; ++k) {
-                EFE_TRY(lap_apply(ctx, p, Ap));
+                EFE_TRY(lap_apply(ctx, p, Ap, shift));
                 k_dotp<<<NRED, 256, 0, ctx->stream>>>(n, p, Ap, S.cg_part);
                 k_cg_alpha<<<1, 32, 0, ctx->stream>>>(S.cg_part, sc);
-                k_cg_update<<<NRED, 256, 0, ctx->stream>>>(n, sc, phi, r, p, Ap, S.d_dinv, z, S.cg_part);
+                k_cg_update<<<NRED, 256, 0, ctx->stream>>>(n, sc, phi, r, p, Ap, dinv, z, S.cg_part);
                 k_cg_beta<<<1, 32, 0, ctx->stream>>>(S.cg_part, sc, 0);
                 k_cg_p<<<nb(n, 256), 256, 0, ctx->stream>>>(n, sc, z, p);
             }
@@ -913,8 +945,10 @@ efe_status efe_scf(efe_ctx *ctx, const efe_scf_opts *o, double *X, int N, const 
            *HX = take(sizeof(double) * rows * N), *Vout = take(sizeof(double) * rows * N),
            *dlam = take(sizeof(double) * N), *hin = take(sizeof(double) * nq * HS), *hres = take(sizeof(double) * nq * HS),
            *mixpart = take(sizeof(double) * (NRED + 1) * kMixNV);
+    const bool kerker = o->precond_k2 > 0.0;
+    double *phik = kerker ? take(sizeof(double) * nn) : nullptr, *phik_q = kerker ? take(sizeof(double) * nq) : nullptr;
     if (!rho_in || !rho_out || !veff || !vxc || !exc || !phi || !phi2 || !phi_q || !tmp || !HX || !Vout || !dlam || !hin ||
-        !hres || !mixpart) {
+        !hres || !mixpart || (kerker && (!phik || !phik_q))) {
         cleanup();
         return EFE_ERR_OOM;
     }
@@ -980,17 +1014,25 @@ efe_status efe_scf(efe_ctx *ctx, const efe_scf_opts *o, double *X, int N, const 
                 cleanup();
                 return EFE_ERR_CUDA;
             }
-            const double bd[3] = {eig[0], eig[N - 1], lz[2]};
-            // mixed schedule: after the first iteration, bf16 passes only while the
-            // occupied residuals are large
-            const efe_precision pp =
-                (prec == EFE_BF16 && o->bf16_resid > 0.0 && maxres <= o->bf16_resid) ? EFE_FP32 : prec;
-            SCF_TRY(efe_filter(ctx, X, HX, dlam, N, o->cheb_degree, bd, pp, Vout));
-            SCF_TRY(efe_rayleigh_ritz(ctx, Vout, HX, N, eig.data(), resid.data()));
-            if (cudaMemcpyAsync(X, Vout, sizeof(double) * rows * N, cudaMemcpyDeviceToDevice, ctx->stream) !=
-                cudaSuccess) {
-                cleanup();
-                return EFE_ERR_CUDA;
+            const int npass = std::max(1, o->passes);
+            for (int ps = 0; ps < npass; ++ps) {
+                if (ps > 0 && cudaMemcpyAsync(dlam, eig.data(), sizeof(double) * N, cudaMemcpyHostToDevice,
+                                              ctx->stream) != cudaSuccess) {
+                    cleanup();
+                    return EFE_ERR_CUDA;
+                }
+                const double bd[3] = {eig[0], eig[N - 1], lz[2]};
+                // mixed schedule: after the first iteration, bf16 passes only while the
+                // occupied residuals are large (bf16_resid = 0: every pass in bf16)
+                const efe_precision pp =
+                    (prec == EFE_BF16 && o->bf16_resid > 0.0 && maxres <= o->bf16_resid) ? EFE_FP32 : prec;
+                SCF_TRY(efe_filter(ctx, X, HX, dlam, N, o->cheb_degree, bd, pp, Vout));
+                SCF_TRY(efe_rayleigh_ritz(ctx, Vout, HX, N, eig.data(), resid.data()));
+                if (cudaMemcpyAsync(X, Vout, sizeof(double) * rows * N, cudaMemcpyDeviceToDevice, ctx->stream) !=
+                    cudaSuccess) {
+                    cleanup();
+                    return EFE_ERR_CUDA;
+                }
             }
         }
         mark(1);
@@ -1078,7 +1120,16 @@ efe_status efe_scf(efe_ctx *ctx, const efe_scf_opts *o, double *X, int N, const 
             }
             for (int i = 0; i < mm; ++i) gc.g[i] = gamma[i];
         }
-        k_mix_update<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, ring, mm, gc, o->mix_beta, rho_in);
+        k_mix_update<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, ring, mm, gc, o->mix_beta, rho_in,
+                                                            kerker ? tmp : nullptr);
+        if (kerker) {
+            // Kerker: beta Rbar -> beta (Rbar - k2 (-Lap + k2)^-1 Rbar); phik = 4 pi (-Lap + k2)^-1 Rbar
+            int kit = 0;
+            SCF_TRY(poisson(ctx, tmp, phik, phik_q, o->poisson_tol, 100000, &kit, nullptr, nh > 1, o->precond_k2));
+            res->poisson_iters += kit;
+            k_axpy_n<<<nb(nq, 256), 256, 0, ctx->stream>>>(nq, 1.0, rho_in, -o->mix_beta * o->precond_k2 / (4.0 * kPi),
+                                                           phik_q, rho_in);
+        }
         mark(4);
         if (cudaGetLastError() != cudaSuccess) {
             cleanup();

@@ -63,7 +63,8 @@ class efe_scf_opts(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("first_tol", ctypes.c_double), ("first_max_pass", ctypes.c_int),
                 ("renormalize", ctypes.c_int), ("kappa", ctypes.c_double), ("poisson_tol", ctypes.c_double),
                 ("precision", ctypes.c_int), ("log", SCF_LOG), ("log_user", ctypes.c_void_p),
-                ("bf16_resid", ctypes.c_double), ("profile", ctypes.c_int)]
+                ("bf16_resid", ctypes.c_double), ("profile", ctypes.c_int), ("passes", ctypes.c_int),
+                ("precond_k2", ctypes.c_double)]
 
 
 class efe_scf_result(ctypes.Structure):
@@ -349,7 +350,8 @@ class EFE:
                          int(opts.get("first_max_pass", 20)), int(opts.get("renormalize", 1)),
                          float(opts.get("kappa", 2.4)), float(opts.get("poisson_tol", 1e-12)),
                          int(opts.get("precision", EFE_FP64)), SCF_LOG(0), None,
-                         float(opts.get("bf16_resid", 1.0)), int(opts.get("profile", 0)))
+                         float(opts.get("bf16_resid", 0.0)), int(opts.get("profile", 0)),
+                         int(opts.get("passes", 1)), float(opts.get("precond_k2", 0.0)))
         hist = []
         if log is not None:
             def cb(user, it, E, F, mu, dr, dE, r0):

@@ -123,7 +123,7 @@ def test_density_matches_oracle():
     assert _rel(rho.cpu().numpy(), ro) < 1e-12
 
 
-def _run_scf(prec):
+def _run_scf(prec, **opts):
     o, g, w = _dimer()
     rows = o.nn + o.n_enr
     X0 = W.random_block(rows, w["nstates"], 1)
@@ -132,7 +132,7 @@ def _run_scf(prec):
     u0[:o.nn] *= o.mask[:, None]
     X = torch.tensor(X0, device="cuda")
     return g.efe_scf(X, torch.tensor(u0, device="cuda"), cheb_degree=w["cheb_degree"], precision=prec,
-                     log=lambda h: None)
+                     log=lambda h: None, **opts)
 
 
 def test_scf_fp64_matches_oracle():
@@ -150,5 +150,22 @@ def test_scf_fp64_matches_oracle():
 def test_scf_mixed_bf16_within_target():
     ref = json.load(open(os.path.join(HERE, "golden", "dimer_scf.json")))
     out = _run_scf(2)
+    assert out["converged"]
+    assert abs(out["E"] - ref["E"]) / 2 < 1e-5, (out["E"], ref["E"])
+
+
+def test_scf_schedule_options_reach_the_same_solution():
+    ref = json.load(open(os.path.join(HERE, "golden", "dimer_scf.json")))
+    # two filter passes (each with Rayleigh-Ritz) per iteration after the first
+    out = _run_scf(0, passes=2)
+    assert out["converged"]
+    assert abs(out["E"] - ref["E"]) / 2 < 1e-8, (out["E"], ref["E"])
+    assert out["iters"] <= ref["iters"] + 2
+    # Kerker-preconditioned Anderson steps: another path to the same fixed point
+    out = _run_scf(0, precond_k2=0.64)
+    assert out["converged"]
+    assert abs(out["E"] - ref["E"]) / 2 < 1e-8, (out["E"], ref["E"])
+    # mixed with FP32 passes once the occupied residuals are below 1 (bf16 in the first iteration only)
+    out = _run_scf(2, bf16_resid=1.0)
     assert out["converged"]
     assert abs(out["E"] - ref["E"]) / 2 < 1e-5, (out["E"], ref["E"])
