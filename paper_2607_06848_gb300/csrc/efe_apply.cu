@@ -509,8 +509,9 @@ __global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x,
             for (int u = 0; u < 8; ++u) { acc.x += y[u].x; acc.y += y[u].y; acc.z += y[u].z; acc.w += y[u].w; }
             {
                 for (long long e = e0; e < e1; ++e) {
-                    const int rb = (4 * nm_atom[e]) * lde + j;
-                    if (use_h) {
+                    const int av = nm_atom[e];
+                    const int rb = (4 * (av & kNmAtomMask)) * lde + j;
+                    if (use_h && (av & kNmHasE)) {
                         const float4 h = f4(Ec + 4 * e);
                         const float *yb = Ye + rb;
                         fma4(acc, h.x, f4(yb));
@@ -518,7 +519,7 @@ __global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x,
                         fma4(acc, h.z, f4(yb + 2 * lde));
                         fma4(acc, h.w, f4(yb + 3 * lde));
                     }
-                    if (use_p) {
+                    if (use_p && (av & kNmHasP)) {
                         const float4 pp = f4(Pc + 4 * e);
                         const float *wb = W + rb;
                         fma4(acc, pp.x, f4(wb));
@@ -548,16 +549,19 @@ template <typename T>
 __global__ void __launch_bounds__(256, 4) k_support_reduce3(const long long *sup_off, const int *sup_node,
                                                          const float *coefA, const float *coefB, const T *S,
                                                          const double *scale, int N, int ld, int chunk, int nch,
-                                                         double *part) {
+                                                         const int2 *order, double *part) {
     // thread t: float4 column group cg = t % ncg, position lane pl = t / ncg
     __shared__ float acc[8][256];
-    const int I = blockIdx.y;
+    // block -> (atom, chunk): from the order table (blocks sorted by their first
+    // node, so that atoms sharing a region read its rows while they are in L2)
+    const int I = order ? order[blockIdx.x].x : blockIdx.y;
+    const int ch = order ? order[blockIdx.x].y : blockIdx.x;
     const int ncg = (N + 3) / 4;                 // <= 64
     const int npl = blockDim.x / ncg;
     const int cg = threadIdx.x % ncg, pl = threadIdx.x / ncg;
     for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) acc[i / 256][i % 256] = 0.f;
     __syncthreads();
-    const long long beg = sup_off[I] + (long long)blockIdx.x * chunk;
+    const long long beg = sup_off[I] + (long long)ch * chunk;
     const long long end = min(sup_off[I + 1], beg + chunk);
     const bool two = coefB != nullptr;
     float4 r[8];
@@ -605,7 +609,7 @@ __global__ void __launch_bounds__(256, 4) k_support_reduce3(const long long *sup
     }
     __syncthreads();
     const int nr = two ? 8 : 4;
-    double *o = part + ((long long)(I * nch + blockIdx.x) * 8) * N;
+    double *o = part + ((long long)(I * nch + ch) * 8) * N;
     for (int i = threadIdx.x; i < nr * 256; i += blockDim.x) {
         const int rr = i / 256, jj = i % 256;
         if (jj < N) o[(long long)rr * N + jj] = acc[rr][jj];
@@ -994,6 +998,38 @@ efe_status hx_scratch(efe_ctx *ctx, int N, HxScratch &s) {
     return EFE_OK;
 }
 
+// Launch order of the support reductions: every (atom, chunk) pair, sorted by
+// the chunk's first support node (chunks past an atom's list keep their slot:
+// their blocks write the zero partials the sum reads).
+efe_status chunk_order(efe_ctx *ctx, int chunk, int nch) {
+    if (ctx->d_chunk_order && ctx->chunk_order_nch == nch) return EFE_OK;
+    const int na = std::max(ctx->natoms, 1);
+    std::vector<int> first(ctx->sup_total);
+    if (ctx->sup_total > 0)
+        EFE_CUDA(ctx, cudaMemcpy(first.data(), ctx->d_sup_node, sizeof(int) * ctx->sup_total, cudaMemcpyDeviceToHost));
+    std::vector<std::pair<long long, int2>> key;
+    key.reserve((size_t)na * nch);
+    for (int I = 0; I < ctx->natoms; ++I)
+        for (int c = 0; c < nch; ++c) {
+            const long long g = ctx->sup_off[I] + (long long)c * chunk;
+            const long long k = g < ctx->sup_off[I + 1] ? (long long)first[g] : (1LL << 62);
+            key.push_back({k, make_int2(I, c)});
+        }
+    std::stable_sort(key.begin(), key.end(),
+                     [](const std::pair<long long, int2> &a, const std::pair<long long, int2> &b) {
+                         return a.first < b.first;
+                     });
+    std::vector<int2> ord(key.size());
+    for (size_t i = 0; i < key.size(); ++i) ord[i] = key[i].second;
+    if (ctx->d_chunk_order) cudaFree(ctx->d_chunk_order);
+    ctx->d_chunk_order = nullptr;
+    EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_chunk_order, sizeof(int2) * std::max<size_t>(ord.size(), 1)));
+    if (!ord.empty())
+        EFE_CUDA(ctx, cudaMemcpy(ctx->d_chunk_order, ord.data(), sizeof(int2) * ord.size(), cudaMemcpyHostToDevice));
+    ctx->chunk_order_nch = nch;
+    return EFE_OK;
+}
+
 }  // namespace
 
 // Generic H^E product for storage type T (double or float).  Xp: n_nodes x N scratch.
@@ -1359,7 +1395,10 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     EFE_CUDA(ctx, cudaMemsetAsync(W32, 0, sizeof(float) * ((size_t)std::max(ctx->n_proj, 1) * lde + 4), ctx->stream));
     const bool cpl = (ctx->enrich || ctx->nonlocal) && ctx->natoms > 0;
     HxScratch s{};
-    if (cpl) EFE_TRY(hx_scratch(ctx, N, s));
+    if (cpl) {
+        EFE_TRY(hx_scratch(ctx, N, s));
+        EFE_TRY(chunk_order(ctx, s.chunk, s.nch));
+    }
     const unsigned rb_all = (unsigned)((rows + 7) / 8);
     const int nruns_x = (mh.Gx + kRun - 1) / kRun;                   // runs of kRun nodes along x
     const unsigned rb_run = (unsigned)(((long long)mh.Gy * mh.Gz * nruns_x + 7) / 8);   // 8 warps per block
@@ -1380,7 +1419,6 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
         ctx->launches++;
         Zprev = Z0;
     }
-    const dim3 gred(s.nch, std::max(ctx->natoms, 1), 1);
     if (N > 256) {
         ctx->err = "the tensor-core filter takes at most 256 columns per call";
         return EFE_ERR_ARG;
@@ -1406,10 +1444,10 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
         }
         if (cpl) {
             // E Y_c and P_c Y_c over the supports, from the FP32 Z scaled by M^cc^-1
-            k_support_reduce3<float><<<gred, 256, 0, ctx->stream>>>(
+            k_support_reduce3<float><<<(unsigned)(s.nch * std::max(ctx->natoms, 1)), 256, 0, ctx->stream>>>(
                 ctx->d_sup_off, ctx->d_sup_node, ctx->enrich ? ctx->d_E32 : ctx->d_Pc32,
                 (ctx->enrich && ctx->nonlocal) ? ctx->d_Pc32 : nullptr, Zcur, ctx->d_minv, N, ldz, s.chunk, s.nch,
-                s.part);
+                ctx->d_chunk_order, s.part);
             const long long n8 = (long long)ctx->natoms * 8 * N;
             k_support_sum<<<nblk(n8, 256), 256, 0, ctx->stream>>>(ctx->natoms, s.nch, N, s.part,
                                                                   ctx->enrich ? s.Rh : s.Wc,
@@ -1680,7 +1718,7 @@ void efe_destroy(efe_ctx *ctx) {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     efe_scf_free(ctx);
-    void *ptrs[] = {ctx->d_nm_atom, ctx->d_nm_E32, ctx->d_nm_P32, ctx->d_E, ctx->d_PE, ctx->d_HEee, ctx->d_hostio, ctx->d_B1, ctx->d_D1, ctx->d_wq, ctx->d_Khat, ctx->d_mcc, ctx->d_minv, ctx->d_He, ctx->d_He32,
+    void *ptrs[] = {ctx->d_chunk_order, ctx->d_nm_atom, ctx->d_nm_E32, ctx->d_nm_P32, ctx->d_E, ctx->d_PE, ctx->d_HEee, ctx->d_hostio, ctx->d_B1, ctx->d_D1, ctx->d_wq, ctx->d_Khat, ctx->d_mcc, ctx->d_minv, ctx->d_He, ctx->d_He32,
                     ctx->d_He16, ctx->d_atoms, ctx->d_hproj, ctx->d_sup_off, ctx->d_sup_node, ctx->d_C, ctx->d_B,
                     ctx->d_Kca, ctx->d_Hca, ctx->d_Pc, ctx->d_E32, ctx->d_Pc32, ctx->d_node_ptr,
                     ctx->d_node_ent, ctx->d_ent_atom,

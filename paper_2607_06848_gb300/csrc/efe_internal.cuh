@@ -28,6 +28,9 @@ struct PairInfo {
     int cell;
 };
 
+// flags in the high bits of the node-major atom index of a coupling entry
+constexpr int kNmHasE = 1 << 30, kNmHasP = 1 << 29, kNmAtomMask = (1 << 29) - 1;
+
 struct efe_ctx {
     std::string err;
     cudaStream_t stream = nullptr;
@@ -74,8 +77,11 @@ struct efe_ctx {
     double *d_E = nullptr;
     float *d_E32 = nullptr, *d_Pc32 = nullptr;   // FP32 copies for the mixed filter
     // the same in node-major (CSR) order, with the atom of each entry, for the node kernels
-    int *d_nm_atom = nullptr;
+    int *d_nm_atom = nullptr;                 // atom | kNmHasE | kNmHasP
     float *d_nm_E32 = nullptr, *d_nm_P32 = nullptr;
+    // launch order of the support reductions' (atom, chunk) blocks, by first node
+    int2 *d_chunk_order = nullptr;
+    int chunk_order_nch = 0;
     // node -> (atom, pos) CSR over all nodes
     long long *d_node_ptr = nullptr;          // n_nodes + 1
     int *d_node_ent = nullptr;                // entries: global support index (sup_off[I] + pos)

@@ -161,16 +161,25 @@ __global__ void k_static_pairs(MeshDev m, Tables1D T, FuncParams fp, const PairI
 
 // Potential coupling for one pair: Hca[l][f] += int v a_f N_l.
 // node-major copies of the coupling tables (statics on the first call, H^ca always)
+// Node-major copies of the coupling entries.  nm_atom carries the atom in its
+// low 29 bits and two flags: bit 30 when the entry's E is nonzero, bit 29 when
+// its P_c is (E vanishes exactly outside the enrichment's one-cell dilation,
+// P_c outside the projector ball), so the node kernels skip the zero halves.
 __global__ void k_node_major(long long n, const int *node_ent, const int *ent_atom, const float *E32,
                              const float *P32, int statics, int *nm_atom, float *nm_E, float *nm_P) {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= n) return;
     const int g = node_ent[e];
-    if (E32) reinterpret_cast<float4 *>(nm_E)[e] = reinterpret_cast<const float4 *>(E32)[g];
-    if (statics) {
-        nm_atom[e] = ent_atom[g];
-        reinterpret_cast<float4 *>(nm_P)[e] = reinterpret_cast<const float4 *>(P32)[g];
+    float4 ev = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (E32) {
+        ev = reinterpret_cast<const float4 *>(E32)[g];
+        reinterpret_cast<float4 *>(nm_E)[e] = ev;
     }
+    const float4 pv = reinterpret_cast<const float4 *>(P32)[g];
+    if (statics) reinterpret_cast<float4 *>(nm_P)[e] = pv;
+    const bool he = ev.x != 0.f || ev.y != 0.f || ev.z != 0.f || ev.w != 0.f;
+    const bool hp = pv.x != 0.f || pv.y != 0.f || pv.z != 0.f || pv.w != 0.f;
+    nm_atom[e] = ent_atom[g] | (he ? kNmHasE : 0) | (hp ? kNmHasP : 0);
 }
 
 __global__ void k_potential_pairs(MeshDev m, Tables1D T, FuncParams fp, const PairInfo *pairs,
