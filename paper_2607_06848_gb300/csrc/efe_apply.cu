@@ -359,16 +359,25 @@ __global__ void k_gather(MeshDev m, long long n_nodes, int N, const float *Yc, i
 // coordinates and coupling lists are read once per row, lanes run over the
 // columns).  All arithmetic is FP32; the values feed bf16 products.
 // ---------------------------------------------------------------------------
-__global__ void k_to_float_strided(long long rows, int N, const double *x, float *y, int ldy) {
+__global__ void k_to_float_strided(long long rows, int N, const double *x, float *y, int ldy,
+                                   __nv_bfloat16 *y16 = nullptr) {
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= rows * N) return;
-    y[(size_t)(idx / N) * ldy + idx % N] = (float)x[idx];
+    const size_t o = (size_t)(idx / N) * ldy + idx % N;
+    y[o] = (float)x[idx];
+    if (y16) y16[o] = __float2bfloat16_rn((float)x[idx]);
 }
 // ---------------------------------------------------------------------------
 // Vectorised row kernels of the tensor-core filter.  FE-row buffers use a row
 // stride ldz = N rounded up to 4 floats (16-byte rows): lanes move float4s.
 // ---------------------------------------------------------------------------
 __device__ inline float4 f4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ inline float4 f4(const __nv_bfloat16 *p) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
 __device__ inline void fma4(float4 &a, float s, const float4 b) {
     a.x += s * b.x; a.y += s * b.y; a.z += s * b.z; a.w += s * b.w;
 }
@@ -436,12 +445,15 @@ __global__ void __launch_bounds__(256) k_pre_bf16_w(MeshDev m, int nruns_x, cons
 //   HY[n] = sum over the cells of n of Y_cell[row(n)] + sum_e (E_e . Ye + Pc_e . W)
 //   Zn[n] = a (HY[n] - c Z1[n]) - b Z0[n] + a G[n] ck      (Eq. residualapprox)
 // with E the FE-enrichment block of H^E (E^T Ye is the enrichment's part of
-// the FE rows).
+// the FE rows).  The enriched rows Ye and the projector amplitudes W are read
+// from bf16 copies: every (node, entry) pair reloads 8 of their rows from L1,
+// and the bf16 rounding matches that of the cell operands.
 __global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x, int ldz, const float *__restrict__ Yc,
                                                       int ldy, const long long *__restrict__ node_ptr,
                                                       const int *__restrict__ nm_atom, const float *__restrict__ Ec,
-                                                      const float *__restrict__ Pc, const float *__restrict__ Ye,
-                                                      const float *__restrict__ W, int lde, int use_h, int use_p,
+                                                      const float *__restrict__ Pc,
+                                                      const __nv_bfloat16 *__restrict__ Ye,
+                                                      const __nv_bfloat16 *__restrict__ W, int lde, int use_h, int use_p,
                                                       const float *__restrict__ Z1, const float *__restrict__ Z0,
                                                       const float *__restrict__ G, const float *__restrict__ ck,
                                                       float a, float c, float b, float *__restrict__ Zn) {
@@ -513,7 +525,7 @@ __global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x,
                     const int rb = (4 * (av & kNmAtomMask)) * lde + j;
                     if (use_h && (av & kNmHasE)) {
                         const float4 h = f4(Ec + 4 * e);
-                        const float *yb = Ye + rb;
+                        const __nv_bfloat16 *yb = Ye + rb;
                         fma4(acc, h.x, f4(yb));
                         fma4(acc, h.y, f4(yb + lde));
                         fma4(acc, h.z, f4(yb + 2 * lde));
@@ -521,7 +533,7 @@ __global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x,
                     }
                     if (use_p && (av & kNmHasP)) {
                         const float4 pp = f4(Pc + 4 * e);
-                        const float *wb = W + rb;
+                        const __nv_bfloat16 *wb = W + rb;
                         fma4(acc, pp.x, f4(wb));
                         fma4(acc, pp.y, f4(wb + lde));
                         fma4(acc, pp.z, f4(wb + 2 * lde));
@@ -628,7 +640,8 @@ __global__ void __launch_bounds__(256) k_rows_residual_f(long long rows, int N, 
         Z1[r * ldz + j] = s1e * gv;
     }
 }
-__global__ void k_enr_minv_f(int n_enr, int N, int ld, const double *Binv, const float *X, float *Y, int ldy) {
+__global__ void k_enr_minv_f(int n_enr, int N, int ld, const double *Binv, const float *X, float *Y, int ldy,
+                             __nv_bfloat16 *Y16 = nullptr) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n_enr * N) return;
     const int k = idx / N, j = idx % N;
@@ -637,6 +650,7 @@ __global__ void k_enr_minv_f(int n_enr, int N, int ld, const double *Binv, const
     float s = 0.f;
     for (int g = 0; g < 4; ++g) s += (float)bb[g] * X[(size_t)(4 * I + g) * ld + j];
     Y[(size_t)k * ldy + j] = s;
+    if (Y16) Y16[(size_t)k * ldy + j] = __float2bfloat16_rn(s);
 }
 __global__ void k_enr_rec_v(int n_enr, int N, int ldz, const double *Yraw, const double *Q, const float *Z1,
                             const float *Z0, const float *G, const float *ck, float a, float c, float b, float *Zn) {
@@ -1374,7 +1388,7 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     const size_t nz = (size_t)rows * ldz;
     size_t need = 16384 + sizeof(double) * (size_t)rows * N + sizeof(double) * (size_t)(m + 2) * N +
                   sizeof(float) * ckf.size() + sizeof(float) * 4 * nz +
-                  sizeof(float) * 2 * ((size_t)std::max(ne_, ctx->n_proj) * lde + 4) + 2 * (size_t)nn * ldb +
+                  (sizeof(float) + 2) * 2 * ((size_t)std::max(ne_, ctx->n_proj) * lde + 8) + 2 * (size_t)nn * ldb +
                   4 * (size_t)ncells * mh.ne * ldy;
     EFE_TRY(efe_workspace(ctx, need));
     Carver cv{(char *)ctx->d_ws, ctx->ws_bytes};
@@ -1384,6 +1398,8 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     float *G = cv.take<float>(nz), *Z0 = cv.take<float>(nz), *Z1 = cv.take<float>(nz), *Z2 = cv.take<float>(nz);
     float *Ye = cv.take<float>((size_t)std::max(ne_, 1) * lde + 4);
     float *W32 = cv.take<float>((size_t)std::max(ctx->n_proj, 1) * lde + 4);
+    __nv_bfloat16 *Ye16 = cv.take<__nv_bfloat16>((size_t)std::max(ne_, 1) * lde + 8);
+    __nv_bfloat16 *W16 = cv.take<__nv_bfloat16>((size_t)std::max(ctx->n_proj, 1) * lde + 8);
     __nv_bfloat16 *Xb = cv.take<__nv_bfloat16>((size_t)nn * ldb);
     float *Ycells = cv.take<float>((size_t)ncells * mh.ne * ldy);
     EFE_CUDA(ctx, cudaMemcpyAsync(dck, ck.data(), sizeof(double) * ck.size(), cudaMemcpyHostToDevice, ctx->stream));
@@ -1393,6 +1409,8 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     EFE_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
     EFE_CUDA(ctx, cudaMemsetAsync(Ye, 0, sizeof(float) * ((size_t)std::max(ne_, 1) * lde + 4), ctx->stream));
     EFE_CUDA(ctx, cudaMemsetAsync(W32, 0, sizeof(float) * ((size_t)std::max(ctx->n_proj, 1) * lde + 4), ctx->stream));
+    EFE_CUDA(ctx, cudaMemsetAsync(Ye16, 0, 2 * ((size_t)std::max(ne_, 1) * lde + 8), ctx->stream));
+    EFE_CUDA(ctx, cudaMemsetAsync(W16, 0, 2 * ((size_t)std::max(ctx->n_proj, 1) * lde + 8), ctx->stream));
     const bool cpl = (ctx->enrich || ctx->nonlocal) && ctx->natoms > 0;
     HxScratch s{};
     if (cpl) {
@@ -1428,7 +1446,7 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
         const float ak = (float)(2.0 * sig[k] / e), bk = (float)(sig[k - 1] * sig[k]), cf = (float)c;
         if (ne_) {
             k_enr_minv_f<<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(ne_, N, ldz, ctx->d_Mblk_inv,
-                                                                                Zcur + nn * ldz, Ye, lde);
+                                                                                Zcur + nn * ldz, Ye, lde, Ye16);
             ctx->launches++;
         }
         // cell operand: the FE part of Y = M~^-1 Z in bf16 (no T transform: the
@@ -1458,7 +1476,7 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
                 k_proj_w<float><<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
                     ctx->n_proj, ne_, s.Wc, ctx->enrich ? ctx->d_PE : nullptr, Ye, lde, ctx->d_hproj, N, s.W);
                 k_to_float_strided<<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
-                    ctx->n_proj, N, s.W, W32, lde);
+                    ctx->n_proj, N, s.W, W32, lde, W16);
                 ctx->launches += 2;
             }
             if (ctx->enrich) {
@@ -1472,7 +1490,7 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
         if (rev) cudaEventRecord(rev->first, ctx->stream);
         k_gather_rec_w<<<rb_run, 256, 0, ctx->stream>>>(mh, nruns_x, ldz, Ycells, ldy, cpl ? ctx->d_node_ptr : nullptr,
                                                         ctx->d_nm_atom, ctx->d_nm_E32, ctx->d_nm_P32,
-                                                        Ye, W32, lde, ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0,
+                                                        Ye16, W16, lde, ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0,
                                                         Zcur, Zprev, G, fck + (size_t)(k - 1) * ldz, ak, cf, bk,
                                                         Znext);
         if (rev) cudaEventRecord(rev->second, ctx->stream);
