@@ -176,7 +176,12 @@ efe_status efe_lanczos(efe_ctx *ctx, const double *u0, int k, double out[3]);
  *         + (2 s_k/e) G diag(C_{k-1}(lam));
  *   Vout = M~^-1 Z_m + V diag(C_m(lam)).
  * V, HV, Vout: device rows x N (HV = H^E V in double); lam: device N doubles;
- * bounds (host): a0 <= lowest wanted, [a, b] the damped interval. */
+ * bounds (host): a0 <= lowest wanted, [a, b] the damped interval.  With
+ * prec = EFE_BF16 the products inside the recurrence apply H^E through its
+ * blocks (E = H^ac - C H^cc, H^E_ee = H^aa - C H^ca - E C^T and the projector
+ * overlaps P^E = P_a - P_c C^T, assembled in FP64 by efe_set_potential and
+ * setup) rather than as T^T H_raw T, whose two terms cancel when the
+ * enrichment is nearly representable by the FE space. */
 efe_status efe_filter(efe_ctx *ctx, const double *V, const double *HV, const double *lam,
                       int N, int m, const double bounds[3], efe_precision prec, double *Vout);
 
