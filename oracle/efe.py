@@ -342,6 +342,54 @@ class EFESystem:
         return out
 
 
+def assembled_fe_hamiltonian(sysm):
+    """H^cc over all nodes as a sparse matrix, rows and columns of Dirichlet nodes zero:
+    the sum over cells of the cell matrices H_e (Eq. Discrete_Eig_Gen_H, FE block)."""
+    m = sysm.mesh
+    cn = m.cell_nodes()
+    ne = m.ne
+    r = np.repeat(cn, ne, axis=1).ravel()
+    c = np.tile(cn, (1, ne)).ravel()
+    H = sp.csr_matrix((sysm.He.reshape(-1), (r, c)), shape=(sysm.nn, sysm.nn))
+    mk = sp.diags(sysm.mask.astype(float))
+    return (mk @ H @ mk).tocsr()
+
+
+def orthogonal_blocks(sysm):
+    """The blocks of H^E = T^T H_raw T that touch the enriched rows, written out
+    (Sec. II.B orthogonalization, T = [[I, -C^T], [0, I]]):
+
+      FE-enrichment block   E     = H^ac - C H^cc                 (n_enr x nn)
+      enriched block        H^E_ee = H^aa - C H^ca - E C^T          (local part)
+      projector overlaps    P^E   = P_a - P_c C^T                  (n_proj x n_enr)
+
+    Returns (Hcc, E, HEee, PE); PE is None without projectors."""
+    Hcc = assembled_fe_hamiltonian(sysm)
+    C = sysm.C.toarray()
+    Hca = sysm.Hca.toarray()
+    E = Hca.T - C @ Hcc.toarray()
+    HEee = sysm.Haa - C @ Hca - E @ C.T
+    PE = sysm.Pa - sysm.Pc.toarray() @ C.T if sysm.n_proj else None
+    return Hcc, E, HEee, PE
+
+
+def apply_H_blocks(sysm, X, blocks=None):
+    """H^E X from the blocks of H^E (no T transform): FE rows
+    H^cc X_c + E^T X_e + P_c^T W, enriched rows E X_c + H^E_ee X_e + P^E^T W with
+    W = D (P_c X_c + P^E X_e).  Equal to apply_H in exact arithmetic."""
+    Hcc, E, HEee, PE = orthogonal_blocks(sysm) if blocks is None else blocks
+    Xc, Xe = sysm.split(np.asarray(X, float))
+    Xc = Xc * sysm.mask[:, None]
+    Yc = Hcc @ Xc + E.T @ Xe
+    Ye = E @ Xc + HEee @ Xe
+    if sysm.n_proj:
+        W = sysm.D[:, None] * (sysm.Pc @ Xc + PE @ Xe)
+        Yc = Yc + sysm.Pc.T @ W
+        Ye = Ye + PE.T @ W
+    Yc = Yc * sysm.mask[:, None]
+    return np.concatenate([Yc, Ye], axis=0)
+
+
 def dense_raw_matrices(sysm):
     """H_raw and M_raw over (interior nodes + enrichment), assembled entry by entry.
 

@@ -9,7 +9,8 @@ import numpy as np
 import pytest
 import scipy.linalg as sla
 
-from oracle.efe import (EFESystem, cutoff, dense_raw_matrices, enrichment_values,
+from oracle.efe import (EFESystem, apply_H_blocks, cutoff, dense_raw_matrices, enrichment_values,
+                        orthogonal_blocks,
                         projector_values)
 from oracle.fe import Mesh
 
@@ -157,3 +158,89 @@ def test_nonlocal_is_separable_rank():
     d = HE - HE0
     sv = np.linalg.svd(d, compute_uv=False)
     assert sv[7] > 1e-6 * sv[0] and sv[8] < 1e-10 * sv[0]   # 2 atoms x 4 projectors
+
+
+def _one_atom(h, n, p, centre, hp=(0.8, -1.3)):
+    m = Mesh(h, (n, n, n), p)
+    s = EFESystem(m, np.asarray([centre], float), enrich=dict(alpha=1.2, r0=R0, t=0.33),
+                  proj=dict(rc=1.0, rtrunc=6.0, h=np.asarray([hp], float)))
+    q = m.all_quad_points()
+    s.set_potential(-2.0 / np.sqrt(1.0 + np.sum((q - s.atoms[0]) ** 2, axis=1)))
+    return s
+
+
+def test_block_form_equals_transform_form():
+    # H^E through its blocks E = H^ac - C H^cc, H^E_ee = H^aa - C H^ca - E C^T and
+    # P^E = P_a - P_c C^T (the mixed filter's form) against T^T H_raw T, on the
+    # filter's operands M~^-1 Z: the overlapping dimer and a degree-6 atom whose
+    # enrichment is nearly in the FE space (the transform form itself loses
+    # ~3 digits there, hence the looser bound)
+    for s, tol in ((_dimer_system(), 1e-13), (_one_atom(40.0 / 24.0, 6, 6, (5.0, 5.1, 4.9)), 1e-11)):
+        X = np.random.default_rng(3).standard_normal((s.nn + s.n_enr, 4))
+        X[:s.nn] *= s.mask[:, None]
+        Y = s.apply_Minv_approx(X)
+        a, b = s.apply_H(Y), apply_H_blocks(s, Y)
+        assert np.abs(a - b).max() < tol * np.abs(a).max()
+        # the blocks are those of the dense H^E
+        Hcc, E, HEee, PE = orthogonal_blocks(s)
+        if s.nn < 1000:
+            HE, _, _ = _efe_dense(s)
+            ni = int(s.mask.sum())
+            idx = np.nonzero(s.mask)[0]
+            HP = (PE.T * s.D[None, :]) @ PE
+            assert np.allclose(HE[ni:, ni:], HEee + HP, atol=1e-11)
+            assert np.allclose(HE[ni:, :ni], E[:, idx] + (PE.T * s.D[None, :]) @ s.Pc.toarray()[:, idx],
+                               atol=1e-11)
+
+
+def test_transform_form_cancels_at_degree_6():
+    # why the mixed filter uses the blocks: at degree 6, h = 40/24 the enrichment
+    # is nearly representable (M^ee ~ 1e-6 A_ee), the orthogonalized coordinates
+    # of M~^-1 Z are large, and the two FE-row terms of T^T H_raw T,
+    # H^cc (X_c - C^T X_e) and H^ca X_e, are each tens of times their sum
+    ratios = {}
+    for key, s in (("p2", _dimer_system()), ("p6", _one_atom(40.0 / 24.0, 6, 6, (5.0, 5.1, 4.9)))):
+        X = np.random.default_rng(3).standard_normal((s.nn + s.n_enr, 4))
+        X[:s.nn] *= s.mask[:, None]
+        Xc, Xe = s.split(s.apply_Minv_approx(X))
+        Xcp = (Xc * s.mask[:, None]) - s.C.T @ Xe
+        A = s.mesh.apply_cells(s.He, Xcp) * s.mask[:, None]
+        B = (s.Hca @ Xe) * s.mask[:, None]
+        ratios[key] = np.abs(A).max() / np.abs(A + B).max()
+        ratios[key + "_mee"] = np.linalg.eigvalsh(s.Mee).min() / np.linalg.eigvalsh(s.Aee).min()
+    assert ratios["p6_mee"] < 1e-4 < ratios["p2_mee"]
+    assert ratios["p6"] > 10.0 > 5.0 > ratios["p2"], ratios
+
+
+def test_E_vanishes_outside_one_cell_dilation():
+    # E = H^ac - C H^cc is nonzero only at nodes of cells that share a node with
+    # a cell meeting the enrichment ball (r <= r_end): C lives on the nodes of
+    # those cells and H^cc reaches one cell further; some nonzeros do lie outside
+    # the cells that meet the ball, so the supports must include the layer
+    h, n, p = 1.5, 12, 2
+    s = _one_atom(h, n, p, (9.1, 8.9, 9.0))
+    _, E, _, _ = orthogonal_blocks(s)
+    m = s.mesh
+    r_end = R0 * (1.0 + 1.0 / 0.33)
+    cn = m.cell_nodes()
+    X = s.atoms[0]
+    meets = np.zeros((n, n, n), bool)
+    for c in range(m.ncells):
+        cx, cy, cz = m.cell_coords(c)
+        lo = np.array([cx, cy, cz]) * h
+        d = np.clip(X, lo, lo + h) - X
+        meets[cz, cy, cx] = d @ d <= r_end ** 2
+    dil = meets.copy()
+    for ax in range(3):
+        dil = dil | np.roll(dil, 1, axis=ax) | np.roll(dil, -1, axis=ax)   # the ball is far from the box faces
+    inner = np.zeros(s.nn, bool)
+    outer = np.zeros(s.nn, bool)
+    for c in range(m.ncells):
+        cx, cy, cz = m.cell_coords(c)
+        if meets[cz, cy, cx]:
+            inner[cn[c]] = True
+        if dil[cz, cy, cx]:
+            outer[cn[c]] = True
+    nz = np.abs(E).max(axis=0) > 0.0
+    assert not np.any(nz & ~outer)
+    assert np.any(nz & ~inner)
