@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x,
     const bool yz_in = iy > 0 && iz > 0 && iy < m.Gy - 1 && iz < m.Gz - 1;
     const long long n0 = yz * m.Gx + x0;
     // y/z part of the cell rows: cell index (without x) and local offset (without x)
-    long long cyz[4];
+    int cyz[4];                // cell index without x (cells < 2^31)
     int lyz[4];
     bool vyz[4];
     {
@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x,
             vyz[t] = (sy <= ay.two) && (sz <= az.two);
             const int cy = ay.k0 + sy, cz = az.k0 + sz;
             const int ly = sy ? 0 : ay.a0, lz = sz ? 0 : az.a0;
-            cyz[t] = ((long long)cz * m.ny + cy) * m.nx;
+            cyz[t] = (cz * m.ny + cy) * m.nx;
             lyz[t] = (lz * m.np1 + ly) * m.np1;
         }
     }
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x,
             for (int u = 0; u < 8; ++u) {
                 const int sx = u & 1, t = u >> 1;
                 const bool ok = vyz[t] && (sx <= ax.two);
-                const long long cell = cyz[t] + ax.k0 + sx;
+                const long long cell = (long long)(cyz[t] + ax.k0 + sx);
                 const int l = lyz[t] + (sx ? 0 : ax.a0);
                 y[u] = ok ? f4(Yc + (cell * m.ne + l) * ldy + j) : make_float4(0.f, 0.f, 0.f, 0.f);
             }

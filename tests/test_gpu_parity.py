@@ -54,6 +54,9 @@ def _case(name):
     if name == "p1_enriched":
         return dict(h=1.0, ncell=(13, 13, 13), p=1, atoms=np.array([[6.5, 6.4, 6.6]]),
                     hproj=np.array([[0.9, -0.7]]), enrich=True, nl=True)
+    if name == "p7_enriched":
+        return dict(h=2.0, ncell=(5, 5, 5), p=7, atoms=np.array([[5.0, 5.0, 5.0]]), hproj=np.array([[0.7, -1.1]]),
+                    enrich=True, nl=True)
     if name == "p8_cfe":
         return dict(h=2.0, ncell=(2, 2, 2), p=8, atoms=np.array([[2.0, 2.0, 2.0]]), hproj=np.zeros((1, 2)),
                     enrich=False, nl=False)
