@@ -1251,7 +1251,7 @@ struct Carver {
 
 template <typename T>
 efe_status filter_impl(efe_ctx *ctx, const double *V, const double *HV, const double *lam_dev, int N, int m,
-                       const double bounds[3], double *Vout, bool tensor = false, bool standard = false) {
+                       const double bounds[3], double *Vout, bool standard = false) {
     const long long rows = ctx->n_rows, nn = ctx->n_nodes;
     const long long n = rows * N;
     const double a0 = bounds[0], a = bounds[1], b = bounds[2];
@@ -1269,22 +1269,12 @@ efe_status filter_impl(efe_ctx *ctx, const double *V, const double *HV, const do
     // the standard filter has no forcing term and no V diag(C_m) part
     if (standard) std::fill(ck.begin(), ck.end(), 0.0);
     const double e = 0.5 * (b - a), c = 0.5 * (b + a);
-    const int ldb = (N + 7) / 8 * 8, ldy = (N + 3) / 4 * 4;
-    const long long ncells = (long long)ctx->m.nx * ctx->m.ny * ctx->m.nz;
     size_t need = 256 * 16 + sizeof(double) * (2 * n + (size_t)(m + 1) * N) + sizeof(T) * (5 * n + nn * N);
-    if (tensor) need += 512 + 2 * (size_t)nn * ldb + 4 * (size_t)ncells * ctx->m.ne * ldy;
     EFE_TRY(efe_workspace(ctx, need));
     Carver cv{(char *)ctx->d_ws, ctx->ws_bytes};
     double *G = cv.take<double>(n), *MV = cv.take<double>(n), *dck = cv.take<double>((size_t)(m + 1) * N);
     T *Z0 = cv.take<T>(n), *Z1 = cv.take<T>(n), *Z2 = cv.take<T>(n), *Y = cv.take<T>(n), *HY = cv.take<T>(n);
     T *Xp = cv.take<T>((size_t)nn * N);
-    __nv_bfloat16 *Xb = nullptr;
-    float *Ycells = nullptr;
-    if (tensor) {
-        Xb = cv.take<__nv_bfloat16>((size_t)nn * ldb);
-        Ycells = cv.take<float>((size_t)ncells * ctx->m.ne * ldy);
-        EFE_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
-    }
     EFE_CUDA(ctx, cudaMemcpyAsync(dck, ck.data(), sizeof(double) * ck.size(), cudaMemcpyHostToDevice, ctx->stream));
     ctx->cell_events_used = 0;
     ctx->cell_launches = 0;
@@ -1305,15 +1295,7 @@ efe_status filter_impl(efe_ctx *ctx, const double *V, const double *HV, const do
     const T *He = std::is_same<T, double>::value ? (const T *)ctx->d_He : (const T *)ctx->d_He32;
     for (int k = 2; k <= m; ++k) {
         EFE_TRY(mtilde_inv<T>(ctx, Zcur, Y, N));
-        if constexpr (std::is_same<T, float>::value) {
-            if (tensor) {
-                EFE_TRY(hx_bf16(ctx, Y, HY, N, Xb, Ycells));
-            } else {
-                EFE_TRY(hx_generic<T>(ctx, Y, HY, N, He, Xp));
-            }
-        } else {
-            EFE_TRY(hx_generic<T>(ctx, Y, HY, N, He, Xp));
-        }
+        EFE_TRY(hx_generic<T>(ctx, Y, HY, N, He, Xp));
         const double ak = 2.0 * sig[k] / e, bk = sig[k - 1] * sig[k];
         k_recurrence<T><<<nblk(n, 256), 256, 0, ctx->stream>>>(n, N, ak, c, bk, HY, Zcur, Zprev, G,
                                                                dck + (size_t)(k - 1) * N, Znext);
@@ -1332,14 +1314,6 @@ efe_status filter_impl(efe_ctx *ctx, const double *V, const double *HV, const do
     ctx->stats.ms_cell = cell_events_ms(ctx);
     ctx->stats.launches = ctx->launches - l0;
     ctx->stats.cell_launches = ctx->cell_launches;
-    if (tensor) {
-        int flag = 0;
-        EFE_CUDA(ctx, cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (flag) {
-            ctx->err = "tensor-core cell product: a bounded wait gave up (role " + std::to_string(flag) + ")";
-            return EFE_ERR_TIMEOUT;
-        }
-    }
     return EFE_OK;
 }
 
@@ -1534,8 +1508,8 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
 
 efe_status efe_filter_dispatch(efe_ctx *ctx, const double *V, const double *HV, const double *lam, int N, int m,
                                const double bounds[3], efe_precision prec, double *Vout, bool standard = false) {
-    if (prec == EFE_FP64) return filter_impl<double>(ctx, V, HV, lam, N, m, bounds, Vout, false, standard);
-    if (prec == EFE_FP32) return filter_impl<float>(ctx, V, HV, lam, N, m, bounds, Vout, false, standard);
+    if (prec == EFE_FP64) return filter_impl<double>(ctx, V, HV, lam, N, m, bounds, Vout, standard);
+    if (prec == EFE_FP32) return filter_impl<float>(ctx, V, HV, lam, N, m, bounds, Vout, standard);
     if (prec == EFE_BF16) return filter_tensor(ctx, V, HV, lam, N, m, bounds, Vout, standard);
     ctx->err = "unknown precision";
     return EFE_ERR_ARG;
