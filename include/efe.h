@@ -149,14 +149,18 @@ efe_status efe_get_stats(const efe_ctx *ctx, efe_stats *stats);
 
 /* Assemble the potential-dependent operator (Eq. KS with v_KS = veff):
  * cell matrices H_e = 1/2 K_e + int veff N_i N_j, the raw coupling blocks
- * H^ac, H^aa.  veff_q: device, n_quad doubles at the Gauss points.  Must be
- * called before any H product. */
+ * H^ac, H^aa and, with enrichment, the blocks of H^E the mixed filter uses
+ * (E = H^ac - C H^cc, H^E_ee = H^aa - C H^ca - E C^T, FP64).  veff_q: device,
+ * n_quad doubles at the Gauss points.  Must be called before any H product. */
 efe_status efe_set_potential(efe_ctx *ctx, const double *veff_q);
 
 /* Y = H^E X = T^T H_raw T X (Eq. Discrete_Eig_Gen_H).  X, Y: device, rows x N,
  * not aliased.  prec selects the arithmetic of the cell products (EFE_FP64:
  * double; EFE_FP32 / EFE_BF16: inputs rounded, FP32 accumulate), used by the
- * parity tests of the mixed filter. */
+ * parity tests of the tensor-core cell products.  The bf16 product keeps the
+ * transform form: for vectors with large orthogonalized coordinates (such as
+ * M~^-1 Z when the enrichment is nearly in the FE space) its relative error
+ * grows with the cancellation; efe_filter applies the block form instead. */
 efe_status efe_apply_h(efe_ctx *ctx, const double *X, double *Y, int N, efe_precision prec);
 
 /* Y = M^E X with the exact M^E (diagonal M^cc, full M^ee). device, rows x N. */
