@@ -117,14 +117,17 @@ def zz_overlap_correction(atoms, Z, alpha):
     return e
 
 
-def poisson_solve(mesh, fq, tol=1e-12, max_iter=5000, boundary=None):
-    """FE solution of -1/(4 pi) Lap phi = f with phi = 0 (or ``boundary``) on the box.
+def poisson_solve(mesh, fq, tol=1e-12, max_iter=5000, boundary=None, k2=0.0):
+    """FE solution of -1/(4 pi) Lap phi + k2/(4 pi) phi = f (k2 = 0: Poisson, Eq.
+    poisson) with phi = 0 (or ``boundary``) on the box.
 
-    Weak form: (1/4pi) K phi = F, F_j = int N_j f, by Jacobi-preconditioned
-    conjugate gradients to ||r|| < tol ||F||.  Returns (phi_nodes, iterations).
+    Weak form: (1/4pi) (K + k2 M) phi = F, F_j = int N_j f, M the lumped (GLL)
+    mass, by Jacobi-preconditioned conjugate gradients to ||r|| < tol ||F||.
+    Returns (phi_nodes, iterations).
     """
     Ke = mesh.stiffness_cell() / (4.0 * math.pi)
     mask = mesh.interior_mask()
+    shift = (k2 / (4.0 * math.pi)) * mesh.lumped_mass() if k2 else np.zeros(mesh.nnodes)
     F = mesh.integrate_against_basis(fq)
     g = np.zeros(mesh.nnodes)
     if boundary is not None:
@@ -133,9 +136,9 @@ def poisson_solve(mesh, fq, tol=1e-12, max_iter=5000, boundary=None):
     F = F * mask
 
     def A(x):
-        return mesh.apply_cells(Ke, (x * mask)[:, None])[:, 0] * mask
+        return (mesh.apply_cells(Ke, (x * mask)[:, None])[:, 0] + shift * x) * mask
 
-    diag = mesh.apply_cells(np.diag(np.diag(Ke)), np.ones((mesh.nnodes, 1)))[:, 0]
+    diag = mesh.apply_cells(np.diag(np.diag(Ke)), np.ones((mesh.nnodes, 1)))[:, 0] + shift
     dinv = np.where(mask, 1.0 / diag, 0.0)
     x = np.zeros(mesh.nnodes)
     r = F.copy()
@@ -167,25 +170,37 @@ def density(sysm, V, f):
     return 2.0 * np.sum(psi * psi * np.asarray(f)[None, :], axis=1)
 
 
-def anderson_mix(hist_in, hist_out, w, beta):
+def anderson_mix(hist_in, hist_out, w, beta, precond=None):
     """Anderson mixing (Walker-Ni form) on densities at quadrature points.
 
     hist_in/hist_out: lists of rho_in, rho_out (oldest first); w: quadrature
     weights (the inner product).  gamma minimises ||R_k - dR gamma||_w;
-    rho_next = (x_k - dX gamma) + beta (R_k - dR gamma).
+    rho_next = (x_k - dX gamma) + beta P(R_k - dR gamma), P = precond or the
+    identity (the paper's plain Anderson).
     """
+    P = precond if precond is not None else (lambda r: r)
     xk = hist_in[-1]
     Rk = hist_out[-1] - hist_in[-1]
     m = len(hist_in) - 1
     if m == 0:
-        return xk + beta * Rk
+        return xk + beta * P(Rk)
     dX = np.stack([hist_in[j + 1] - hist_in[j] for j in range(m)], axis=1)
     R = [hist_out[j] - hist_in[j] for j in range(m + 1)]
     dR = np.stack([R[j + 1] - R[j] for j in range(m)], axis=1)
     A = dR.T @ (w[:, None] * dR)
     b = dR.T @ (w * Rk)
     gamma = np.linalg.lstsq(A, b, rcond=None)[0]
-    return (xk - dX @ gamma) + beta * (Rk - dR @ gamma)
+    return (xk - dX @ gamma) + beta * P(Rk - dR @ gamma)
+
+
+def kerker(mesh, R, k2, tol=1e-12):
+    """Kerker preconditioning of a density residual (not in the paper, whose
+    mixing is plain Anderson): R - k2 (-Lap + k2)^-1 R, the Fourier factor
+    q^2 / (q^2 + k2) of each mode, with the inverse by the FE solve above
+    (phi = 4 pi (-Lap + k2)^-1 R, so the correction is k2 phi / (4 pi))."""
+    phi, _ = poisson_solve(mesh, R, tol=tol, k2=k2)
+    phq = mesh.interpolate(phi[:, None])[:, 0]
+    return R - (k2 / (4.0 * math.pi)) * phq
 
 
 def initial_density(mesh, atoms, Z, kappa=2.4):
@@ -217,14 +232,15 @@ def total_energy(mesh, eig, f, kT, rho_out, veff_in, bq, phi_out_q, atoms, Z, al
 
 def scf(sysm, Z, X0, lanczos_u0, *, cheb_degree=20, temperature=500.0, alpha_loc=0.8,
         mix_beta=0.5, mix_hist=8, tol_rho=1e-8, tol_e=1e-8, max_iter=60,
-        first_tol=1e-2, first_max_pass=20, renormalize=True, rho0=None, log=None):
+        first_tol=1e-2, first_max_pass=20, renormalize=True, rho0=None, log=None, precond_k2=0.0):
     """Self-consistent field loop (Sec. II.A; Sec. IV for 500 K and Anderson).
 
     Per iteration: phi[rho_in] by Poisson, v_eff = v_xc[rho_in] + phi; cell and
     coupling matrices; eigenpairs by residual ChFSI (first iteration: passes
     until the max residual < first_tol, from X0; later: one pass); mu;
-    rho_out; energy; Anderson mixing.  Converged when ||rho_out - rho_in||/N_e
-    < tol_rho and |dE| < tol_e per atom.
+    rho_out; energy; Anderson mixing (precond_k2 > 0: with the Kerker step
+    above, an addition to the paper's plain Anderson).  Converged when
+    ||rho_out - rho_in||/N_e < tol_rho and |dE| < tol_e per atom.
     """
     mesh = sysm.mesh
     atoms = sysm.atoms
@@ -273,5 +289,6 @@ def scf(sysm, Z, X0, lanczos_u0, *, cheb_degree=20, temperature=500.0, alpha_loc
         hin.append(rho_in)
         hout.append(rho_out)
         hin, hout = hin[-(mix_hist + 1):], hout[-(mix_hist + 1):]
-        rho_in = anderson_mix(hin, hout, w, mix_beta)
+        pre = (lambda r: kerker(mesh, r, precond_k2)) if precond_k2 > 0.0 else None
+        rho_in = anderson_mix(hin, hout, w, mix_beta, precond=pre)
     return dict(E=E, F=F, mu=mu, eig=lam, occ=f, V=V, rho=rho_out, iters=it, history=history)

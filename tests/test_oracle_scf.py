@@ -120,3 +120,48 @@ def test_dimer_scf():
     # 2 sum f = N_e exactly; the raw density integral differs only by lumping
     assert abs(2 * out["occ"].sum() - 8.0) < 1e-11
     assert abs(m.integrate(out["rho"]) - 8.0) < 2e-2
+
+
+def test_kerker_factor_on_sine_modes():
+    # the Kerker step multiplies each mode of the residual by q^2 / (q^2 + k2):
+    # sin(a pi x/L) sin(b pi y/L) sin(c pi z/L) vanishes on the box and has
+    # q^2 = (a^2 + b^2 + c^2) pi^2 / L^2; the FE solve converges to it in h and p
+    L = 8.0
+    errs = {}
+    for n, p in ((4, 4), (8, 4), (4, 6)):
+        m = Mesh(L / n, (n, n, n), p)
+        q = m.all_quad_points()
+        for (a, b, c) in ((1, 1, 1), (2, 1, 1)):
+            R = (np.sin(a * math.pi * q[:, 0] / L) * np.sin(b * math.pi * q[:, 1] / L)
+                 * np.sin(c * math.pi * q[:, 2] / L))
+            q2 = (a * a + b * b + c * c) * math.pi ** 2 / L ** 2
+            for k2 in (0.64, 2.0):
+                fac = q2 / (q2 + k2)
+                PR = S.kerker(m, R, k2)
+                errs[(n, p, a, k2)] = np.abs(PR - fac * R).max() / np.abs(fac * R).max()
+    assert max(v for k, v in errs.items() if k[:2] == (4, 6)) < 2e-6
+    for a in (1, 2):
+        for k2 in (0.64, 2.0):
+            assert errs[(8, 4, a, k2)] < errs[(4, 4, a, k2)] / 16.0
+
+
+@pytest.mark.slow
+def test_kerker_scf_reaches_the_same_fixed_point():
+    # a preconditioner of the mixing step changes the path, not the solution:
+    # the dimer SCF with the Kerker step ends at the golden FP64 energy
+    import json
+    import os
+    from paper_2607_06848_gb300 import workloads as W
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "dimer_scf.json")))
+    w = W.dimer()
+    m = Mesh(w["h"], w["ncell"], w["p"])
+    s = EFESystem(m, w["atoms"], enrich=dict(alpha=1.2, r0=5 * 0.33 / 1.33, t=0.33),
+                  proj=dict(rc=1.0, rtrunc=6.0, h=w["hproj"]))
+    rows = s.nn + s.n_enr
+    X0 = W.random_block(rows, w["nstates"], 1)
+    u0 = W.random_block(rows, 1, 2)
+    X0[:s.nn] *= s.mask[:, None]
+    u0[:s.nn] *= s.mask[:, None]
+    out = S.scf(s, w["Z"], X0, u0, cheb_degree=20, precond_k2=0.64)
+    assert out["history"][-1]["drho"] < 1e-8
+    assert abs(out["E"] - ref["E"]) / 2 < 1e-8, (out["E"], ref["E"])
