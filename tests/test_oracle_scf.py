@@ -120,6 +120,21 @@ def test_dimer_scf():
     # 2 sum f = N_e exactly; the raw density integral differs only by lumping
     assert abs(2 * out["occ"].sum() - 8.0) < 1e-11
     assert abs(m.integrate(out["rho"]) - 8.0) < 2e-2
+    # the energy by another route: kinetic + nonlocal as orbital expectation
+    # values (H^E with v = 0), E_xc and the electrostatics of rho_out directly.
+    # With the raw density, 2 sum f eps_i - int rho_out v_eff is exactly that
+    # expectation value (same quadrature in V and in rho), so the two agree to
+    # rounding at any iteration; a dropped or mis-signed term would not
+    V, f, rho = out["V"], out["occ"], out["rho"]
+    Z = np.asarray(w["Z"], float)
+    s.set_potential(np.zeros(len(rho)))
+    tnl = 2.0 * float(np.sum(f * np.sum(V * s.apply_H(V), axis=0)))
+    eps, _ = S.lda_pw92(rho)
+    bq = S.gaussian_charge(m.all_quad_points(), s.atoms, Z, 0.8)
+    _, phq, _ = S.hartree_potential(m, rho, bq)
+    E_direct = (tnl + m.integrate(rho * eps) + 0.5 * m.integrate((rho + bq) * phq)
+                - S.self_energy(Z, 0.8) + S.zz_overlap_correction(s.atoms, Z, 0.8))
+    assert abs(E_direct - out["E"]) < 1e-10, (E_direct, out["E"])
 
 
 def test_kerker_factor_on_sine_modes():
