@@ -348,7 +348,8 @@ typedef struct {
 
 /* The SCF loop: v_eff = v_xc[rho_in] + phi[rho_in + b_sm]; operator assembly;
  * eigenpairs by residual ChFSI (first iteration: Lanczos bounds and passes
- * until first_tol; later: one filter pass + Rayleigh-Ritz); Fermi level;
+ * until first_tol; later: opts.passes filter passes, each with Rayleigh-Ritz);
+ * Fermi level;
  * rho_out; E = 2 sum f eps - int rho_out v_eff + E_xc[rho_out]
  * + 1/2 int (rho_out + b) phi[rho_out] - E_self + dE_ZZ; Anderson mixing.
  * X: device rows x N, start vectors in, eigenvectors out; u0: device rows
