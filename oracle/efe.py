@@ -49,25 +49,37 @@ def cutoff(r, r0, t):
     return h, dh
 
 
-def enrichment_values(pts, center, alpha, r0=None, t=0.33):
+def enrichment_values(pts, center, alpha, r0=None, t=0.33, radial="gauss"):
     """Atomic parts a_f (f = s, px, py, pz) and their gradients at points.
 
     Returns (vals (4, n), grads (4, 3, n)).  ``r0=None`` switches the cutoff
-    off (h = 1), used only by closed-form checks.
+    off (h = 1), used only by closed-form checks.  The radial part g(r) is
+    exp(-alpha r^2) (``radial="gauss"``, the workloads' functions) or the
+    hydrogen-like exp(-alpha r) (``radial="slater"``, alpha = Z: the exact
+    1s orbital of -Z/r, used by the closed-form check of Sec. II.B's claim
+    that atomic orbitals in the span give the atomic eigenvalues).
     """
     d = pts - center[None, :]
     r = np.sqrt(np.sum(d * d, axis=1))
-    g = np.exp(-alpha * r * r)
+    if radial == "gauss":
+        g = np.exp(-alpha * r * r)
+        gpr = -2.0 * alpha * g                      # g'(r)/r
+    elif radial == "slater":
+        g = np.exp(-alpha * r)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            gpr = np.where(r > 0, -alpha * g / np.where(r > 0, r, 1.0), 0.0)
+    else:
+        raise ValueError("radial must be 'gauss' or 'slater'")
     if r0 is None:
         h = np.ones_like(r)
         dh = np.zeros_like(r)
     else:
         h, dh = cutoff(r, r0, t)
     f = g * h
-    # f'(r)/r, finite at r = 0 because h' vanishes below r0
+    # f'(r)/r = g'(r)/r h + g h'(r)/r, h'/r finite at r = 0 because h' vanishes below r0
     with np.errstate(divide="ignore", invalid="ignore"):
         dh_over_r = np.where(r > 0, dh / np.where(r > 0, r, 1.0), 0.0)
-    fpr = g * (dh_over_r - 2.0 * alpha * h)
+    fpr = gpr * h + g * dh_over_r
     vals = np.empty((4, len(r)))
     grads = np.empty((4, 3, len(r)))
     vals[0] = Y00 * f
@@ -163,7 +175,8 @@ class EFESystem:
         for i, I in enumerate(atoms):
             if self.enrich is not None:
                 e = self.enrich
-                v, g = enrichment_values(pts, self.atoms[I], e["alpha"], e.get("r0"), e.get("t", 0.33))
+                v, g = enrichment_values(pts, self.atoms[I], e["alpha"], e.get("r0"), e.get("t", 0.33),
+                                         e.get("radial", "gauss"))
                 A[4 * i:4 * i + 4] = v
                 dA[4 * i:4 * i + 4] = g
             if self.proj is not None:

@@ -7,6 +7,8 @@ Workloads (shaped like the paper's Sec. IV systems; the paper's geometries and
 pseudopotentials are not available, so seeded stand-ins are used):
   dimer      2 atoms 2.2 bohr apart at the centre of a 16-bohr cube, Z = 4,
              8^3 cells of degree 4, 8 states, filter degree 20.
+  atom       1 atom on the centre node of the dimer's mesh (partially filled
+             p shell at 500 K).
   cluster64  64 atoms (Z = 4) placed uniformly at random in [6, 34]^3 with
              pairwise distance >= 4.2 bohr, 40-bohr cube, 24^3 cells of
              degree 6, 154 states, filter degree 30.
@@ -47,6 +49,17 @@ def dimer(seed=0):
     return dict(name="dimer", h=2.0, ncell=(8, 8, 8), p=4, atoms=atoms,
                 Z=np.full(2, 4.0), hproj=projector_strengths(2, seed), nstates=8,
                 cheb_degree=20)
+
+
+def single_atom(seed=0):
+    """One atom (Z = 4) on the centre node of the dimer's mesh (8^3 cells of
+    degree 4 in a 16-bohr cube).  The mesh, the enrichment and the projectors
+    are symmetric under the cube's rotations about that node, so the p level
+    is 3-fold degenerate and holds 2 of the 4 electrons: the Fermi level
+    falls inside the shell and every p state is occupied 1/3 (F != E)."""
+    L = 16.0
+    return dict(name="atom", h=2.0, ncell=(8, 8, 8), p=4, atoms=np.array([[L / 2, L / 2, L / 2]]),
+                Z=np.full(1, 4.0), hproj=projector_strengths(1, seed), nstates=8, cheb_degree=20)
 
 
 def cluster(n_atoms, side, ncell, p, nstates, cheb_degree, seed=0, margin=6.0,

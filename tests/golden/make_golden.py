@@ -1,7 +1,7 @@
 """Writes the stored expected values of tests/golden/ by calling only the FP64
 oracle (no value here comes from the CUDA path).
 
-    python tests/golden/make_golden.py
+    python tests/golden/make_golden.py [dimer] [atom]     (default: all)
 """
 import json
 import os
@@ -37,7 +37,30 @@ def dimer_scf():
                 iters=out["iters"], history=[{k: float(v) for k, v in h.items()} for h in out["history"]])
 
 
+def atom_scf():
+    """One atom on the centre node of the dimer's mesh (8 states, degree 20): its
+    Fermi level lies in the 3-fold p shell, so F != E.  SCF to 1e-8."""
+    w = W.single_atom()
+    m = Mesh(w["h"], w["ncell"], w["p"])
+    s = EFESystem(m, w["atoms"], enrich=dict(alpha=1.2, r0=5.0 * 0.33 / 1.33, t=0.33),
+                  proj=dict(rc=1.0, rtrunc=6.0, h=w["hproj"]))
+    rows = s.nn + s.n_enr
+    X0 = W.random_block(rows, w["nstates"], 1)
+    u0 = W.random_block(rows, 1, 2)
+    X0[:s.nn] *= s.mask[:, None]
+    u0[:s.nn] *= s.mask[:, None]
+    out = S.scf(s, w["Z"], X0, u0, cheb_degree=w["cheb_degree"])
+    return dict(source="oracle.scf.scf on workloads.single_atom(); X0 = random_block(rows, 8, 1), "
+                       "u0 = random_block(rows, 1, 2), boundary rows zeroed",
+                E=out["E"], F=out["F"], mu=out["mu"], eig=[float(x) for x in out["eig"]],
+                occ=[float(x) for x in out["occ"]], iters=out["iters"],
+                history=[{k: float(v) for k, v in h.items()} for h in out["history"]])
+
+
+CASES = {"dimer": dimer_scf, "atom": atom_scf}
+
 if __name__ == "__main__":
-    with open(os.path.join(HERE, "dimer_scf.json"), "w") as f:
-        json.dump(dimer_scf(), f, indent=1)
-    print("wrote dimer_scf.json")
+    for name in (sys.argv[1:] or list(CASES)):
+        with open(os.path.join(HERE, name + "_scf.json"), "w") as f:
+            json.dump(CASES[name](), f, indent=1)
+        print("wrote %s_scf.json" % name)

@@ -6,7 +6,9 @@ quadrature integrals, the FE Poisson solve (CG to 1e-12 on both sides, so
 agreement to ~1e-10), the density of given vectors and occupations, and the
 full SCF against the oracle's stored result (energy to 1e-8 Ha/atom,
 eigenvalues to 1e-8 Ha), plus the mixed-precision SCF (bf16 tensor-core filter
-passes) against it at the 1e-5 Ha/atom target.
+passes) against it at the 1e-5 Ha/atom target; and the SCF of one atom whose
+Fermi level lies in its 3-fold p shell (partial occupations, F != E) against
+its own stored result.
 """
 import json
 import os
@@ -169,3 +171,32 @@ def test_scf_schedule_options_reach_the_same_solution():
     out = _run_scf(2, bf16_resid=1.0)
     assert out["converged"]
     assert abs(out["E"] - ref["E"]) / 2 < 1e-5, (out["E"], ref["E"])
+
+
+def test_scf_partial_shell_matches_oracle():
+    # occupations 2/3 in the degenerate p shell: the entropy term is 6e-3 Ha,
+    # so F and E are checked separately
+    from paper_2607_06848_gb300 import EFE
+    ref = json.load(open(os.path.join(HERE, "golden", "atom_scf.json")))
+    w = W.single_atom()
+    g = EFE(w["h"], w["ncell"], w["p"], w["atoms"], w["Z"], enrich=dict(alpha=1.2, r_end=5.0, t=0.33),
+            psp=dict(rc=1.0, r_trunc=6.0, h=w["hproj"], rloc=0.8))
+    try:
+        rows = g.dims["n_rows"]
+        nn = g.dims["n_nodes"]
+        mask = Mesh(w["h"], w["ncell"], w["p"]).interior_mask()
+        X0 = W.random_block(rows, w["nstates"], 1)
+        u0 = W.random_block(rows, 1, 2)
+        X0[:nn] *= mask[:, None]
+        u0[:nn] *= mask[:, None]
+        for prec, tol in ((0, 1e-8), (2, 1e-5)):
+            out = g.efe_scf(torch.tensor(X0, device="cuda"), torch.tensor(u0, device="cuda"),
+                            cheb_degree=w["cheb_degree"], precision=prec, log=lambda h: None)
+            assert out["converged"]
+            assert abs(out["E"] - ref["E"]) < tol, (prec, out["E"], ref["E"])
+            assert abs(out["F"] - ref["F"]) < tol, (prec, out["F"], ref["F"])
+            assert abs((out["F"] - out["E"]) - (ref["F"] - ref["E"])) < max(tol, 1e-9)
+            if prec == 0:
+                assert np.max(np.abs(out["eig"][:4] - np.array(ref["eig"][:4]))) < 1e-8
+    finally:
+        g.close()
