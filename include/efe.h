@@ -287,12 +287,15 @@ efe_status efe_integrate(efe_ctx *ctx, const double *a_q, const double *b_q, dou
  * service.  The per-cell partial sums go to a fixed array in the library's
  * device memory, sized for at most 65,536 cells (512 KB, held by every GPU
  * that loads the library until the process exits); larger meshes get
- * EFE_ERR_ARG.  The first call on a device looks the array up for that
- * device, so make that first call before any stream capture.  Every call
- * shares the array: calls that overlap on the GPU (several streams, several
- * contexts on one device) race; serialise them.  Nothing in the array needs
- * to start at zero: each call overwrites what it reads.  a_q, b_q: device
- * n_quad (b_q may be NULL); out: host. */
+ * EFE_ERR_ARG.  The call runs on the device the context was made on (made
+ * current for the call, the caller's device restored after).  The first call
+ * on a device looks the array's address up with that device current and
+ * caches it for the life of the process (the lookup is thread-safe), so make
+ * that first call before any stream capture.  Every call shares the array:
+ * calls that overlap on the GPU (several streams, several contexts on one
+ * device) race; serialise them.  Nothing in the array needs to start at
+ * zero: each call overwrites what it reads.  a_q, b_q: device n_quad (b_q may
+ * be NULL); out: host. */
 efe_status efe_integrate_noalloc(efe_ctx *ctx, const double *a_q, const double *b_q, double *out);
 
 typedef void (*efe_scf_log_fn)(void *user, int iter, double E, double F, double mu,

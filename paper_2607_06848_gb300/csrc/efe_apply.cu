@@ -1755,6 +1755,10 @@ efe_status efe_setup(const efe_mesh *mesh, const efe_atoms *atoms, const efe_enr
         return fail("bad pseudopotential");
     efe_ctx *ctx = new efe_ctx();
     ctx->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        delete ctx;
+        return fail("efe_setup: no current CUDA device");
+    }
     MeshDev &m = ctx->m;
     m.nx = mesh->ncell[0];
     m.ny = mesh->ncell[1];

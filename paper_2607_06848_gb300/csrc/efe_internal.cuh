@@ -34,6 +34,7 @@ constexpr int kNmHasE = 1 << 30, kNmHasP = 1 << 29, kNmAtomMask = (1 << 29) - 1;
 struct efe_ctx {
     std::string err;
     cudaStream_t stream = nullptr;
+    int device = 0;                           // CUDA device current at efe_setup (the stream's device)
     cusolverDnHandle_t solver = nullptr;
     MeshDev m{};
     int natoms = 0, n_enr = 0, n_proj = 0;

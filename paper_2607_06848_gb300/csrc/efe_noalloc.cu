@@ -6,7 +6,9 @@
 #include "efe_internal.cuh"
 #include "efe_funcs.cuh"
 
+#include <atomic>
 #include <cstdio>
+#include <mutex>
 
 namespace {
 
@@ -15,9 +17,51 @@ namespace {
 constexpr int kNoallocMaxCells = 65536;
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocMaxCells + 1];
 
-// per-device address of g_noalloc_scratch, looked up once with that device current
+// Per-device address of g_noalloc_scratch.  In host code the symbol's name is
+// only a host-side stand-in; the device address comes from
+// cudaGetSymbolAddress with that device current, once per device, and is
+// cached for the life of the process (the lookup is serialised by a mutex so
+// that two host threads making their first call at once do not race).
 constexpr int kMaxDevices = 64;
-double *g_scratch_addr[kMaxDevices] = {nullptr};
+std::atomic<double *> g_scratch_addr[kMaxDevices];
+std::mutex g_scratch_mutex;
+
+// Address of the array on `dev` (the context's device), current device unchanged on return.
+cudaError_t scratch_address(int dev, double **out) {
+    double *p = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (p) {
+        *out = p;
+        return cudaSuccess;
+    }
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    p = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        int cur = 0;
+        cudaError_t e = cudaGetDevice(&cur);
+        if (e != cudaSuccess) return e;
+        if (cur != dev && (e = cudaSetDevice(dev)) != cudaSuccess) return e;
+        e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_noalloc_scratch);
+        if (cur != dev) cudaSetDevice(cur);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev].store(p, std::memory_order_release);
+    }
+    *out = p;
+    return cudaSuccess;
+}
+
+// Makes `dev` current for the scope of one call and restores the caller's device.
+struct DeviceScope {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceScope(int dev) {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+        else if (err == cudaSuccess) prev = -1;
+    }
+    ~DeviceScope() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 // scratch[c] = sum over the Gauss points of cell c of w_q J a(q) [b(q)]
 __global__ void k_cell_integrals(MeshDev m, Tables1D T, const double *a, const double *b, double *scratch) {
@@ -66,19 +110,17 @@ extern "C" efe_status efe_integrate_noalloc(efe_ctx *ctx, const double *a_q, con
                    std::to_string(kNoallocMaxCells) + " cells; use efe_integrate";
         return EFE_ERR_ARG;
     }
-    int dev = 0;
-    EFE_CUDA(ctx, cudaGetDevice(&dev));
+    const int dev = ctx->device;   // the device the context (and its stream) was made on
     if (dev < 0 || dev >= kMaxDevices) {
         ctx->err = "efe_integrate_noalloc: device index out of range";
         return EFE_ERR_ARG;
     }
-    if (!g_scratch_addr[dev]) {
-        // once per device, with that device current (must precede any stream capture)
-        double *p = nullptr;
-        EFE_CUDA(ctx, cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_noalloc_scratch));
-        g_scratch_addr[dev] = p;
-    }
-    double *scratch = g_scratch_addr[dev];
+    // the launches below go to ctx->stream, so they run with the context's device current
+    DeviceScope scope(dev);
+    EFE_CUDA(ctx, scope.err);
+    double *scratch = nullptr;
+    // first call on a device: the address lookup (make it before any stream capture)
+    EFE_CUDA(ctx, scratch_address(dev, &scratch));
     Tables1D T = make_tables(ctx);
     k_cell_integrals<<<(unsigned)ncells, 256, 0, ctx->stream>>>(m, T, a_q, b_q, scratch);
     EFE_TRY(efe_check_launch(ctx, "k_cell_integrals"));
