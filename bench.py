@@ -167,47 +167,79 @@ def _traffic_per_unit(name, key):
     return None
 
 
-def roofline_bf16(w, d, N, m, ms_cell_launch, ms_rec_launch, pk, pk_kind):
-    """HBM rooflines of the two heaviest kernels of the bf16 filter, from their
-    live CUDA-event times; the one with the larger share of the step comes first.
+def algorithmic_bytes_bf16(w, d, N, m):
+    """Algorithmic HBM bytes of the bf16 filter, following the scope table's
+    measurement rule: per recurrence step 4 arrays x 2 B per DOF x vector (read
+    Y_{k-1} = M~^-1 Z_{k-1}, Y_{k-2}, Ghat; write Y_k -- bf16 storage; the first
+    step has no Y_{k-2}) plus the per-cell bf16 H_e stream (n_cells n_e^2 x 2 B,
+    unpadded).  Around the m - 1 steps: M V (read V, write MV), the start (read
+    HV, MV; write Ghat, Y_1) and V_out (read Y_m, V; write V_out): 54 B per
+    DOF x vector.  Returns per-launch bytes of the two kernels and the total of
+    one filter.  DOF = interior FE nodes + enriched rows."""
+    M = d["n_fe_dof"] + d["n_enr"]
+    z0 = (m - 2) / (m - 1)                    # share of the steps that read Y_{k-2}
+    rec = 2.0 * N * (3.0 + z0) * d["n_fe_dof"]
+    he = 2.0 * d["n_cells"] * d["ne"] ** 2
+    total = (m - 1) * (2.0 * N * (3.0 + z0) * M + he) + 54.0 * M * N
+    return rec, he, total
 
-    k_cell_mma (tensor-core cell products) streams per cell the bf16 H_e tile
-    (n_e^2 x 2 B), gathers X'_e (n_e N x 2 B) and writes Y_e (n_e N x 4 B):
-    2 n_e^2 N flop against 2 n_e^2 + 6 n_e N bytes -> ~66 flop/B at N = 154,
-    below the ridge (~292 flop/B), so HBM-bound.
-    k_gather_rec_w (node recurrence) reads, per interior node, its cell rows
-    (one per cell containing the node) and Z_{k-1}, Z_{k-2}, G, writes Z_k, and
-    writes zeros at Dirichlet nodes, 4 N bytes each (the coupling reads 16 bytes
-    of E and P_c per support entry and the small enriched rows, which stay in
-    cache: not counted)."""
-    p = w["p"]
-    nx, ny, nz = w["ncell"]
-    inc = (nx * (p + 1) - 2) * (ny * (p + 1) - 2) * (nz * (p + 1) - 2)   # interior (cell, node) pairs
-    z0 = (m - 2) / (m - 1)                       # the first recurrence step has no Z_{k-2}
-    rec_bytes = 4.0 * N * (inc + (2 + z0 + 1) * d["n_fe_dof"] + (d["n_nodes"] - d["n_fe_dof"]))
-    cell_bytes = d["n_cells"] * (2.0 * d["ne"] ** 2 + 6.0 * d["ne"] * N)
+
+def roofline_bf16(w, d, N, m, ms_cell_launch, ms_rec_launch, ms_filter, pk, pk_kind):
+    """HBM rooflines of the bf16 filter from live CUDA-event times: the whole
+    filter pass, and its two heaviest kernels (k_gather_rec_b: the FE-node
+    recurrence with the gather of the cell products; k_cell_mma: the tcgen05
+    cell products), with the algorithmic bytes of algorithmic_bytes_bf16 (the
+    recurrence's four arrays go to the node kernel, the H_e stream to the cell
+    kernel; what either moves beyond that -- the per-cell product round trip,
+    the operand gather, tile padding -- is excess, visible in 'traffic' where
+    an ncu summary of the current kernel exists).  Sorted by share of the pass:
+    the dominant kernel first, the whole pass last."""
     hbm = pk["hbm_gbs"]
+    rec_b, he_b, total_b = algorithmic_bytes_bf16(w, d, N, m)
     out = []
-    for name, bytes_, ms, traffic_key in (
-            ("k_gather_rec_w (FE-node recurrence: gather of cell products, coupling, Eq. residualapprox)",
-             rec_bytes, ms_rec_launch, None),
-            ("k_cell_mma (tcgen05 cell products, one launch per H apply)", cell_bytes, ms_cell_launch,
-             "bytes_per_cell")):
+    for name, bytes_, ms, traffic_file, key, per in (
+            ("k_gather_rec_b (FE-node recurrence: gather of cell products, coupling, Eq. residualapprox)",
+             rec_b, ms_rec_launch, "k_gather_rec_b_traffic.txt", "traffic_over_algorithmic", rec_b),
+            ("k_cell_mma (tcgen05 cell products, one launch per H apply)", he_b, ms_cell_launch,
+             "k_cell_mma_traffic.txt", "bytes_per_cell", d["n_cells"])):
         achieved = bytes_ / (ms / 1e3) / 1e9 if ms and ms > 0 else None
         traffic = None
         if d["ne"] == 343 and N == 154:      # counters taken on these kernels at this shape (p = 6, N = 154)
-            if traffic_key:
-                per = _traffic_per_unit("k_cell_mma_traffic.txt", traffic_key)
-                traffic = per * d["n_cells"] if per else None
-            else:
-                ratio = _traffic_per_unit("k_gather_rec_w_traffic.txt", "traffic_over_algorithmic")
-                traffic = ratio * bytes_ if ratio else None
+            f = _traffic_per_unit(traffic_file, key)
+            traffic = f * per if f else None
         out.append({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm if achieved else None, "traffic": traffic,
                     "algorithmic_bytes": bytes_, "peak_kind": pk_kind + " (burst copy)", "kernel": name,
                     "ms_per_launch": ms, "ms_per_step": ms * (m - 1) if ms else None})
     out.sort(key=lambda r: -(r["ms_per_step"] or 0.0))
+    achieved = total_b / (ms_filter / 1e3) / 1e9 if ms_filter > 0 else None
+    out.append({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm if achieved else None, "traffic": None, "algorithmic_bytes": total_b,
+                "peak_kind": pk_kind + " (burst copy)",
+                "kernel": "whole filter pass (m - 1 recurrence steps + G, V_out)", "ms_per_step": ms_filter,
+                "bound_value": M_N_m(d, N, m) / (total_b / (hbm * 1e9)) / 1e9})
     return out
+
+
+def M_N_m(d, N, m):
+    """The metric's units of one filter pass: (FE DOF + enriched DOF) x vectors x degree."""
+    return (d["n_fe_dof"] + d["n_enr"]) * N * m
+
+
+def roofline_rr(d, N, ms_rr, pk):
+    """Rayleigh-Ritz at the benchmark's size in FP64 on the CUDA cores: the FP64
+    H^E X (2 n_e^2 N flop per cell), the Grams X^T M X and X^T H X (2 M N^2
+    each) and the rotation of X, HX, MX (3 x 2 M N^2); the generalized N x N
+    eigensolve is not counted.  Peak: 152 SMs x 2 FP64 FMA lanes x 2 flop x max
+    clock (the nominal ~1.25 TFLOP/s of GB300's FP64)."""
+    M = d["n_rows"]
+    flops = 2.0 * d["ne"] ** 2 * N * d["n_cells"] + 5 * 2.0 * M * N * N
+    peak = 152 * 2 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = flops / (ms_rr / 1e3) / 1e12 if ms_rr > 0 else None
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None, "traffic": None, "flops": flops,
+            "peak_kind": "derived from SM count, FP64 lanes and max clock", "ms": ms_rr,
+            "kernel": "Rayleigh-Ritz (FP64 H^E X, Grams, rotation; cuSOLVER sygvd not counted)"}
 
 
 def roofline_simt(head, d, N, ms_sweep, pk):
@@ -331,11 +363,21 @@ def run_ours(args):
     clk = ClockSampler(local)
     ms, cell_ms, launches, rec_ms_launch = timed(precs[head], args.steps, args.warmup)
     clocks = clk.stop()
-    by_prec = {head: {"ms_per_step": ms, "value": units / (ms / 1e3) / 1e9, "steps": args.steps}}
+    by_prec = {head: {"ms_per_step": ms, "value": units / (ms / 1e3) / 1e9, "steps": args.steps,
+                      "warmup": args.warmup}}
     for extra in args.also:
         if extra != head:
-            mse, _, _, _ = timed(precs[extra], 1, 0)
-            by_prec[extra] = {"ms_per_step": mse, "value": units / (mse / 1e3) / 1e9, "steps": 1}
+            mse, _, _, _ = timed(precs[extra], 1, 1)
+            by_prec[extra] = {"ms_per_step": mse, "value": units / (mse / 1e3) / 1e9, "steps": 1, "warmup": 1}
+    # Rayleigh-Ritz at this size (one warm call, then one timed; its FP64 H^E X dominates)
+    Xr = X.clone()
+    HXr = torch.empty_like(Xr)
+    g.efe_rayleigh_ritz(Xr, HXr)
+    Xr.copy_(X)
+    torch.cuda.synchronize()
+    g.efe_rayleigh_ritz(Xr, HXr)
+    ms_rr = g.stats()["ms_rr"]
+    del Xr, HXr
 
     # end to end through the public call with host buffers (pinned)
     Vh = torch.empty((rows, N), dtype=torch.float64, pin_memory=True)
@@ -360,7 +402,7 @@ def run_ours(args):
     pk, pk_kind = peaks()
     ms_sweep = cell_ms / (m - 1)          # m - 1 H applies per filter pass
     if head == "bf16":
-        rl = roofline_bf16(w, d, N, m, ms_sweep, rec_ms_launch, pk, pk_kind)
+        rl = roofline_bf16(w, d, N, m, ms_sweep, rec_ms_launch, ms, pk, pk_kind)
     else:
         rl = [roofline_simt(head, d, N, ms_sweep, pk)]
     line = {
@@ -378,6 +420,7 @@ def run_ours(args):
         "by_precision": by_prec,
         "roofline": rl[0],
         "roofline_kernels": rl,
+        "rayleigh_ritz": roofline_rr(d, N, ms_rr, pk),
         "e2e": {"value": job_value(units, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,

@@ -185,9 +185,20 @@ efe_status efe_lanczos(efe_ctx *ctx, const double *u0, int k, double out[3]);
  * blocks (E = H^ac - C H^cc, H^E_ee = H^aa - C H^ca - E C^T and the projector
  * overlaps P^E = P_a - P_c C^T, assembled in FP64 by efe_set_potential and
  * setup) rather than as T^T H_raw T, whose two terms cancel when the
- * enrichment is nearly representable by the FE space. */
+ * enrichment is nearly representable by the FE space.  In bf16 the FE rows of
+ * the recurrence are carried as Y_k = M~^-1 Z_k (and G as M~^-1 G) in bf16
+ * storage -- Y_k is the operand of the next cell products -- with FP32
+ * arithmetic; the storage rounding scales with the residual like that of the
+ * operands.  The enriched rows keep Z_k in FP32. */
 efe_status efe_filter(efe_ctx *ctx, const double *V, const double *HV, const double *lam,
                       int N, int m, const double bounds[3], efe_precision prec, double *Vout);
+
+/* Storage of the per-cell products H_e Y_e inside the bf16 filter before the
+ * per-node sums: EFE_BF16 (the default; half the memory traffic of that
+ * round trip) or EFE_FP32.  Both accumulate in FP32 on the tensor cores and
+ * sum in FP32.  Not a part of the paper's method: a precision knob of this
+ * implementation.  EFE_ERR_ARG for other values. */
+efe_status efe_set_cell_storage(efe_ctx *ctx, efe_precision prec);
 
 /* Rayleigh-Ritz with the exact M^E (Eq. projectedKSEig), in place:
  * X <- X D, HX <- H^E X D with D^T (X^T M X) D = I, ascending eigenvalues.

@@ -401,62 +401,33 @@ __device__ __forceinline__ AxisCells axis_cells(int i, int p, int nc) {
     return a;
 }
 
-// Xb[n][4q..4q+3] = bf16( minv[n] Z[n] ) at interior nodes, zero at the
-// Dirichlet nodes and in the padding columns (ldb >= ldz)
-__global__ void __launch_bounds__(256) k_pre_bf16_w(MeshDev m, int nruns_x, const float *__restrict__ Z, int ldz,
-                                                    int ldb, const double *__restrict__ minv,
-                                                    __nv_bfloat16 *__restrict__ Xb) {
-    const int lane = threadIdx.x & 31;
-    const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const long long nrows = (long long)m.Gy * m.Gz;
-    if (wid >= nrows * nruns_x) return;
-    const int xr = (int)(wid % nruns_x);
-    const long long yz = wid / nruns_x;
-    const int iy = (int)(yz % m.Gy), iz = (int)(yz / m.Gy);
-    const int x0 = xr * kRun;
-    const int nrun = min(kRun, m.Gx - x0);
-    const bool yz_in = iy > 0 && iz > 0 && iy < m.Gy - 1 && iz < m.Gz - 1;
-    const long long n0 = yz * m.Gx + x0;
-    const int ncg = ldb / 4;
-    int k = 0, cg = lane;
-    while (cg >= ncg) { cg -= ncg; ++k; }
-    for (; k < nrun;) {
-        const int ix = x0 + k;
-        const long long n = n0 + k;
-        const int j = 4 * cg;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (yz_in && ix > 0 && ix < m.Gx - 1 && j < ldz) {
-            const float mi = (float)minv[n];
-            v = f4(Z + (size_t)n * ldz + j);
-            v.x *= mi; v.y *= mi; v.z *= mi; v.w *= mi;
-        }
-        __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
-        uint2 pk;
-        pk.x = *reinterpret_cast<uint32_t *>(&lo);
-        pk.y = *reinterpret_cast<uint32_t *>(&hi);
-        *reinterpret_cast<uint2 *>(Xb + (size_t)n * ldb + j) = pk;
-        cg += 32;
-        while (cg >= ncg) { cg -= ncg; ++k; }
-    }
+// bf16 quads: 4 consecutive columns as one 8-byte load/store
+__device__ inline void st4(__nv_bfloat16 *p, const float4 v) {
+    __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+    uint2 pk;
+    pk.x = *reinterpret_cast<uint32_t *>(&lo);
+    pk.y = *reinterpret_cast<uint32_t *>(&hi);
+    *reinterpret_cast<uint2 *>(p) = pk;
 }
 
-// One recurrence step at the FE nodes of a run, fused with the gather of the
-// cell products and the FE-enrichment coupling:
-//   HY[n] = sum over the cells of n of Y_cell[row(n)] + sum_e (E_e . Ye + Pc_e . W)
-//   Zn[n] = a (HY[n] - c Z1[n]) - b Z0[n] + a G[n] ck      (Eq. residualapprox)
-// with E the FE-enrichment block of H^E (E^T Ye is the enrichment's part of
-// the FE rows).  The enriched rows Ye and the projector amplitudes W are read
-// from bf16 copies: every (node, entry) pair reloads 8 of their rows from L1,
-// and the bf16 rounding matches that of the cell operands.
-__global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x, int ldz, const float *__restrict__ Yc,
-                                                      int ldy, const long long *__restrict__ node_ptr,
-                                                      const int *__restrict__ nm_atom, const float *__restrict__ Ec,
-                                                      const float *__restrict__ Pc,
-                                                      const __nv_bfloat16 *__restrict__ Ye,
-                                                      const __nv_bfloat16 *__restrict__ W, int lde, int use_h, int use_p,
-                                                      const float *__restrict__ Z1, const float *__restrict__ Z0,
-                                                      const float *__restrict__ G, const float *__restrict__ ck,
-                                                      float a, float c, float b, float *__restrict__ Zn) {
+// One recurrence step of the bf16 filter at the FE nodes of a run, in the
+// variables Y = M~^-1 Z (FE rows: Y = (M^cc)^-1 Z), stored in bf16:
+//   HY[n] = sum over the cells of n of Y_cell[row(n)]
+//   Y_k[n] = a ((M^cc_n)^-1 HY[n] - c Y_{k-1}[n]) - b Y_{k-2}[n] + a Ghat[n] ck
+// (Eq. residualapprox multiplied by (M^cc)^-1, Ghat = (M^cc)^-1 G), all
+// arithmetic in FP32.  The cell rows already hold the FE row's coupling
+// E^T Y_e + P_c^T W (added by the cell products of the cell that owns the
+// node), so this is a plain streaming pass.  The storage rounding of Y and
+// Ghat is relative to residual-sized quantities, like the bf16 rounding of the
+// cell operands (which are Y_{k-1} itself).  Cell rows: FP32 or bf16 (TC).
+// A warp takes a run of kRun nodes along x and walks its rows as one flat
+// list of 4-column groups (every lane busy; many independent loads in flight).
+template <typename TC>
+__global__ void __launch_bounds__(256, 4)
+    k_gather_rec_b(MeshDev m, int nruns_x, int ldb, const TC *__restrict__ Yc, const double *__restrict__ minv,
+                   const __nv_bfloat16 *__restrict__ Y1, const __nv_bfloat16 *__restrict__ Y0,
+                   const __nv_bfloat16 *__restrict__ G, const float *__restrict__ ck, float a, float c, float b,
+                   __nv_bfloat16 *__restrict__ Yn) {
     const int lane = threadIdx.x & 31;
     const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nrows = (long long)m.Gy * m.Gz;
@@ -468,7 +439,6 @@ __global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x,
     const int nrun = min(kRun, m.Gx - x0);
     const bool yz_in = iy > 0 && iz > 0 && iy < m.Gy - 1 && iz < m.Gz - 1;
     const long long n0 = yz * m.Gx + x0;
-    // y/z part of the cell rows: cell index (without x) and local offset (without x)
     int cyz[4];                // cell index without x (cells < 2^31)
     int lyz[4];
     bool vyz[4];
@@ -484,23 +454,17 @@ __global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x,
             lyz[t] = (lz * m.np1 + ly) * m.np1;
         }
     }
-    const int ncg = ldz / 4;
+    const int ncg = ldb / 4;
     int k = 0, cg = lane;
     while (cg >= ncg) { cg -= ncg; ++k; }
     for (; k < nrun;) {
         const int ix = x0 + k;
         const long long n = n0 + k;
         const int j = 4 * cg;
-        const size_t row = (size_t)n * ldz + j;
+        const size_t row = (size_t)n * ldb + j;
         if (!(yz_in && ix > 0 && ix < m.Gx - 1)) {
-            *reinterpret_cast<float4 *>(Zn + row) = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<uint2 *>(Yn + row) = make_uint2(0u, 0u);
         } else {
-            // coupling range first, so that its loads overlap the row loads below
-            long long e0 = 0, e1 = 0;
-            if (node_ptr) {
-                e0 = node_ptr[n];
-                e1 = node_ptr[n + 1];
-            }
             const AxisCells ax = axis_cells(ix, m.p, m.nx);
             float4 y[8];
 #pragma unroll
@@ -509,53 +473,55 @@ __global__ void __launch_bounds__(256, 4) k_gather_rec_w(MeshDev m, int nruns_x,
                 const bool ok = vyz[t] && (sx <= ax.two);
                 const long long cell = (long long)(cyz[t] + ax.k0 + sx);
                 const int l = lyz[t] + (sx ? 0 : ax.a0);
-                y[u] = ok ? f4(Yc + (cell * m.ne + l) * ldy + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+                y[u] = ok ? f4(Yc + (cell * m.ne + l) * ldb + j) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            const float4 z1 = f4(Z1 + row);
-            const float4 z0 = Z0 ? f4(Z0 + row) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 y1 = f4(Y1 + row);
+            const float4 y0 = Y0 ? f4(Y0 + row) : make_float4(0.f, 0.f, 0.f, 0.f);
             const float4 gg = f4(G + row);
             const float4 kk = f4(ck + j);
-            // u = 4 sz + 2 sy + sx: the cells summed in the order z, y, x (outer to inner)
+            const float mi = (float)minv[n];
+            // the cells in the order z, y, x (outer to inner)
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int u = 0; u < 8; ++u) { acc.x += y[u].x; acc.y += y[u].y; acc.z += y[u].z; acc.w += y[u].w; }
-            {
-                for (long long e = e0; e < e1; ++e) {
-                    const int av = nm_atom[e];
-                    const int rb = (4 * (av & kNmAtomMask)) * lde + j;
-                    if (use_h && (av & kNmHasE)) {
-                        const float4 h = f4(Ec + 4 * e);
-                        const __nv_bfloat16 *yb = Ye + rb;
-                        fma4(acc, h.x, f4(yb));
-                        fma4(acc, h.y, f4(yb + lde));
-                        fma4(acc, h.z, f4(yb + 2 * lde));
-                        fma4(acc, h.w, f4(yb + 3 * lde));
-                    }
-                    if (use_p && (av & kNmHasP)) {
-                        const float4 pp = f4(Pc + 4 * e);
-                        const __nv_bfloat16 *wb = W + rb;
-                        fma4(acc, pp.x, f4(wb));
-                        fma4(acc, pp.y, f4(wb + lde));
-                        fma4(acc, pp.z, f4(wb + 2 * lde));
-                        fma4(acc, pp.w, f4(wb + 3 * lde));
-                    }
-                }
-            }
-            float4 zn;
-            zn.x = a * (acc.x - c * z1.x) - b * z0.x + a * gg.x * kk.x;
-            zn.y = a * (acc.y - c * z1.y) - b * z0.y + a * gg.y * kk.y;
-            zn.z = a * (acc.z - c * z1.z) - b * z0.z + a * gg.z * kk.z;
-            zn.w = a * (acc.w - c * z1.w) - b * z0.w + a * gg.w * kk.w;
-            *reinterpret_cast<float4 *>(Zn + row) = zn;
+            float4 yn;
+            yn.x = a * (mi * acc.x - c * y1.x) - b * y0.x + a * gg.x * kk.x;
+            yn.y = a * (mi * acc.y - c * y1.y) - b * y0.y + a * gg.y * kk.y;
+            yn.z = a * (mi * acc.z - c * y1.z) - b * y0.z + a * gg.z * kk.z;
+            yn.w = a * (mi * acc.w - c * y1.w) - b * y0.w + a * gg.w * kk.w;
+            st4(Yn + row, yn);
         }
         cg += 32;
         while (cg >= ncg) { cg -= ncg; ++k; }
     }
 }
 
+// The coupling table of the cell products, YW[I][cb][r][c] (bf16, MN-major
+// 8 x 8 core matrices): rows r < 4 are Y_e rows 4I + r, rows r >= 4 are W rows
+// 4I + r - 4, column j = 8 cb + c; zero past N and for the extra block I = natoms.
+__global__ void k_pack_yw(int natoms, int nCB, int N, int ldb, const __nv_bfloat16 *__restrict__ Ye16,
+                          const __nv_bfloat16 *__restrict__ W16, __nv_bfloat16 *__restrict__ YW) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)(natoms + 1) * nCB * 64) return;
+    const int cc = (int)(idx % 8), r = (int)((idx / 8) % 8);
+    const long long ib = idx / 64;
+    const int cb = (int)(ib % nCB), I = (int)(ib / nCB);
+    const int j = 8 * cb + cc;
+    __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+    if (I < natoms && j < N) {
+        if (r < 4) {
+            if (Ye16) v = Ye16[(size_t)(4 * I + r) * ldb + j];
+        } else if (W16) {
+            v = W16[(size_t)(4 * I + r - 4) * ldb + j];
+        }
+    }
+    YW[idx] = v;
+}
+
 // Support reduction: warps over positions (8 rows in flight per warp), lanes
 // over 4-column vectors (two 128-column slots), one block per (chunk, atom).
 __device__ inline float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ inline float4 ld4(const __nv_bfloat16 *p) { return f4(p); }
 
 template <typename T>
 __global__ void __launch_bounds__(256, 4) k_support_reduce3(const long long *sup_off, const int *sup_node,
@@ -628,18 +594,63 @@ __global__ void __launch_bounds__(256, 4) k_support_reduce3(const long long *sup
     }
 }
 
-// strided row kernels for the FP32 buffers of the tensor-core filter
-__global__ void __launch_bounds__(256) k_rows_residual_f(long long rows, int N, int ldz, const double *HV,
-                                                         const double *MV, const double *lam, float s1e, float *G,
-                                                         float *Z1) {
+// Start of the bf16 filter, a warp per row, lanes over 4-column groups.
+// g = HV - (M V) diag(lv): the eigen-residual G (the standard filter passes
+// lv = c and the approximate M~; both are diagonal M^cc on the FE rows, formed
+// here from V, so M V is never stored for them; MVe holds the enriched rows
+// of M V).  FE rows (the Y = (M^cc)^-1 Z variables, bf16, row stride ldb,
+// zero at the Dirichlet nodes and in the padding columns): Ghat = (M^cc)^-1 g,
+// Y_1 = s1e Ghat, Y_0 = V (standard filter only).  Enriched rows (FP32,
+// stride ldb): G_e = g, Z_1 = s1e g, Z_0 = MVe (standard only).
+__global__ void __launch_bounds__(256) k_filter_start_b(long long nn, long long rows, int N, int ldb,
+                                                        const double *__restrict__ HV, const double *__restrict__ V,
+                                                        const double *__restrict__ MVe,
+                                                        const double *__restrict__ lv, const double *__restrict__ mcc,
+                                                        const double *__restrict__ minv, double s1e,
+                                                        __nv_bfloat16 *__restrict__ Gb,
+                                                        __nv_bfloat16 *__restrict__ Y1b,
+                                                        __nv_bfloat16 *__restrict__ Y0b, float *__restrict__ Ge,
+                                                        float *__restrict__ Z1e, float *__restrict__ Z0e) {
     const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (r >= rows) return;
-    for (int j = threadIdx.x & 31; j < ldz; j += 32) {
-        const float gv = j < N ? (float)(HV[r * N + j] - MV[r * N + j] * lam[j]) : 0.f;
-        G[r * ldz + j] = gv;
-        Z1[r * ldz + j] = s1e * gv;
+    const bool fe = r < nn;
+    const double mc = fe ? mcc[r] : 0.0, mi = fe ? minv[r] : 0.0;
+    const double *hv = HV + r * N, *vv = V + r * N;
+    const double *mv = fe ? nullptr : MVe + (r - nn) * N;
+    for (int j0 = 4 * (threadIdx.x & 31); j0 < ldb; j0 += 128) {
+        float g[4], v[4], m4[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int j = j0 + i;
+            g[i] = v[i] = m4[i] = 0.f;
+            if (j < N) {
+                const double mvj = fe ? mc * vv[j] : mv[j];
+                const double gd = hv[j] - mvj * lv[j];
+                if (fe) {
+                    g[i] = (float)(mi * gd);
+                    if (Y0b && mi != 0.0) v[i] = (float)vv[j];
+                } else {
+                    g[i] = (float)gd;
+                    m4[i] = (float)mvj;
+                }
+            }
+        }
+        const float4 G4 = make_float4(g[0], g[1], g[2], g[3]);
+        const float4 S4 = make_float4((float)s1e * g[0], (float)s1e * g[1], (float)s1e * g[2], (float)s1e * g[3]);
+        if (fe) {
+            const size_t o = (size_t)r * ldb + j0;
+            st4(Gb + o, G4);
+            st4(Y1b + o, S4);
+            if (Y0b) st4(Y0b + o, make_float4(v[0], v[1], v[2], v[3]));
+        } else {
+            const size_t o = (size_t)(r - nn) * ldb + j0;
+            *reinterpret_cast<float4 *>(Ge + o) = G4;
+            *reinterpret_cast<float4 *>(Z1e + o) = S4;
+            if (Z0e) *reinterpret_cast<float4 *>(Z0e + o) = make_float4(m4[0], m4[1], m4[2], m4[3]);
+        }
     }
 }
+
 __global__ void k_enr_minv_f(int n_enr, int N, int ld, const double *Binv, const float *X, float *Y, int ldy,
                              __nv_bfloat16 *Y16 = nullptr) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -663,15 +674,17 @@ __global__ void k_enr_rec_v(int n_enr, int N, int ldz, const double *Yraw, const
     const float z0 = Z0 ? Z0[o] : 0.f;
     Zn[o] = a * (hy - c * Z1[o]) - b * z0 + a * G[o] * ck[j];
 }
-__global__ void __launch_bounds__(256) k_rows_minv_vout(long long nn, long long rows, int N, int ldz,
-                                                        const double *minv, const float *Z, const float *Ye, int lde,
-                                                        const double *V, const double *cm, double *Vout) {
+// V_out = M~^-1 Z_m + V diag(C_m(lam)): FE rows from the bf16 Y_m, enriched
+// rows from Ye = (M~^ee)^-1 Z_e (FP32); warp per row.
+__global__ void __launch_bounds__(256) k_vout_b(long long nn, long long rows, int N, int ldb,
+                                                const __nv_bfloat16 *__restrict__ Yb, const float *__restrict__ Ye,
+                                                const double *__restrict__ V, const double *__restrict__ cm,
+                                                double *__restrict__ Vout) {
     const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (r >= rows) return;
     const bool fe = r < nn;
-    const float mi = fe ? (float)minv[r] : 0.f;
     for (int j = threadIdx.x & 31; j < N; j += 32) {
-        const float y = fe ? mi * Z[r * ldz + j] : Ye[(r - nn) * lde + j];
+        const float y = fe ? __bfloat162float(Yb[r * ldb + j]) : Ye[(r - nn) * ldb + j];
         Vout[r * N + j] = (double)y + V[r * N + j] * cm[j];
     }
 }
@@ -1319,11 +1332,16 @@ efe_status filter_impl(efe_ctx *ctx, const double *V, const double *HV, const do
 
 }  // namespace
 
-// Residual filter with tcgen05 cell products (bf16 operands, FP32 accumulate)
-// and FP32 recurrence storage; G, V_out and the Chebyshev scalars as in
-// filter_impl.  Per recurrence step: M~^-1 on the enriched rows, the fused
-// bf16 producer of T M~^-1 Z, the tensor-core cell products, the coupling
-// reductions, and the fused gather + recurrence.
+// Residual filter with tcgen05 cell products (bf16 operands, FP32 accumulate).
+// The recurrence runs in the variables Y = M~^-1 Z: the FE rows of Y_k are
+// exactly the B operand of the next cell products, so they are stored once,
+// in bf16, and read by TMA with no separate operand pass; Ghat = (M^cc)^-1 G
+// likewise.  The enriched rows keep Z in FP32 (a few hundred rows).  All
+// arithmetic is FP32 (FP32 accumulation in the products and the sums); G,
+// V_out and the Chebyshev scalars are formed in FP64 as in filter_impl.  Per
+// recurrence step: Y_e = (M~^ee)^-1 Z_e, the tensor-core cell products, the
+// coupling reductions E Y_c, P_c Y_c over the supports, the enriched rows, and
+// the fused gather + recurrence of the FE rows.
 static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV, const double *lam_dev, int N,
                                 int m, const double bounds[3], double *Vout, bool standard) {
     const MeshDev &mh = ctx->m;
@@ -1336,6 +1354,10 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     }
     if (nn > 2147483647LL) {
         ctx->err = "mesh too large for 32-bit node indices";
+        return EFE_ERR_ARG;
+    }
+    if (N > 256) {
+        ctx->err = "the tensor-core filter takes at most 256 columns per call";
         return EFE_ERR_ARG;
     }
     if (!ctx->he16_valid) EFE_TRY(efe_tc_prepare(ctx));
@@ -1354,38 +1376,52 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
         std::fill(ck.begin(), ck.end(), 0.0);
         cvec.assign(N, c);
     }
-    const int ldz = (N + 3) / 4 * 4, ldb = (N + 7) / 8 * 8, ldy = ldz, lde = ldz;
-    std::vector<float> ckf((size_t)(m + 1) * ldz, 0.f);
+    // one row stride for every filter buffer: 8 bf16 = 16 B (TMA rows), and a
+    // multiple of 4 floats for the FP32 rows
+    const int ldb = (N + 7) / 8 * 8;
+    std::vector<float> ckf((size_t)(m + 1) * ldb, 0.f);
     for (int k = 0; k <= m; ++k)
-        for (int j = 0; j < N; ++j) ckf[(size_t)k * ldz + j] = (float)ck[(size_t)k * N + j];
+        for (int j = 0; j < N; ++j) ckf[(size_t)k * ldb + j] = (float)ck[(size_t)k * N + j];
     const long long ncells = (long long)mh.nx * mh.ny * mh.nz;
-    const size_t nz = (size_t)rows * ldz;
-    size_t need = 16384 + sizeof(double) * (size_t)rows * N + sizeof(double) * (size_t)(m + 2) * N +
-                  sizeof(float) * ckf.size() + sizeof(float) * 4 * nz +
-                  (sizeof(float) + 2) * 2 * ((size_t)std::max(ne_, ctx->n_proj) * lde + 8) + 2 * (size_t)nn * ldb +
-                  4 * (size_t)ncells * mh.ne * ldy;
+    const bool cells16 = ctx->cells_bf16;
+    const size_t nb = (size_t)nn * ldb, neb = (size_t)std::max(ne_, 1) * ldb + 8,
+                 npb = (size_t)std::max(ctx->n_proj, 1) * ldb + 8;
+    const size_t ycells = (size_t)ncells * mh.ne * ldb;
+    const bool cpl = (ctx->enrich || ctx->nonlocal) && ctx->natoms > 0;
+    // the coupling table read by the cell products: every column chunk they may read
+    const int nCB = efe_tc_columns(ctx, N, ldb) / 8;
+    const size_t nyw = cpl ? (size_t)(ctx->natoms + 1) * nCB * 64 : 64;
+    size_t need = 32768 + sizeof(double) * ((size_t)std::max(ne_, 1) * N + (size_t)(m + 2) * N) +
+                  sizeof(float) * ckf.size() +
+                  2 * 4 * nb + sizeof(float) * (5 * neb + npb) + 2 * (neb + npb + nyw) +
+                  (cells16 ? 2 : 4) * ycells;
     EFE_TRY(efe_workspace(ctx, need));
     Carver cv{(char *)ctx->d_ws, ctx->ws_bytes};
-    double *MV = cv.take<double>((size_t)rows * N), *dck = cv.take<double>((size_t)(m + 1) * N);
+    double *MV = cv.take<double>((size_t)std::max(ne_, 1) * N), *dck = cv.take<double>((size_t)(m + 1) * N);
     double *dc = cv.take<double>((size_t)N);
     float *fck = cv.take<float>(ckf.size());
-    float *G = cv.take<float>(nz), *Z0 = cv.take<float>(nz), *Z1 = cv.take<float>(nz), *Z2 = cv.take<float>(nz);
-    float *Ye = cv.take<float>((size_t)std::max(ne_, 1) * lde + 4);
-    float *W32 = cv.take<float>((size_t)std::max(ctx->n_proj, 1) * lde + 4);
-    __nv_bfloat16 *Ye16 = cv.take<__nv_bfloat16>((size_t)std::max(ne_, 1) * lde + 8);
-    __nv_bfloat16 *W16 = cv.take<__nv_bfloat16>((size_t)std::max(ctx->n_proj, 1) * lde + 8);
-    __nv_bfloat16 *Xb = cv.take<__nv_bfloat16>((size_t)nn * ldb);
-    float *Ycells = cv.take<float>((size_t)ncells * mh.ne * ldy);
+    __nv_bfloat16 *Yb[3], *Gb;
+    for (auto &y : Yb) y = cv.take<__nv_bfloat16>(nb);
+    Gb = cv.take<__nv_bfloat16>(nb);
+    float *Ze[3], *Ge;
+    for (auto &z : Ze) z = cv.take<float>(neb);
+    Ge = cv.take<float>(neb);
+    float *Ye = cv.take<float>(neb);
+    float *W32 = cv.take<float>(npb);
+    __nv_bfloat16 *Ye16 = cv.take<__nv_bfloat16>(neb);
+    __nv_bfloat16 *W16 = cv.take<__nv_bfloat16>(npb);
+    __nv_bfloat16 *YW = cv.take<__nv_bfloat16>(nyw);
+    void *Ycells = cells16 ? (void *)cv.take<__nv_bfloat16>(ycells) : (void *)cv.take<float>(ycells);
     EFE_CUDA(ctx, cudaMemcpyAsync(dck, ck.data(), sizeof(double) * ck.size(), cudaMemcpyHostToDevice, ctx->stream));
     EFE_CUDA(ctx, cudaMemcpyAsync(fck, ckf.data(), sizeof(float) * ckf.size(), cudaMemcpyHostToDevice, ctx->stream));
     if (standard)
         EFE_CUDA(ctx, cudaMemcpyAsync(dc, cvec.data(), sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
     EFE_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
-    EFE_CUDA(ctx, cudaMemsetAsync(Ye, 0, sizeof(float) * ((size_t)std::max(ne_, 1) * lde + 4), ctx->stream));
-    EFE_CUDA(ctx, cudaMemsetAsync(W32, 0, sizeof(float) * ((size_t)std::max(ctx->n_proj, 1) * lde + 4), ctx->stream));
-    EFE_CUDA(ctx, cudaMemsetAsync(Ye16, 0, 2 * ((size_t)std::max(ne_, 1) * lde + 8), ctx->stream));
-    EFE_CUDA(ctx, cudaMemsetAsync(W16, 0, 2 * ((size_t)std::max(ctx->n_proj, 1) * lde + 8), ctx->stream));
-    const bool cpl = (ctx->enrich || ctx->nonlocal) && ctx->natoms > 0;
+    // padding columns of the small enriched-row buffers are read as zeros
+    EFE_CUDA(ctx, cudaMemsetAsync(Ye, 0, sizeof(float) * neb, ctx->stream));
+    EFE_CUDA(ctx, cudaMemsetAsync(W32, 0, sizeof(float) * npb, ctx->stream));
+    EFE_CUDA(ctx, cudaMemsetAsync(Ye16, 0, 2 * neb, ctx->stream));
+    EFE_CUDA(ctx, cudaMemsetAsync(W16, 0, 2 * npb, ctx->stream));
     HxScratch s{};
     if (cpl) {
         EFE_TRY(hx_scratch(ctx, N, s));
@@ -1399,46 +1435,34 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     ctx->cell_launches = 0;
     Timer tm(ctx->stream);
     const long long l0 = ctx->launches;
-    EFE_TRY(m_apply(ctx, V, MV, N, !standard));
-    k_rows_residual_f<<<rb_all, 256, 0, ctx->stream>>>(rows, N, ldz, HV, MV, standard ? dc : lam_dev,
-                                                       (float)(sig[1] / e), G, Z1);
-    ctx->launches++;
-    float *Zprev = nullptr, *Zcur = Z1, *Znext = Z2, *Zspare = Z0;
-    if (standard) {
-        // Z_0 = M~ V in FP32 (padding columns zero)
-        EFE_CUDA(ctx, cudaMemsetAsync(Z0, 0, sizeof(float) * nz, ctx->stream));
-        k_to_float_strided<<<nblk(rows * N, 256), 256, 0, ctx->stream>>>(rows, N, MV, Z0, ldz);
+    // M V on the enriched rows only (exact M^ee for the residual, its atom blocks
+    // for the standard filter); the FE rows' M^cc V is formed inside the start
+    if (ne_) {
+        k_enr_mat<double><<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(
+            ne_, N, standard ? ctx->d_Mblk : ctx->d_Mee, standard ? 1 : 0, V + nn * N, MV);
         ctx->launches++;
-        Zprev = Z0;
     }
-    if (N > 256) {
-        ctx->err = "the tensor-core filter takes at most 256 columns per call";
-        return EFE_ERR_ARG;
-    }
-    if (N > 128 * 2) return EFE_ERR_ARG;
+    k_filter_start_b<<<rb_all, 256, 0, ctx->stream>>>(nn, rows, N, ldb, HV, V, MV, standard ? dc : lam_dev,
+                                                      ctx->d_mcc, ctx->d_minv, sig[1] / e, Gb, Yb[1],
+                                                      standard ? Yb[0] : nullptr, Ge, Ze[1],
+                                                      standard ? Ze[0] : nullptr);
+    ctx->launches++;
+    EFE_TRY(efe_check_launch(ctx, "k_filter_start_b"));
+    int iprev = standard ? 0 : -1, icur = 1, inext = 2;
     for (int k = 2; k <= m; ++k) {
         const float ak = (float)(2.0 * sig[k] / e), bk = (float)(sig[k - 1] * sig[k]), cf = (float)c;
+        const __nv_bfloat16 *Ycur = Yb[icur], *Yprev = iprev >= 0 ? Yb[iprev] : nullptr;
+        const float *Zcur = Ze[icur], *Zprev = iprev >= 0 ? Ze[iprev] : nullptr;
         if (ne_) {
-            k_enr_minv_f<<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(ne_, N, ldz, ctx->d_Mblk_inv,
-                                                                                Zcur + nn * ldz, Ye, lde, Ye16);
+            k_enr_minv_f<<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(ne_, N, ldb, ctx->d_Mblk_inv, Zcur,
+                                                                                Ye, ldb, Ye16);
             ctx->launches++;
         }
-        // cell operand: the FE part of Y = M~^-1 Z in bf16 (no T transform: the
-        // enrichment enters through the blocks E and H^E_ee of H^E)
-        k_pre_bf16_w<<<rb_run, 256, 0, ctx->stream>>>(mh, nruns_x, Zcur, ldz, ldb, ctx->d_minv, Xb);
-        ctx->launches++;
-        EFE_TRY(efe_check_launch(ctx, "k_pre_bf16_w"));
-        {
-            auto *ev = cell_event_pair(ctx);
-            if (ev) cudaEventRecord(ev->first, ctx->stream);
-            EFE_TRY(efe_tc_cells(ctx, Xb, ldb, N, Ycells, ldy, ctx->d_err));
-            if (ev) cudaEventRecord(ev->second, ctx->stream);
-        }
         if (cpl) {
-            // E Y_c and P_c Y_c over the supports, from the FP32 Z scaled by M^cc^-1
-            k_support_reduce3<float><<<(unsigned)(s.nch * std::max(ctx->natoms, 1)), 256, 0, ctx->stream>>>(
+            // E Y_c and P_c Y_c over the supports, from the bf16 rows of Y_c
+            k_support_reduce3<__nv_bfloat16><<<(unsigned)(s.nch * std::max(ctx->natoms, 1)), 256, 0, ctx->stream>>>(
                 ctx->d_sup_off, ctx->d_sup_node, ctx->enrich ? ctx->d_E32 : ctx->d_Pc32,
-                (ctx->enrich && ctx->nonlocal) ? ctx->d_Pc32 : nullptr, Zcur, ctx->d_minv, N, ldz, s.chunk, s.nch,
+                (ctx->enrich && ctx->nonlocal) ? ctx->d_Pc32 : nullptr, Ycur, nullptr, N, ldb, s.chunk, s.nch,
                 ctx->d_chunk_order, s.part);
             const long long n8 = (long long)ctx->natoms * 8 * N;
             k_support_sum<<<nblk(n8, 256), 256, 0, ctx->stream>>>(ctx->natoms, s.nch, N, s.part,
@@ -1448,47 +1472,61 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
             // W = D (P_c Y_c + P^E Y_e); enriched rows E Y_c + H^E_ee Y_e + P^E^T W
             if (ctx->nonlocal) {
                 k_proj_w<float><<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
-                    ctx->n_proj, ne_, s.Wc, ctx->enrich ? ctx->d_PE : nullptr, Ye, lde, ctx->d_hproj, N, s.W);
+                    ctx->n_proj, ne_, s.Wc, ctx->enrich ? ctx->d_PE : nullptr, Ye, ldb, ctx->d_hproj, N, s.W);
                 k_to_float_strided<<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
-                    ctx->n_proj, N, s.W, W32, lde, W16);
+                    ctx->n_proj, N, s.W, W32, ldb, W16);
                 ctx->launches += 2;
             }
             if (ctx->enrich) {
                 k_enr_raw<float><<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(
-                    ne_, ctx->n_proj, s.Rh, ctx->d_HEee, ctx->nonlocal ? ctx->d_PE : nullptr, s.W, Ye, lde, N,
+                    ne_, ctx->n_proj, s.Rh, ctx->d_HEee, ctx->nonlocal ? ctx->d_PE : nullptr, s.W, Ye, ldb, N,
                     s.Yraw);
                 ctx->launches++;
             }
+            // the FE rows' coupling E^T Y_e + P_c^T W enters the cell products
+            k_pack_yw<<<nblk((long long)(ctx->natoms + 1) * nCB * 64, 256), 256, 0, ctx->stream>>>(
+                ctx->natoms, nCB, N, ldb, ctx->enrich ? Ye16 : nullptr, ctx->nonlocal ? W16 : nullptr, YW);
+            ctx->launches++;
+            EFE_TRY(efe_check_launch(ctx, "coupling"));
+        }
+        {
+            auto *ev = cell_event_pair(ctx);
+            if (ev) cudaEventRecord(ev->first, ctx->stream);
+            EFE_TRY(efe_tc_cells(ctx, Ycur, ldb, N, Ycells, ldb, ctx->d_err, cells16 ? 1 : 0, cpl ? YW : nullptr,
+                                 nCB));
+            if (ev) cudaEventRecord(ev->second, ctx->stream);
         }
         auto *rev = rec_event_pair(ctx);
         if (rev) cudaEventRecord(rev->first, ctx->stream);
-        k_gather_rec_w<<<rb_run, 256, 0, ctx->stream>>>(mh, nruns_x, ldz, Ycells, ldy, cpl ? ctx->d_node_ptr : nullptr,
-                                                        ctx->d_nm_atom, ctx->d_nm_E32, ctx->d_nm_P32,
-                                                        Ye16, W16, lde, ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0,
-                                                        Zcur, Zprev, G, fck + (size_t)(k - 1) * ldz, ak, cf, bk,
-                                                        Znext);
+        if (cells16)
+            k_gather_rec_b<__nv_bfloat16><<<rb_run, 256, 0, ctx->stream>>>(
+                mh, nruns_x, ldb, (const __nv_bfloat16 *)Ycells, ctx->d_minv, Ycur, Yprev, Gb,
+                fck + (size_t)(k - 1) * ldb, ak, cf, bk, Yb[inext]);
+        else
+            k_gather_rec_b<float><<<rb_run, 256, 0, ctx->stream>>>(
+                mh, nruns_x, ldb, (const float *)Ycells, ctx->d_minv, Ycur, Yprev, Gb, fck + (size_t)(k - 1) * ldb,
+                ak, cf, bk, Yb[inext]);
         if (rev) cudaEventRecord(rev->second, ctx->stream);
         ctx->launches++;
-        EFE_TRY(efe_check_launch(ctx, "k_gather_rec_w"));
+        EFE_TRY(efe_check_launch(ctx, "k_gather_rec_b"));
         if (ne_) {
-            k_enr_rec_v<<<nblk((long long)ne_ * ldz, 256), 256, 0, ctx->stream>>>(
-                ne_, N, ldz, s.Yraw, nullptr, Zcur + nn * ldz, Zprev ? Zprev + nn * ldz : nullptr, G + nn * ldz,
-                fck + (size_t)(k - 1) * ldz, ak, cf, bk, Znext + nn * ldz);
+            k_enr_rec_v<<<nblk((long long)ne_ * ldb, 256), 256, 0, ctx->stream>>>(
+                ne_, N, ldb, s.Yraw, nullptr, Zcur, Zprev, Ge, fck + (size_t)(k - 1) * ldb, ak, cf, bk, Ze[inext]);
             ctx->launches++;
         }
-        float *old_prev = Zprev ? Zprev : Zspare;
-        Zprev = Zcur;
-        Zcur = Znext;
-        Znext = old_prev;
+        // rotate: Y_{k-1} becomes Y_{k-2}; the old Y_{k-2} (or the unused third buffer) takes Y_{k+1}
+        const int old_prev = iprev >= 0 ? iprev : 3 - icur - inext;
+        iprev = icur;
+        icur = inext;
+        inext = old_prev;
     }
     // V_out = M~^-1 Z_m + V diag(C_m(lam))
     if (ne_) {
-        k_enr_minv_f<<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(ne_, N, ldz, ctx->d_Mblk_inv,
-                                                                            Zcur + nn * ldz, Ye, lde);
+        k_enr_minv_f<<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(ne_, N, ldb, ctx->d_Mblk_inv, Ze[icur],
+                                                                            Ye, ldb);
         ctx->launches++;
     }
-    k_rows_minv_vout<<<rb_all, 256, 0, ctx->stream>>>(nn, rows, N, ldz, ctx->d_minv, Zcur, Ye, lde, V,
-                                                      dck + (size_t)m * N, Vout);
+    k_vout_b<<<rb_all, 256, 0, ctx->stream>>>(nn, rows, N, ldb, Yb[icur], Ye, V, dck + (size_t)m * N, Vout);
     ctx->launches++;
     EFE_TRY(efe_check_launch(ctx, "filter_tensor"));
     ctx->stats.ms_filter = tm.stop();
@@ -1716,7 +1754,7 @@ void efe_destroy(efe_ctx *ctx) {
                     ctx->d_node_ent, ctx->d_ent_atom,
                     ctx->d_pairs, ctx->d_pair_pos, ctx->d_cell_atom_ptr, ctx->d_cell_atoms, ctx->d_Aee, ctx->d_Kaa,
                     ctx->d_Haa, ctx->d_Mee, ctx->d_Pa, ctx->d_Mblk_inv, ctx->d_Mblk, ctx->d_ws, ctx->d_part,
-                    ctx->d_info, ctx->d_err, ctx->d_solver_ws};
+                    ctx->d_info, ctx->d_err, ctx->d_solver_ws, ctx->d_cx_off, ctx->d_cx_atoms, ctx->d_Ax};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
@@ -1755,10 +1793,6 @@ efe_status efe_setup(const efe_mesh *mesh, const efe_atoms *atoms, const efe_enr
         return fail("bad pseudopotential");
     efe_ctx *ctx = new efe_ctx();
     ctx->stream = (cudaStream_t)stream;
-    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
-        delete ctx;
-        return fail("efe_setup: no current CUDA device");
-    }
     MeshDev &m = ctx->m;
     m.nx = mesh->ncell[0];
     m.ny = mesh->ncell[1];
@@ -1809,7 +1843,7 @@ efe_status efe_setup(const efe_mesh *mesh, const efe_atoms *atoms, const efe_enr
         return st;
     };
     efe_status st;
-    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    if (cudaGetDevice(&ctx->device) != cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
         ctx->err = "invalid CUDA stream or no device";
         return bail(EFE_ERR_CUDA);
     }
@@ -1867,6 +1901,16 @@ efe_status efe_get_dims(const efe_ctx *ctx, efe_dims *d) {
 efe_status efe_get_stats(const efe_ctx *ctx, efe_stats *s) {
     if (!ctx || !s) return EFE_ERR_ARG;
     *s = ctx->stats;
+    return EFE_OK;
+}
+
+efe_status efe_set_cell_storage(efe_ctx *ctx, efe_precision prec) {
+    EFE_CHECK_CTX(ctx);
+    if (prec != EFE_BF16 && prec != EFE_FP32) {
+        ctx->err = "efe_set_cell_storage: EFE_BF16 or EFE_FP32";
+        return EFE_ERR_ARG;
+    }
+    ctx->cells_bf16 = prec == EFE_BF16;
     return EFE_OK;
 }
 

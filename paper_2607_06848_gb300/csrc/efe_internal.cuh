@@ -129,6 +129,14 @@ struct efe_ctx {
     void *d_hostio = nullptr;
     size_t hostio_bytes = 0;
     long long cell_launches = 0;
+    bool cells_bf16 = true;                   // mixed filter: per-cell products stored in bf16 (else FP32)
+    // coupling as extra k-steps of the tensor-core cell products (efe_tc.cu)
+    bool cx_built = false;
+    int *d_cx_off = nullptr;                  // n_cells + 1: first extra k-step of each cell
+    int *d_cx_atoms = nullptr;                // two atom slots per extra k-step (natoms: zero block)
+    void *d_Ax = nullptr;                     // extra A stages, bf16 [k-step][MT][2048]
+    long long cx_steps = 0;
+    int cx_max_slots = 0;                     // largest atom-slot count of a cell
 };
 
 // error helpers
@@ -167,4 +175,6 @@ void efe_scf_free(efe_ctx *ctx);
 efe_status efe_cells_shared(efe_ctx *ctx, const double *K, const double *X, double *Y, int N);
 efe_status efe_xprime_fp64(efe_ctx *ctx, const double *X, double *Xp, int N);
 void efe_sym_eig(int n, const std::vector<double> &A, std::vector<double> &w, std::vector<double> &V);
-efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, float *Ycells, int ldy, int *d_err);
+efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, void *Ycells, int ldy, int *d_err,
+                        int out_bf16 = 0, const void *YW = nullptr, int nCB = 0);
+int efe_tc_columns(const efe_ctx *ctx, int N, int ldb);

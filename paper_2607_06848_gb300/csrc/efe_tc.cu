@@ -21,11 +21,29 @@
 //   D = accumulator, M-tile mt at TMEM columns [mt*Npad, (mt+1)*Npad).
 // The MMAs run k-step-major (all M-tiles of a k-step, then the next k-step),
 // so each plane pair is released as soon as its k-steps are done and the
-// freed shared memory deepens the A ring; the epilogue of a cell overlaps the
-// loads of the next.
-// Per-cell results go to Ycells[cell][row][ldy] (FP32); a gather kernel sums
-// the up-to-8 contributions of each node, so no colouring or atomics are
-// needed and every cell of the mesh runs in one persistent launch.
+// freed shared memory deepens the A ring.  One cell's FP32 accumulators for
+// all columns would fill the SM's tensor memory, so that the next cell's MMAs
+// would wait for the epilogue's drain; instead the columns are split into
+// chunks of at most 256 / MT and two blocks run on each SM (up to 256 TMEM
+// columns and ~111 KB of shared memory each): while one block drains its
+// cell, the other's MMAs and loads proceed.  Blocks with the same blockIdx.x
+// walk the same cells (one column chunk each, blockIdx.y), so a cell's H_e
+// tiles come from DRAM once and from L2 for the other chunks.
+// Coupling (the bf16 filter): the FE rows of H^E Y also hold E^T Y_e + P_c^T W
+// (the FE-enrichment block of H^E and the projector rows).  Each FE node is
+// owned by exactly one cell (the one in which its local indices lie in
+// [0, p)^3), and a cell's owned rows receive these terms as extra k-steps of
+// the same accumulation: A holds, per extra k-step, the coefficients of two
+// atoms (8 columns each: E_f, P_c,f for f = s, px, py, pz; zero for rows the
+// cell does not own), B the rows Y_e(atom) and W(atom) (8 rows per atom,
+// one bulk copy per atom from a table laid out as MN-major core matrices).
+// So the coupling runs on the tensor cores, and the node kernel that sums the
+// cells is a plain streaming pass.
+// Per-cell results go to Ycells[cell][row][ldy] (FP32 or bf16); a gather
+// kernel sums the up-to-8 contributions of each node, so no colouring or
+// atomics are needed and every cell of the mesh runs in one persistent launch.
+// The epilogue stages each warp's 32 rows through shared memory (XOR-swizzled
+// 16-byte units) and writes whole 128-byte row segments.
 #include "efe_internal.cuh"
 
 #include <cuda.h>
@@ -40,16 +58,26 @@ namespace {
 constexpr int TC_THREADS = 256;      // w0 TMA producer, w1 MMA issuer, w2 TMEM owner, w4-7 epilogue
 constexpr int MAX_A_STAGES = 24;     // A ring depth limit (one stage = one k-step of all M-tiles)
 constexpr int B_SLOTS = 2;           // plane-pair ring
-constexpr int SMEM_LIMIT = 232448;   // dynamic shared memory per block (227 KB)
+constexpr int STAGE_BYTES = 2048;    // epilogue staging per warp: 32 rows x 64 B
+constexpr int SMEM_LIMIT = 113664;   // dynamic shared memory per block: two blocks per SM (2 x 111 KB)
+constexpr int TMEM_COLS = 256;       // tensor-memory columns per block (two blocks share the SM's 512)
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz before a wait gives up
 
 struct TcParams {
-    int ncells, nx, ny, p, np1, ne, xpad, Kpad, ksteps, MT, Npad, ncb, col0, ldy;
+    int ncells, nx, ny, p, np1, ne, xpad, Kpad, ksteps, MT, Npad, ncb, ldy;   // column chunk: blockIdx.y
     int plane_rows;                     // (p+1) xpad rows per z-plane
     int kpg;                            // k-steps per plane pair: 2 plane_rows / 16
     int ngroups;                        // plane pairs per cell: ceil((p+1) / 2)
     int a_stages;                       // A ring depth
     int slot_bytes;                     // one B slot: ncb x 2 plane_rows x 16 B
+    int out_bf16;                       // per-cell results stored as bf16 (else FP32)
+    // coupling as extra k-steps (cx_off == nullptr: none)
+    const int *cx_off;                  // ncells + 1: first extra k-step of each cell
+    const int *cx_atoms;                // 2 atom slots per extra k-step (natoms: the zero block)
+    const __nv_bfloat16 *Ax;            // extra A stages [k-step][MT][2048]
+    const __nv_bfloat16 *YW;            // [atom][nCB][8 rows][8 columns]: Y_e (rows 0-3), W (rows 4-7)
+    int nCB;                            // 8-column blocks per atom in YW
+    int x_slot_bytes;                   // shared memory of the extra B slot
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -144,8 +172,17 @@ __device__ __forceinline__ void reg_after_wait(uint32_t r[16]) {
                    "+r"(r[15]));
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    k_cell_mma(const __grid_constant__ CUtensorMap xmap, const __nv_bfloat16 *__restrict__ He16, float *Ycells,
+// 16-byte unit u (0..3) of staged row `row` (rows of 64 B; units XOR-swizzled
+// by bits 1-2 of the row, so that any 8 consecutive rows -- a quarter-warp
+// access -- hit 8 different 16-byte bank groups)
+__device__ __forceinline__ void stage_store(uint32_t base, int row, int u, uint32_t x, uint32_t y, uint32_t z,
+                                            uint32_t w) {
+    const uint32_t a = base + (uint32_t)(row * 64 + ((u ^ ((row >> 1) & 3)) * 16));
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 2)
+    k_cell_mma(const __grid_constant__ CUtensorMap xmap, const __nv_bfloat16 *__restrict__ He16, void *Ycells,
                TcParams P, int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // every TMA destination below is a multiple of 128 B from this base
@@ -154,28 +191,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int stage_bytes = P.MT * 4096;
     unsigned char *sA = smem;
     unsigned char *sB = smem + (size_t)P.a_stages * stage_bytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + (size_t)B_SLOTS * P.slot_bytes);
+    unsigned char *sX = sB + (size_t)B_SLOTS * P.slot_bytes;
+    unsigned char *sStage = sX + P.x_slot_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sStage + 4 * STAGE_BYTES);
     uint64_t *full_a = bars, *empty_a = bars + MAX_A_STAGES;
     uint64_t *full_b = bars + 2 * MAX_A_STAGES, *empty_b = full_b + B_SLOTS;
     uint64_t *acc_full = empty_b + B_SLOTS, *acc_empty = acc_full + 4;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 4);
+    uint64_t *full_x = acc_empty + 4, *empty_x = full_x + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(empty_x + 1);
+    const uint32_t xblk = (uint32_t)P.ncb * 128;      // one atom's 8 rows x Npad columns in sX
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int pair_stride = 2 * P.plane_rows * 16;   // bytes between column blocks in a slot
+    const int col0 = blockIdx.y * P.Npad;             // this block's column chunk
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < P.a_stages; ++i) { mbar_init(&full_a[i], 1); mbar_init(&empty_a[i], 1); }
         for (int i = 0; i < B_SLOTS; ++i) { mbar_init(&full_b[i], 1); mbar_init(&empty_b[i], 1); }
         for (int t = 0; t < 4; ++t) { mbar_init(&acc_full[t], 1); mbar_init(&acc_empty[t], 128); }
+        mbar_init(full_x, 1);
+        mbar_init(empty_x, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // zero both B slots once: rows a lone last plane leaves unwritten meet zero
     // columns of H_e, and must hold finite values
-    for (int i = threadIdx.x; i < B_SLOTS * P.slot_bytes / 4; i += blockDim.x)
+    for (int i = threadIdx.x; i < (B_SLOTS * P.slot_bytes + P.x_slot_bytes) / 4; i += blockDim.x)
         reinterpret_cast<uint32_t *>(sB)[i] = 0u;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (warp == 2) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "n"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
         fence_before();
     }
@@ -190,6 +235,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         bool ok = true;
         uint32_t aused = 0, apar = 0;      // per A slot: issued at least once, parity of its last phase
         uint32_t bused = 0, bpar = 0;      // the same per B slot
+        uint32_t phx = 0, xused = 0, xpar = 0;
         for (int cell = blockIdx.x; cell < P.ncells && ok; cell += gridDim.x) {
             const int cx = cell % P.nx, cy = (cell / P.nx) % P.ny, cz = cell / (P.nx * P.ny);
             const __nv_bfloat16 *Ac = He16 + (size_t)cell * P.ksteps * P.MT * 2048;
@@ -203,7 +249,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int zz = 0; zz < np; ++zz)
                     for (int cb = 0; cb < P.ncb; ++cb)
                         tma_load_4d(slot + (size_t)cb * pair_stride + (size_t)zz * P.plane_rows * 16, &xmap,
-                                    P.col0 + 8 * cb, cx * P.p, cy * P.p, cz * P.p + 2 * g + zz,
+                                    col0 + 8 * cb, cx * P.p, cy * P.p, cz * P.p + 2 * g + zz,
                                     &full_b[sb]);   // {cols, x, y, z}
                 bused |= 1u << sb;
                 bpar = (bpar & ~(1u << sb)) | (phb << sb);
@@ -220,8 +266,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     if (++sa == P.a_stages) { sa = 0; pha ^= 1; }
                 }
             }
+            // the coupling: Y_e / W rows of the cell's atoms, then the extra A stages
+            const int x0 = P.cx_off ? P.cx_off[cell] : 0;
+            const int nxs = P.cx_off ? P.cx_off[cell + 1] - x0 : 0;
+            if (ok && nxs > 0) {
+                if (!mbar_wait(empty_x, phx ^ 1)) { ok = false; break; }
+                mbar_expect_tx(full_x, (uint32_t)(2 * nxs) * xblk);
+                for (int sl = 0; sl < 2 * nxs; ++sl) {
+                    const int atom = P.cx_atoms[2 * x0 + sl];
+                    bulk_load(sX + (size_t)sl * xblk, P.YW + ((size_t)atom * P.nCB + col0 / 8) * 64, xblk, full_x);
+                }
+                xused = 1;
+                xpar = phx;
+                phx ^= 1;
+                for (int j = 0; j < nxs; ++j) {
+                    if (!mbar_wait(&empty_a[sa], pha ^ 1)) { ok = false; break; }
+                    mbar_expect_tx(&full_a[sa], (uint32_t)stage_bytes);
+                    bulk_load(sA + (size_t)sa * stage_bytes, P.Ax + (size_t)(x0 + j) * P.MT * 2048,
+                              (uint32_t)stage_bytes, &full_a[sa]);
+                    aused |= 1u << sa;
+                    apar = (apar & ~(1u << sa)) | (pha << sa);
+                    if (++sa == P.a_stages) { sa = 0; pha ^= 1; }
+                }
+            }
         }
         if (!ok) atomicExch(err, 1);
+        if (xused) mbar_wait(full_x, xpar);
         // drain: every copy this thread issued has landed before the block exits
         for (int i = 0; i < B_SLOTS; ++i)
             if (bused & (1u << i)) mbar_wait(&full_b[i], (bpar >> i) & 1u);
@@ -232,10 +302,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (0u << 15) | (1u << 16) |
                                ((uint32_t)(P.Npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
         int sa = 0, sb = 0;
-        uint32_t pha = 0, phb = 0;
+        uint32_t pha = 0, phb = 0, phx = 0;
         int it = 0;
         bool ok = true;
-        const uint32_t sB_addr = smem_u32(sB), sA_addr = smem_u32(sA);
+        const uint32_t sB_addr = smem_u32(sB), sA_addr = smem_u32(sA), sX_addr = smem_u32(sX);
         for (int cell = blockIdx.x; cell < P.ncells && ok; cell += gridDim.x, ++it) {
             // every M-tile accumulates over the whole cell: all of them must be drained
             for (int mt = 0; mt < P.MT && ok; ++mt)
@@ -263,12 +333,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
             if (!ok) break;
+            const int x0 = P.cx_off ? P.cx_off[cell] : 0;
+            const int nxs = P.cx_off ? P.cx_off[cell + 1] - x0 : 0;
+            if (nxs > 0) {
+                if (!mbar_wait(full_x, phx)) { ok = false; break; }
+                fence_after();
+                for (int j = 0; j < nxs; ++j) {
+                    if (!mbar_wait(&full_a[sa], pha)) { ok = false; break; }
+                    fence_after();
+                    // two atoms (16 K rows): K groups xblk apart, 8-column blocks 128 B apart
+                    const uint64_t bd = smem_desc(sX_addr + (uint32_t)(2 * j) * xblk, xblk, 128);
+                    for (int mt = 0; mt < P.MT; ++mt) {
+                        const uint64_t ad = smem_desc(sA_addr + sa * stage_bytes + mt * 4096, 128, 256);
+                        mma_bf16(tmem + (uint32_t)(mt * P.Npad), ad, bd, idesc, 1u);
+                    }
+                    mma_commit(&empty_a[sa]);
+                    if (++sa == P.a_stages) { sa = 0; pha ^= 1; }
+                }
+                if (!ok) break;
+                mma_commit(empty_x);
+                phx ^= 1;
+            }
             for (int mt = 0; mt < P.MT; ++mt) mma_commit(&acc_full[mt]);
         }
         if (!ok) atomicExch(err, 2);
     } else if (warp >= 4) {
         // ---------------- epilogue ----------------
+        // TMEM -> registers (thread = row) -> shared memory (row of 64 B, its
+        // 16-byte units XOR-swizzled by the row) -> global (4 lanes per row
+        // segment: whole 32-byte sectors, 8 rows per warp store)
         const int q = warp & 3;
+        unsigned char *stg = sStage + q * STAGE_BYTES;
+        const uint32_t stg_addr = smem_u32(stg);
+        const int ew = P.out_bf16 ? 2 : 4;              // bytes per stored element
+        const int cw = 64 / ew;                         // columns per staged chunk
+        const int upu = 16 / ew;                        // columns per 16-byte unit
         int it = 0;
         bool ok = true;
         for (int cell = blockIdx.x; cell < P.ncells && ok; cell += gridDim.x, ++it) {
@@ -277,31 +376,58 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const bool got = mbar_wait(&acc_full[mt], it & 1);
                 if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
                 fence_after();
-                const int row = mt * 128 + q * 32 + lane;
-                float *dst = Ycells + ((size_t)cell * P.ne + row) * P.ldy + P.col0;
+                const int rbase = mt * 128 + q * 32;
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * P.Npad);
-                // up to 64 columns per TMEM round trip: four loads, one wait
-                for (int c = 0; c < P.Npad; c += 64) {
-                    const int ng = min(4, (P.Npad - c) / 16);        // warp-uniform
-                    uint32_t r[4][16];
+                unsigned char *ybase = reinterpret_cast<unsigned char *>(Ycells) +
+                                       (((size_t)cell * P.ne + rbase) * P.ldy + col0) * ew;
+                for (int c0 = 0; rbase < P.ne && c0 < P.Npad; c0 += cw) {
+                    const int nl = min(cw, P.Npad - c0) / 16;  // x16 loads, warp-uniform
+                    const int nu = nl * 16 / upu;                // 16-byte units per row
+                    uint32_t r[2][16];
 #pragma unroll
-                    for (int g = 0; g < 4; ++g)
-                        if (g < ng) tmem_ld16_nw(tbase + (uint32_t)(c + 16 * g), r[g]);
+                    for (int g = 0; g < 2; ++g)
+                        if (g < nl) tmem_ld16_nw(tbase + (uint32_t)(c0 + 16 * g), r[g]);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        if (g >= ng) continue;
+                    for (int g = 0; g < 2; ++g) {
+                        if (g >= nl) continue;
                         reg_after_wait(r[g]);
-                        if (row < P.ne) {
-                            const int cc = c + 16 * g;
+                        if (P.out_bf16) {
+                            // one x16 load = two 16-byte units of 8 bf16
 #pragma unroll
-                            for (int i = 0; i < 16; i += 4)
-                                if (P.col0 + cc + i + 3 < P.ldy)
-                                    *reinterpret_cast<float4 *>(dst + cc + i) =
-                                        make_float4(__uint_as_float(r[g][i]), __uint_as_float(r[g][i + 1]),
-                                                    __uint_as_float(r[g][i + 2]), __uint_as_float(r[g][i + 3]));
+                            for (int h = 0; h < 2; ++h) {
+                                uint32_t w[4];
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) {
+                                    __nv_bfloat162 bb = __floats2bfloat162_rn(__uint_as_float(r[g][8 * h + 2 * i]),
+                                                                              __uint_as_float(r[g][8 * h + 2 * i + 1]));
+                                    w[i] = *reinterpret_cast<uint32_t *>(&bb);
+                                }
+                                stage_store(stg_addr, lane, 2 * g + h, w[0], w[1], w[2], w[3]);
+                            }
+                        } else {
+                            // one x16 load = four 16-byte units of 4 floats
+#pragma unroll
+                            for (int h = 0; h < 4; ++h)
+                                stage_store(stg_addr, lane, 4 * g + h, r[g][4 * h], r[g][4 * h + 1], r[g][4 * h + 2],
+                                            r[g][4 * h + 3]);
                         }
                     }
+                    __syncwarp();
+                    for (int idx = lane; idx < 32 * nu; idx += 32) {
+                        const int row = idx / nu, u = idx - row * nu;
+                        const int col = c0 + u * upu;
+                        if (rbase + row < P.ne && col0 + col < P.ldy) {
+                            uint4 v;
+                            const uint32_t a = stg_addr + (uint32_t)(row * 64 + ((u ^ ((row >> 1) & 3)) * 16));
+                            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                                         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                                         : "r"(a)
+                                         : "memory");
+                            *reinterpret_cast<uint4 *>(ybase + ((size_t)row * P.ldy + col) * ew) = v;
+                        }
+                    }
+                    __syncwarp();
                 }
                 fence_before();
                 mbar_arrive(&acc_empty[mt]);
@@ -312,7 +438,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     if (warp == 2) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TMEM_COLS));
     }
 }
 
@@ -345,6 +471,46 @@ __global__ void k_tile_he16(int ncells, int np1, int xpad, int MT, int ksteps, c
     }
 }
 
+// The coupling's extra A stages of each cell, in the layout of the H_e tiles:
+// stage j of cell c holds atom slots 2j, 2j+1 (columns 8 kg + ki: E_ki for
+// ki < 4, P_c,ki-4 otherwise) at the rows of the interior nodes the cell owns
+// (local indices in [0, p)^3); every other row is zero, so each FE row gets
+// its coupling from exactly one cell.  Values from the node-major tables.
+__global__ void k_tile_coupling(MeshDev m, int MT, const int *__restrict__ cx_off, const int *__restrict__ cx_atoms,
+                                int natoms, const long long *__restrict__ node_ptr, const int *__restrict__ nm_atom,
+                                const float *__restrict__ nmE, const float *__restrict__ nmP, int use_e, int use_p,
+                                __nv_bfloat16 *__restrict__ Ax) {
+    const int c = blockIdx.x;
+    const int x0 = cx_off[c], nxs = cx_off[c + 1] - x0;
+    const int cx = c % m.nx, cy = (c / m.nx) % m.ny, cz = c / (m.nx * m.ny);
+    const long long total = (long long)nxs * MT * 2048;
+    for (long long i = threadIdx.x; i < total; i += blockDim.x) {
+        const int e = (int)(i % 2048);
+        const long long blk = i / 2048;
+        const int mt = (int)(blk % MT), j = (int)(blk / MT);
+        const int core = e / 64, within = e % 64;
+        const int rg = core / 2, kg = core % 2, ri = within / 8, ki = within % 8;
+        const int R = mt * 128 + rg * 8 + ri;
+        const int atom = cx_atoms[2 * (x0 + j) + kg];
+        float v = 0.f;
+        if (R < m.ne && atom < natoms) {
+            const int ax = R % m.np1, ay = (R / m.np1) % m.np1, az = R / (m.np1 * m.np1);
+            const int ix = cx * m.p + ax, iy = cy * m.p + ay, iz = cz * m.p + az;
+            if (ax < m.p && ay < m.p && az < m.p && ix >= 1 && iy >= 1 && iz >= 1 && ix <= m.Gx - 2 &&
+                iy <= m.Gy - 2 && iz <= m.Gz - 2) {
+                const long long n = ((long long)iz * m.Gy + iy) * m.Gx + ix;
+                for (long long q = node_ptr[n]; q < node_ptr[n + 1]; ++q)
+                    if ((nm_atom[q] & kNmAtomMask) == atom) {
+                        if (ki < 4) v = use_e ? nmE[4 * q + ki] : 0.f;
+                        else v = use_p ? nmP[4 * q + ki - 4] : 0.f;
+                        break;
+                    }
+            }
+        }
+        Ax[((size_t)(x0 + j) * MT + mt) * 2048 + e] = __float2bfloat16_rn(v);
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode(efe_ctx *ctx) {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -365,17 +531,21 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode(efe_ctx *ctx) {
 
 // Geometry of the tensor-core cell product for this mesh and N columns.
 struct TcShape {
-    int xpad, Kpad, ksteps, MT, Npad, nchunks, plane_rows, kpg, ngroups, a_stages, slot_bytes;
+    int xpad, Kpad, ksteps, MT, Npad, nchunks, plane_rows, kpg, ngroups, a_stages, slot_bytes, x_slot_bytes;
     size_t smem;
 };
 
-// shared memory: A ring + two B slots + barriers (+ alignment slack) within 227 KB
+constexpr size_t TC_FIXED = (2 * MAX_A_STAGES + 2 * B_SLOTS + 10) * 8 + 64 + 1024;   // barriers, TMEM slot, alignment
+
+// shared memory: A ring + two B slots + the coupling slot + epilogue staging +
+// barriers (+ alignment slack) within 227 KB
 static size_t tc_smem(const TcShape &s) {
-    return (size_t)s.a_stages * s.MT * 4096 + (size_t)B_SLOTS * s.slot_bytes +
-           (2 * MAX_A_STAGES + 2 * B_SLOTS + 8) * 8 + 64 + 1024;
+    return (size_t)s.a_stages * s.MT * 4096 + (size_t)B_SLOTS * s.slot_bytes + s.x_slot_bytes + 4 * STAGE_BYTES +
+           TC_FIXED;
 }
 
-static TcShape tc_shape(const efe_ctx *ctx, int N, int ldb) {
+// x_slots: atom slots of the coupling per cell (0: no coupling)
+static TcShape tc_shape(const efe_ctx *ctx, int N, int ldb, int x_slots = 0) {
     TcShape s{};
     const int ne = ctx->m.ne, np1 = ctx->m.np1;
     s.xpad = (np1 + 7) / 8 * 8;
@@ -386,20 +556,68 @@ static TcShape tc_shape(const efe_ctx *ctx, int N, int ldb) {
     s.kpg = 2 * s.plane_rows / 16;
     s.ngroups = (np1 + 1) / 2;
     const int stage = s.MT * 4096;
-    const size_t fixed = (2 * MAX_A_STAGES + 2 * B_SLOTS + 8) * 8 + 64 + 1024;
-    int maxN = std::min(256, (512 / s.MT) / 16 * 16);
+    const size_t fixed = TC_FIXED + 4 * STAGE_BYTES;
+    int maxN = std::min(256, (TMEM_COLS / s.MT) / 16 * 16);
     // keep at least 4 A stages
-    while (maxN > 16 && fixed + 4 * (size_t)stage + (size_t)B_SLOTS * (maxN / 8) * 2 * s.plane_rows * 16 >
+    while (maxN > 16 && fixed + 4 * (size_t)stage + (size_t)B_SLOTS * (maxN / 8) * 2 * s.plane_rows * 16 +
+                                (size_t)x_slots * (maxN / 8) * 128 >
                             (size_t)SMEM_LIMIT)
         maxN -= 16;
     int Nn = std::min(ldb, ((N + 15) / 16) * 16);
     s.nchunks = (Nn + maxN - 1) / maxN;
     s.Npad = ((Nn + s.nchunks - 1) / s.nchunks + 15) / 16 * 16;
     s.slot_bytes = (s.Npad / 8) * 2 * s.plane_rows * 16;
-    const size_t left = (size_t)SMEM_LIMIT - fixed - (size_t)B_SLOTS * s.slot_bytes;
+    s.x_slot_bytes = x_slots * (s.Npad / 8) * 128;
+    const size_t used = fixed + (size_t)B_SLOTS * s.slot_bytes + s.x_slot_bytes;
+    const size_t left = used < (size_t)SMEM_LIMIT ? (size_t)SMEM_LIMIT - used : 0;
     s.a_stages = (int)std::min<size_t>(MAX_A_STAGES, left / stage);
     s.smem = tc_smem(s);
     return s;
+}
+
+// The static part of the coupling in the cell products: per cell the atoms
+// with a coupling entry (E or P_c; all support entries) at an interior node
+// the cell owns, sorted and padded to an even count with the zero block
+// (index natoms), two per extra k-step.
+static efe_status tc_coupling_structure(efe_ctx *ctx, int MT) {
+    if (ctx->cx_built) return EFE_OK;
+    const MeshDev &m = ctx->m;
+    const long long nn = ctx->n_nodes, ns = ctx->sup_total;
+    std::vector<long long> np(nn + 1);
+    std::vector<int> na((size_t)std::max<long long>(ns, 1));
+    EFE_CUDA(ctx, cudaMemcpy(np.data(), ctx->d_node_ptr, sizeof(long long) * (nn + 1), cudaMemcpyDeviceToHost));
+    if (ns > 0) EFE_CUDA(ctx, cudaMemcpy(na.data(), ctx->d_nm_atom, sizeof(int) * ns, cudaMemcpyDeviceToHost));
+    const int ncells = m.nx * m.ny * m.nz;
+    std::vector<int> off(ncells + 1, 0), atoms, list;
+    int maxs = 0;
+    for (int c = 0; c < ncells; ++c) {
+        const int cx = c % m.nx, cy = (c / m.nx) % m.ny, cz = c / (m.nx * m.ny);
+        list.clear();
+        for (int az = 0; az < m.p; ++az)
+            for (int ay = 0; ay < m.p; ++ay)
+                for (int ax = 0; ax < m.p; ++ax) {
+                    const int ix = cx * m.p + ax, iy = cy * m.p + ay, iz = cz * m.p + az;
+                    if (ix < 1 || iy < 1 || iz < 1 || ix > m.Gx - 2 || iy > m.Gy - 2 || iz > m.Gz - 2) continue;
+                    const long long n = ((long long)iz * m.Gy + iy) * m.Gx + ix;
+                    for (long long e = np[n]; e < np[n + 1]; ++e) list.push_back(na[e] & kNmAtomMask);
+                }
+        std::sort(list.begin(), list.end());
+        list.erase(std::unique(list.begin(), list.end()), list.end());
+        if (list.size() & 1) list.push_back(ctx->natoms);
+        off[c + 1] = off[c] + (int)(list.size() / 2);
+        atoms.insert(atoms.end(), list.begin(), list.end());
+        maxs = std::max(maxs, (int)list.size());
+    }
+    if (atoms.empty()) atoms.assign(2, ctx->natoms);
+    EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_cx_off, sizeof(int) * (ncells + 1)));
+    EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_cx_atoms, sizeof(int) * atoms.size()));
+    EFE_CUDA(ctx, cudaMemcpy(ctx->d_cx_off, off.data(), sizeof(int) * (ncells + 1), cudaMemcpyHostToDevice));
+    EFE_CUDA(ctx, cudaMemcpy(ctx->d_cx_atoms, atoms.data(), sizeof(int) * atoms.size(), cudaMemcpyHostToDevice));
+    ctx->cx_steps = off[ncells];
+    EFE_TRY(efe_alloc(ctx, &ctx->d_Ax, sizeof(__nv_bfloat16) * (size_t)std::max(ctx->cx_steps, 1LL) * MT * 2048));
+    ctx->cx_max_slots = maxs;
+    ctx->cx_built = true;
+    return EFE_OK;
 }
 
 efe_status efe_tc_prepare(efe_ctx *ctx) {
@@ -421,12 +639,31 @@ efe_status efe_tc_prepare(efe_ctx *ctx) {
                                                reinterpret_cast<__nv_bfloat16 *>(ctx->d_He16));
     ctx->launches++;
     EFE_TRY(efe_check_launch(ctx, "k_tile_he16"));
+    if ((ctx->enrich || ctx->nonlocal) && ctx->natoms > 0 && ctx->d_node_ptr && ctx->d_nm_atom) {
+        EFE_TRY(tc_coupling_structure(ctx, MT));
+        k_tile_coupling<<<(unsigned)ncells, 256, 0, ctx->stream>>>(
+            m, MT, ctx->d_cx_off, ctx->d_cx_atoms, ctx->natoms, ctx->d_node_ptr, ctx->d_nm_atom, ctx->d_nm_E32,
+            ctx->d_nm_P32, ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0, reinterpret_cast<__nv_bfloat16 *>(ctx->d_Ax));
+        ctx->launches++;
+        EFE_TRY(efe_check_launch(ctx, "k_tile_coupling"));
+    }
     ctx->he16_valid = true;
     return EFE_OK;
 }
 
-// Ycells[cell][row][ldy] = H_e X'_e for all cells; X'_bf16: n_nodes x ldb.
-efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, float *Ycells, int ldy, int *d_err) {
+// Columns of one row of the coupling table YW that the cell products may read
+// for N columns of row stride ldb (all chunks): nchunks x Npad.
+int efe_tc_columns(const efe_ctx *ctx, int N, int ldb) {
+    const TcShape sh = tc_shape(ctx, N, ldb, ctx->cx_built ? ctx->cx_max_slots : 0);
+    return sh.nchunks * sh.Npad;
+}
+
+// Ycells[cell][row][ldy] = H_e X'_e for all cells (FP32, or bf16 when out_bf16);
+// X'_bf16: n_nodes x ldb.  With YW (the Y_e / W table, [natoms + 1][nCB][8][8]
+// bf16, nCB = efe_tc_columns / 8, the last atom block zero) the owned FE rows
+// of each cell also receive E^T Y_e + P_c^T W.
+efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, void *Ycells, int ldy, int *d_err,
+                        int out_bf16, const void *YW, int nCB) {
     const MeshDev &m = ctx->m;
     if (!ctx->he16_valid) EFE_TRY(efe_tc_prepare(ctx));
     PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode(ctx);
@@ -434,7 +671,8 @@ efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, float
     alignas(64) CUtensorMap map;
     cuuint64_t gdim[4] = {(cuuint64_t)ldb, (cuuint64_t)m.Gx, (cuuint64_t)m.Gy, (cuuint64_t)m.Gz};
     cuuint64_t gstr[3] = {(cuuint64_t)ldb * 2, (cuuint64_t)ldb * 2 * m.Gx, (cuuint64_t)ldb * 2 * m.Gx * m.Gy};
-    TcShape sh = tc_shape(ctx, N, ldb);
+    const bool cpl = YW && ctx->cx_built && ctx->cx_steps > 0;
+    TcShape sh = tc_shape(ctx, N, ldb, cpl ? ctx->cx_max_slots : 0);
     cuuint32_t box[4] = {8, (cuuint32_t)sh.xpad, (cuuint32_t)m.np1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult cr = encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(Xp_bf16), gdim, gstr, box,
@@ -448,39 +686,49 @@ efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, float
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int ncells = m.nx * m.ny * m.nz;
-    for (int ch = 0; ch < sh.nchunks; ++ch) {
-        TcParams P{};
-        P.ncells = ncells;
-        P.nx = m.nx;
-        P.ny = m.ny;
-        P.p = m.p;
-        P.np1 = m.np1;
-        P.ne = m.ne;
-        P.xpad = sh.xpad;
-        P.Kpad = sh.Kpad;
-        P.ksteps = sh.ksteps;
-        P.MT = sh.MT;
-        P.Npad = sh.Npad;
-        P.ncb = sh.Npad / 8;
-        P.col0 = ch * sh.Npad;
-        P.ldy = ldy;
-        P.plane_rows = sh.plane_rows;
-        P.kpg = sh.kpg;
-        P.ngroups = sh.ngroups;
-        P.a_stages = sh.a_stages;
-        P.slot_bytes = sh.slot_bytes;
-        if (sh.a_stages < 4 || sh.smem > (size_t)SMEM_LIMIT) {
-            ctx->err = "tensor-core cell product: shared-memory plan does not fit";
-            return EFE_ERR_ARG;
-        }
-        const size_t shm = sh.smem;
-        EFE_CUDA(ctx, cudaFuncSetAttribute(k_cell_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        const int grid = std::min(nsm > 0 ? nsm : 148, ncells);
-        k_cell_mma<<<grid, TC_THREADS, shm, ctx->stream>>>(map, reinterpret_cast<const __nv_bfloat16 *>(ctx->d_He16),
-                                                          Ycells, P, d_err);
-        ctx->launches++;
-        ctx->cell_launches++;
-        EFE_TRY(efe_check_launch(ctx, "k_cell_mma"));
+    TcParams P{};
+    P.ncells = ncells;
+    P.nx = m.nx;
+    P.ny = m.ny;
+    P.p = m.p;
+    P.np1 = m.np1;
+    P.ne = m.ne;
+    P.xpad = sh.xpad;
+    P.Kpad = sh.Kpad;
+    P.ksteps = sh.ksteps;
+    P.MT = sh.MT;
+    P.Npad = sh.Npad;
+    P.ncb = sh.Npad / 8;
+    P.ldy = ldy;
+    P.plane_rows = sh.plane_rows;
+    P.kpg = sh.kpg;
+    P.ngroups = sh.ngroups;
+    P.a_stages = sh.a_stages;
+    P.slot_bytes = sh.slot_bytes;
+    P.out_bf16 = out_bf16;
+    P.cx_off = cpl ? ctx->d_cx_off : nullptr;
+    P.cx_atoms = cpl ? ctx->d_cx_atoms : nullptr;
+    P.Ax = reinterpret_cast<const __nv_bfloat16 *>(ctx->d_Ax);
+    P.YW = reinterpret_cast<const __nv_bfloat16 *>(YW);
+    P.nCB = nCB;
+    P.x_slot_bytes = sh.x_slot_bytes;
+    if (cpl && sh.nchunks * P.ncb > nCB) {
+        ctx->err = "tensor-core cell product: coupling table narrower than the column chunks";
+        return EFE_ERR_ARG;
     }
+    if (sh.a_stages < 4 || sh.smem > (size_t)SMEM_LIMIT || sh.MT * sh.Npad > TMEM_COLS) {
+        ctx->err = "tensor-core cell product: shared- or tensor-memory plan does not fit";
+        return EFE_ERR_ARG;
+    }
+    const size_t shm = sh.smem;
+    EFE_CUDA(ctx, cudaFuncSetAttribute(k_cell_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    // two blocks per SM; blocks (x, y) for all y walk the same cells (column chunk y)
+    const int sms = nsm > 0 ? nsm : 148;
+    const int gx = std::max(1, std::min(ncells, (2 * sms) / sh.nchunks));
+    k_cell_mma<<<dim3(gx, sh.nchunks), TC_THREADS, shm, ctx->stream>>>(
+        map, reinterpret_cast<const __nv_bfloat16 *>(ctx->d_He16), Ycells, P, d_err);
+    ctx->launches++;
+    ctx->cell_launches++;
+    EFE_TRY(efe_check_launch(ctx, "k_cell_mma"));
     return EFE_OK;
 }

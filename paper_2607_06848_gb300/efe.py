@@ -90,6 +90,7 @@ SIGNATURES = {
     "efe_apply_minv": [_P, _P, _P, _I],
     "efe_lanczos": [_P, _P, _I, _D],
     "efe_filter": [_P, _P, _P, _P, _I, _I, _D, _I, _P],
+    "efe_set_cell_storage": [_P, _I],
     "efe_rayleigh_ritz": [_P, _P, _P, _I, _D, _D],
     "efe_chfsi": [_P, _P, _P, _I, _I, _D, _P, _I, ctypes.c_double, _I, _I, _D, _D, ctypes.POINTER(_I)],
     "efe_filter_host": [_P, _D, _D, _D, _I, _I, _D, _I, _D],
@@ -240,6 +241,9 @@ class EFE:
         out = (ctypes.c_double * 3)()
         self._check(self.lib.efe_lanczos(self.ctx, _ptr(u0), int(k), out))
         return tuple(out)
+
+    def efe_set_cell_storage(self, prec):
+        self._check(self.lib.efe_set_cell_storage(self.ctx, int(prec)))
 
     def efe_filter(self, V, HV, lam, m, bounds, Vout, prec=EFE_FP64):
         b = (ctypes.c_double * 3)(*[float(x) for x in bounds])

@@ -5,11 +5,17 @@
   error would show as O(1)), and the multipass residual ChFSI in bf16
   converging to the FP64 eigenvalues (the residual form tolerates the inexact
   products because their error scales with the residual).
+* The filter's own H^E product (the block form E, H^E_ee, P^E with bf16
+  cell operands and bf16 storage of Y = M~^-1 Z): a filter of degree 2 applies
+  it exactly once, so its output against the oracle's degree-2 filter is an
+  apply test of that path, at N = 13 and at N = 200 (two column chunks).
 * Full size, in the configuration the benchmark times (64-atom cluster,
   24^3 cells of degree 6, 154 vectors): bf16 and FP32 products against FP64,
-  and sampled FP64 rows checked one by one against the oracle's cell
-  matrices for nodes whose whole neighbourhood lies outside every atom
-  support (there the row is a plain sum over the <= 8 cells of the node).
+  sampled FP64 rows checked one by one against the oracle's cell matrices for
+  nodes whose whole neighbourhood lies outside every atom support (there the
+  row is a plain sum over the <= 8 cells of the node), and the bf16 filter
+  against the FP64 filter (itself checked against the oracle on the small
+  meshes) from Ritz vectors with a small residual, both cell-product storages.
 """
 import numpy as np
 import pytest
@@ -242,11 +248,12 @@ def test_cluster64_sampled_rows_against_oracle():
         assert np.max(np.abs(Yg16[node] - row)) < 1e-2 * max(scale, 1.0), node
 
 
-def test_cluster64_filter_bf16_vs_fp32():
+def test_cluster64_filter_bf16_vs_fp64():
     # the benchmark's configuration: 64 atoms, 24^3 cells of degree 6, 154
-    # vectors, degree 30; the bf16 filter against the FP32 one (whose parity
-    # with the oracle is tested on the small meshes) from the Ritz vectors of
-    # a random block
+    # vectors, degree 30.  Ritz vectors with a small residual come from bf16
+    # multipass ChFSI; then one FP64 filter pass and one bf16 pass from the same
+    # vectors.  The bf16 error acts on Z ~ G (the residual): bounded by a
+    # multiple of u * max residual, u = 2^-8
     g, w, v = _cluster64()
     rows, N, m = g.dims["n_rows"], w["nstates"], w["cheb_degree"]
     gen = torch.Generator(device="cuda")
@@ -254,13 +261,67 @@ def test_cluster64_filter_bf16_vs_fp32():
     X = torch.randn((rows, N), generator=gen, dtype=torch.float64, device="cuda")
     u0 = torch.randn((rows, 1), generator=gen, dtype=torch.float64, device="cuda")
     HX = torch.empty_like(X)
-    eig, _ = g.efe_rayleigh_ritz(X, HX)
+    eig, res, passes, _ = g.efe_chfsi(X, m, u0=u0, max_pass=12, tol=1e-12, nconv=128, prec=2, HX=HX)
     b = g.efe_lanczos(u0, 10)[2]
     lam = torch.tensor(eig, device="cuda")
-    out32, out16 = torch.empty_like(X), torch.empty_like(X)
-    g.efe_filter(X, HX, lam, m, (eig[0], eig[-1], b), out32, prec=1)
-    g.efe_filter(X, HX, lam, m, (eig[0], eig[-1], b), out16, prec=2)
-    assert bool(torch.isfinite(out16).all())
-    rel = float((out16 - out32).abs().max() / out32.abs().max())
-    # one bf16 rounding of the cell operand per step, errors adding over m steps
-    assert rel < m * 2.0 ** -8, rel
+    bounds = (eig[0], eig[-1], b)
+    out64 = torch.empty_like(X)
+    g.efe_filter(X, HX, lam, m, bounds, out64, prec=0)
+    resid = float(np.max(res))
+    assert resid < 0.1, resid
+    rels = {}
+    for storage in (2, 1):                    # bf16 (default), FP32 cell products
+        g.efe_set_cell_storage(storage)
+        out16 = torch.empty_like(X)
+        g.efe_filter(X, HX, lam, m, bounds, out16, prec=2)
+        assert bool(torch.isfinite(out16).all())
+        rels[storage] = float((out16 - out64).abs().max() / out64.abs().max())
+    g.efe_set_cell_storage(2)
+    bound = 8 * 2.0 ** -8 * resid
+    assert max(rels.values()) < bound, (rels, resid, bound)
+
+
+@pytest.mark.parametrize("name", ["dimer", "ragged", "single_atom", "cfe_only", "nonlocal_only", "p6_cfe",
+                                  "p6_enriched", "p5_enriched"])
+@pytest.mark.parametrize("N", [13, 200])
+def test_filter_degree2_block_form_apply(name, N):
+    # degree 2: Z_2 = a (H^E M~^-1 Z_1 - c Z_1) + a G C_1(lam), Z_1 = (s1/e) G, so
+    # the output holds exactly one product with H^E in the filter's block form
+    # (bf16 operand Y_1 = M~^-1 Z_1, FP32 sums); from random vectors its relative
+    # error is that of one bf16 product, O(2^-8).  N = 200 runs the cell
+    # products in two column chunks (three M-tiles hold 160 columns).
+    o, g = TP._systems(name)
+    X = TP._rand(o, N, 900 + N)
+    lam, V, HV = OC.rayleigh_ritz(o, X)
+    b = OC.lanczos_bounds(o, TP._rand(o, 1, 901))[2]
+    a0, a = float(lam[0]), float(lam[-1])
+    ref = OC.residual_filter(o, V, lam, 2, a, b, a0, HV=HV)
+    Vd = torch.tensor(V, device="cuda")
+    out = torch.empty_like(Vd)
+    g.efe_filter(Vd, torch.tensor(HV, device="cuda"), torch.tensor(lam, device="cuda"), 2, (a0, a, b), out,
+                 prec=2)
+    rel = TP._rel(out.cpu().numpy(), ref)
+    assert rel < 1e-2, rel
+
+
+def test_filter_pass_bf16_two_chunks_p6():
+    # 200 vectors (two column chunks of the cell products) on the degree-6 mesh
+    # with a nearly redundant enrichment: Ritz vectors from the FP64 GPU
+    # solver (itself checked against the oracle), then one bf16 pass against
+    # the oracle's FP64 pass; error bounded by u * max residual
+    o, g = TP._systems("p6_enriched")
+    N, m = 200, 12
+    X = torch.tensor(TP._rand(o, N, 911), device="cuda")
+    u0 = torch.tensor(TP._rand(o, 1, 912), device="cuda")
+    HX = torch.empty_like(X)
+    eig, res, _, _ = g.efe_chfsi(X, m, u0=u0, max_pass=4, tol=1e-12, nconv=N, HX=HX)
+    V = X.cpu().numpy()
+    lam, HV = np.array(eig), HX.cpu().numpy()
+    b = g.efe_lanczos(u0, 10)[2]
+    a0, a = float(lam[0]), float(lam[-1])
+    ref = OC.residual_filter(o, V, lam, m, a, b, a0, HV=HV)
+    out = torch.empty_like(X)
+    g.efe_filter(X, HX, torch.tensor(lam, device="cuda"), m, (a0, a, b), out, prec=2)
+    resid = float(np.max(res))
+    rel = TP._rel(out.cpu().numpy(), ref)
+    assert rel < 4 * 2.0 ** -8 * resid, (rel, resid)
