@@ -207,6 +207,27 @@ __global__ void k_support_sum(int natoms, int nch, int N, const double *part, do
     else if (outB) outB[(long long)(4 * I + r - 4) * N + j] = s;
 }
 
+// E Y_c per atom from the padding-row partials of the cell products:
+// Rh[4I + f][j] = sum over the atom's (cell, atom) pairs q of Epart[4q + f][j].
+// Block = (atom, f, 32 columns); 8 lanes per column take every 8th pair,
+// then a fixed-order sum over the lanes (deterministic).
+__global__ void __launch_bounds__(256) k_epart_sum(int N, int ld, const int *pair_off, const int *pairs,
+                                                   const float *Epart, double *Rh) {
+    __shared__ double red[8][32];
+    const int I = blockIdx.z, f = blockIdx.y, j = blockIdx.x * 32 + (threadIdx.x & 31), pl = threadIdx.x >> 5;
+    double acc = 0.0;
+    if (j < N)
+        for (int q = pair_off[I] + pl; q < pair_off[I + 1]; q += 8)
+            acc += (double)Epart[((size_t)pairs[q] * 4 + f) * ld + j];
+    red[pl][threadIdx.x & 31] = acc;
+    __syncthreads();
+    if (pl == 0 && j < N) {
+        const int t = threadIdx.x & 31;
+        Rh[(size_t)(4 * I + f) * N + j] = ((red[0][t] + red[1][t]) + (red[2][t] + red[3][t])) +
+                                          ((red[4][t] + red[5][t]) + (red[6][t] + red[7][t]));
+    }
+}
+
 // W = D (Wc + Pa X_e)  (nonlocal strengths applied)
 template <typename T>
 __global__ void k_proj_w(int n_proj, int n_enr, const double *Wc, const double *Pa, const T *Xe, int ld,
@@ -231,6 +252,42 @@ __global__ void k_enr_raw(int n_enr, int n_proj, const double *Rhac, const doubl
     for (int k2 = 0; k2 < n_enr; ++k2) s += Haa[(long long)k * n_enr + k2] * (double)Xe[(long long)k2 * ld + j];
     if (Pa)
         for (int p = 0; p < n_proj; ++p) s += Pa[(long long)p * n_enr + k] * W[(long long)p * N + j];
+    Ye[idx] = s;
+}
+
+// The same two products restricted to the nonzero atom blocks: nb_ptr/nb list,
+// per atom I, the atoms J whose blocks (I, J) of H^E_ee or of P^E (either
+// orientation) are not all zero (supports that overlap); exact zeros skipped.
+template <typename T>
+__global__ void k_proj_w_sp(int n_proj, int n_enr, const double *Wc, const double *Pa, const T *Xe, int ld,
+                            const double *D, int N, const int *nb_ptr, const int *nb, double *W) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)n_proj * N) return;
+    const int p = (int)(idx / N), j = (int)(idx % N), I = p / 4;
+    double s = Wc[idx];
+    if (Pa)
+        for (int q = nb_ptr[I]; q < nb_ptr[I + 1]; ++q) {
+            const int k0 = 4 * nb[q];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) s += Pa[(long long)p * n_enr + k0 + g] * (double)Xe[(long long)(k0 + g) * ld + j];
+        }
+    W[idx] = D[p] * s;
+}
+template <typename T>
+__global__ void k_enr_raw_sp(int n_enr, const double *Rhac, const double *Haa, const double *Pa, const double *W,
+                             const T *Xe, int ld, int N, const int *nb_ptr, const int *nb, double *Ye) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)n_enr * N) return;
+    const int k = (int)(idx / N), j = (int)(idx % N), I = k / 4;
+    double s = Rhac[idx];
+    for (int q = nb_ptr[I]; q < nb_ptr[I + 1]; ++q) {
+        const int k0 = 4 * nb[q];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            s += Haa[(long long)k * n_enr + k0 + g] * (double)Xe[(long long)(k0 + g) * ld + j];
+            if (Pa) s += Pa[(long long)(k0 + g) * n_enr + k] * W[(long long)(k0 + g) * N + j];
+        }
+    }
     Ye[idx] = s;
 }
 
@@ -1027,19 +1084,20 @@ efe_status hx_scratch(efe_ctx *ctx, int N, HxScratch &s) {
 
 // Launch order of the support reductions: every (atom, chunk) pair, sorted by
 // the chunk's first support node (chunks past an atom's list keep their slot:
-// their blocks write the zero partials the sum reads).
-efe_status chunk_order(efe_ctx *ctx, int chunk, int nch) {
-    if (ctx->d_chunk_order && ctx->chunk_order_nch == nch) return EFE_OK;
+// their blocks write the zero partials the sum reads).  off/d_nodes: the
+// per-atom lists (all support entries, or those with a projector row).
+efe_status build_chunk_order(efe_ctx *ctx, const std::vector<long long> &off, const int *d_nodes, int chunk,
+                             int nch, int2 **out) {
     const int na = std::max(ctx->natoms, 1);
-    std::vector<int> first(ctx->sup_total);
-    if (ctx->sup_total > 0)
-        EFE_CUDA(ctx, cudaMemcpy(first.data(), ctx->d_sup_node, sizeof(int) * ctx->sup_total, cudaMemcpyDeviceToHost));
+    const long long total = off.empty() ? 0 : off.back();
+    std::vector<int> first((size_t)std::max(total, 1LL));
+    if (total > 0) EFE_CUDA(ctx, cudaMemcpy(first.data(), d_nodes, sizeof(int) * total, cudaMemcpyDeviceToHost));
     std::vector<std::pair<long long, int2>> key;
     key.reserve((size_t)na * nch);
     for (int I = 0; I < ctx->natoms; ++I)
         for (int c = 0; c < nch; ++c) {
-            const long long g = ctx->sup_off[I] + (long long)c * chunk;
-            const long long k = g < ctx->sup_off[I + 1] ? (long long)first[g] : (1LL << 62);
+            const long long g = off[I] + (long long)c * chunk;
+            const long long k = g < off[I + 1] ? (long long)first[g] : (1LL << 62);
             key.push_back({k, make_int2(I, c)});
         }
     std::stable_sort(key.begin(), key.end(),
@@ -1048,12 +1106,63 @@ efe_status chunk_order(efe_ctx *ctx, int chunk, int nch) {
                      });
     std::vector<int2> ord(key.size());
     for (size_t i = 0; i < key.size(); ++i) ord[i] = key[i].second;
-    if (ctx->d_chunk_order) cudaFree(ctx->d_chunk_order);
-    ctx->d_chunk_order = nullptr;
-    EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_chunk_order, sizeof(int2) * std::max<size_t>(ord.size(), 1)));
-    if (!ord.empty())
-        EFE_CUDA(ctx, cudaMemcpy(ctx->d_chunk_order, ord.data(), sizeof(int2) * ord.size(), cudaMemcpyHostToDevice));
+    if (*out) cudaFree(*out);
+    *out = nullptr;
+    EFE_TRY(efe_alloc(ctx, (void **)out, sizeof(int2) * std::max<size_t>(ord.size(), 1)));
+    if (!ord.empty()) EFE_CUDA(ctx, cudaMemcpy(*out, ord.data(), sizeof(int2) * ord.size(), cudaMemcpyHostToDevice));
+    return EFE_OK;
+}
+
+efe_status chunk_order(efe_ctx *ctx, int chunk, int nch) {
+    if (ctx->d_chunk_order && ctx->chunk_order_nch == nch) return EFE_OK;
+    EFE_TRY(build_chunk_order(ctx, ctx->sup_off, ctx->d_sup_node, chunk, nch, &ctx->d_chunk_order));
     ctx->chunk_order_nch = nch;
+    return EFE_OK;
+}
+
+// The support entries with a nonzero projector row (P_c vanishes outside the
+// projector ball, while the supports also cover the enrichment's one-cell
+// dilation), per atom in node order, with their P_c rows; built once.
+efe_status p_support_lists(efe_ctx *ctx, int chunk, int *nch) {
+    if (!ctx->d_psup_off) {
+        const long long S = ctx->sup_total;
+        std::vector<int> node((size_t)std::max(S, 1LL));
+        std::vector<float> pc((size_t)std::max(4 * S, 4LL));
+        if (S > 0) {
+            EFE_CUDA(ctx, cudaMemcpy(node.data(), ctx->d_sup_node, sizeof(int) * S, cudaMemcpyDeviceToHost));
+            EFE_CUDA(ctx, cudaMemcpy(pc.data(), ctx->d_Pc32, sizeof(float) * 4 * S, cudaMemcpyDeviceToHost));
+        }
+        std::vector<long long> off(ctx->natoms + 1, 0);
+        std::vector<int> pn;
+        std::vector<float> pv;
+        for (int I = 0; I < ctx->natoms; ++I) {
+            for (long long g = ctx->sup_off[I]; g < ctx->sup_off[I + 1]; ++g) {
+                const float *q = &pc[4 * g];
+                if (q[0] == 0.f && q[1] == 0.f && q[2] == 0.f && q[3] == 0.f) continue;
+                pn.push_back(node[g]);
+                pv.insert(pv.end(), q, q + 4);
+            }
+            off[I + 1] = (long long)pn.size();
+        }
+        if (pn.empty()) {
+            pn.push_back(0);
+            pv.assign(4, 0.f);
+        }
+        ctx->psup_off = off;
+        EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_psup_off, sizeof(long long) * off.size()));
+        EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_psup_node, sizeof(int) * pn.size()));
+        EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_psup_coef, sizeof(float) * pv.size()));
+        EFE_CUDA(ctx, cudaMemcpy(ctx->d_psup_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice));
+        EFE_CUDA(ctx, cudaMemcpy(ctx->d_psup_node, pn.data(), sizeof(int) * pn.size(), cudaMemcpyHostToDevice));
+        EFE_CUDA(ctx, cudaMemcpy(ctx->d_psup_coef, pv.data(), sizeof(float) * pv.size(), cudaMemcpyHostToDevice));
+    }
+    long long maxs = 0;
+    for (int I = 0; I < ctx->natoms; ++I) maxs = std::max(maxs, ctx->psup_off[I + 1] - ctx->psup_off[I]);
+    *nch = (int)std::max<long long>(1, (maxs + chunk - 1) / chunk);
+    if (!ctx->d_pchunk_order || ctx->pchunk_nch != *nch) {
+        EFE_TRY(build_chunk_order(ctx, ctx->psup_off, ctx->d_psup_node, chunk, *nch, &ctx->d_pchunk_order));
+        ctx->pchunk_nch = *nch;
+    }
     return EFE_OK;
 }
 
@@ -1391,9 +1500,12 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     // the coupling table read by the cell products: every column chunk they may read
     const int nCB = efe_tc_columns(ctx, N, ldb) / 8;
     const size_t nyw = cpl ? (size_t)(ctx->natoms + 1) * nCB * 64 : 64;
+    // E Y_c from the padding rows of the cell products: 4 rows per atom slot
+    const bool epad = cpl && ctx->epad && ctx->cx_built;
+    const size_t nep = epad ? (size_t)ctx->ca_pairs * 4 * ldb : 64;
     size_t need = 32768 + sizeof(double) * ((size_t)std::max(ne_, 1) * N + (size_t)(m + 2) * N) +
                   sizeof(float) * ckf.size() +
-                  2 * 4 * nb + sizeof(float) * (5 * neb + npb) + 2 * (neb + npb + nyw) +
+                  2 * 4 * nb + sizeof(float) * (5 * neb + npb + nep) + 2 * (neb + npb + nyw) +
                   (cells16 ? 2 : 4) * ycells;
     EFE_TRY(efe_workspace(ctx, need));
     Carver cv{(char *)ctx->d_ws, ctx->ws_bytes};
@@ -1411,6 +1523,7 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     __nv_bfloat16 *Ye16 = cv.take<__nv_bfloat16>(neb);
     __nv_bfloat16 *W16 = cv.take<__nv_bfloat16>(npb);
     __nv_bfloat16 *YW = cv.take<__nv_bfloat16>(nyw);
+    float *Epart = cv.take<float>(nep);
     void *Ycells = cells16 ? (void *)cv.take<__nv_bfloat16>(ycells) : (void *)cv.take<float>(ycells);
     EFE_CUDA(ctx, cudaMemcpyAsync(dck, ck.data(), sizeof(double) * ck.size(), cudaMemcpyHostToDevice, ctx->stream));
     EFE_CUDA(ctx, cudaMemcpyAsync(fck, ckf.data(), sizeof(float) * ckf.size(), cudaMemcpyHostToDevice, ctx->stream));
@@ -1423,9 +1536,14 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     EFE_CUDA(ctx, cudaMemsetAsync(Ye16, 0, 2 * neb, ctx->stream));
     EFE_CUDA(ctx, cudaMemsetAsync(W16, 0, 2 * npb, ctx->stream));
     HxScratch s{};
+    int pnch = 0;
     if (cpl) {
         EFE_TRY(hx_scratch(ctx, N, s));
-        EFE_TRY(chunk_order(ctx, s.chunk, s.nch));
+        if (epad) {
+            if (ctx->nonlocal) EFE_TRY(p_support_lists(ctx, s.chunk, &pnch));
+        } else {
+            EFE_TRY(chunk_order(ctx, s.chunk, s.nch));
+        }
     }
     const unsigned rb_all = (unsigned)((rows + 7) / 8);
     const int nruns_x = (mh.Gx + kRun - 1) / kRun;                   // runs of kRun nodes along x
@@ -1459,29 +1577,40 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
             ctx->launches++;
         }
         if (cpl) {
-            // E Y_c and P_c Y_c over the supports, from the bf16 rows of Y_c
-            k_support_reduce3<__nv_bfloat16><<<(unsigned)(s.nch * std::max(ctx->natoms, 1)), 256, 0, ctx->stream>>>(
-                ctx->d_sup_off, ctx->d_sup_node, ctx->enrich ? ctx->d_E32 : ctx->d_Pc32,
-                (ctx->enrich && ctx->nonlocal) ? ctx->d_Pc32 : nullptr, Ycur, nullptr, N, ldb, s.chunk, s.nch,
-                ctx->d_chunk_order, s.part);
-            const long long n8 = (long long)ctx->natoms * 8 * N;
-            k_support_sum<<<nblk(n8, 256), 256, 0, ctx->stream>>>(ctx->natoms, s.nch, N, s.part,
-                                                                  ctx->enrich ? s.Rh : s.Wc,
-                                                                  (ctx->enrich && ctx->nonlocal) ? s.Wc : nullptr);
-            ctx->launches += 2;
-            // W = D (P_c Y_c + P^E Y_e); enriched rows E Y_c + H^E_ee Y_e + P^E^T W
+            if (epad) {
+                // P_c Y_c over the projector entries (W is needed by these cell products);
+                // E Y_c comes out of their padding rows
+                if (ctx->nonlocal) {
+                    k_support_reduce3<__nv_bfloat16><<<(unsigned)(pnch * std::max(ctx->natoms, 1)), 256, 0,
+                                                       ctx->stream>>>(
+                        ctx->d_psup_off, ctx->d_psup_node, ctx->d_psup_coef, nullptr, Ycur, nullptr, N, ldb, s.chunk,
+                        pnch, ctx->d_pchunk_order, s.part);
+                    const long long n8 = (long long)ctx->natoms * 8 * N;
+                    k_support_sum<<<nblk(n8, 256), 256, 0, ctx->stream>>>(ctx->natoms, pnch, N, s.part, s.Wc,
+                                                                          nullptr);
+                    ctx->launches += 2;
+                }
+            } else {
+                // E Y_c and P_c Y_c over the supports, from the bf16 rows of Y_c
+                k_support_reduce3<__nv_bfloat16><<<(unsigned)(s.nch * std::max(ctx->natoms, 1)), 256, 0,
+                                                   ctx->stream>>>(
+                    ctx->d_sup_off, ctx->d_sup_node, ctx->enrich ? ctx->d_E32 : ctx->d_Pc32,
+                    (ctx->enrich && ctx->nonlocal) ? ctx->d_Pc32 : nullptr, Ycur, nullptr, N, ldb, s.chunk, s.nch,
+                    ctx->d_chunk_order, s.part);
+                const long long n8 = (long long)ctx->natoms * 8 * N;
+                k_support_sum<<<nblk(n8, 256), 256, 0, ctx->stream>>>(ctx->natoms, s.nch, N, s.part,
+                                                                      ctx->enrich ? s.Rh : s.Wc,
+                                                                      (ctx->enrich && ctx->nonlocal) ? s.Wc : nullptr);
+                ctx->launches += 2;
+            }
+            // W = D (P_c Y_c + P^E Y_e)
             if (ctx->nonlocal) {
-                k_proj_w<float><<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
-                    ctx->n_proj, ne_, s.Wc, ctx->enrich ? ctx->d_PE : nullptr, Ye, ldb, ctx->d_hproj, N, s.W);
+                k_proj_w_sp<float><<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
+                    ctx->n_proj, ne_, s.Wc, ctx->enrich ? ctx->d_PE : nullptr, Ye, ldb, ctx->d_hproj, N,
+                    ctx->d_enbr_ptr, ctx->d_enbr, s.W);
                 k_to_float_strided<<<nblk((long long)ctx->n_proj * N, 256), 256, 0, ctx->stream>>>(
                     ctx->n_proj, N, s.W, W32, ldb, W16);
                 ctx->launches += 2;
-            }
-            if (ctx->enrich) {
-                k_enr_raw<float><<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(
-                    ne_, ctx->n_proj, s.Rh, ctx->d_HEee, ctx->nonlocal ? ctx->d_PE : nullptr, s.W, Ye, ldb, N,
-                    s.Yraw);
-                ctx->launches++;
             }
             // the FE rows' coupling E^T Y_e + P_c^T W enters the cell products
             k_pack_yw<<<nblk((long long)(ctx->natoms + 1) * nCB * 64, 256), 256, 0, ctx->stream>>>(
@@ -1493,8 +1622,21 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
             auto *ev = cell_event_pair(ctx);
             if (ev) cudaEventRecord(ev->first, ctx->stream);
             EFE_TRY(efe_tc_cells(ctx, Ycur, ldb, N, Ycells, ldb, ctx->d_err, cells16 ? 1 : 0, cpl ? YW : nullptr,
-                                 nCB));
+                                 nCB, epad ? Epart : nullptr));
             if (ev) cudaEventRecord(ev->second, ctx->stream);
+        }
+        if (cpl && ctx->enrich) {
+            // enriched rows: E Y_c + H^E_ee Y_e + P^E^T W
+            if (epad) {
+                k_epart_sum<<<dim3((unsigned)((N + 31) / 32), 4, (unsigned)ctx->natoms), 256, 0, ctx->stream>>>(
+                    N, ldb, ctx->d_atom_pair_off, ctx->d_atom_pairs, Epart, s.Rh);
+                ctx->launches++;
+            }
+            k_enr_raw_sp<float><<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(
+                ne_, s.Rh, ctx->d_HEee, ctx->nonlocal ? ctx->d_PE : nullptr, s.W, Ye, ldb, N, ctx->d_enbr_ptr,
+                ctx->d_enbr, s.Yraw);
+            ctx->launches++;
+            EFE_TRY(efe_check_launch(ctx, "enriched rows"));
         }
         auto *rev = rec_event_pair(ctx);
         if (rev) cudaEventRecord(rev->first, ctx->stream);
@@ -1754,7 +1896,9 @@ void efe_destroy(efe_ctx *ctx) {
                     ctx->d_node_ent, ctx->d_ent_atom,
                     ctx->d_pairs, ctx->d_pair_pos, ctx->d_cell_atom_ptr, ctx->d_cell_atoms, ctx->d_Aee, ctx->d_Kaa,
                     ctx->d_Haa, ctx->d_Mee, ctx->d_Pa, ctx->d_Mblk_inv, ctx->d_Mblk, ctx->d_ws, ctx->d_part,
-                    ctx->d_info, ctx->d_err, ctx->d_solver_ws, ctx->d_cx_off, ctx->d_cx_atoms, ctx->d_Ax};
+                    ctx->d_info, ctx->d_err, ctx->d_solver_ws, ctx->d_cx_off, ctx->d_cx_atoms, ctx->d_Ax,
+                    ctx->d_atom_pair_off, ctx->d_atom_pairs, ctx->d_psup_off, ctx->d_psup_node,
+                    ctx->d_psup_coef, ctx->d_pchunk_order, ctx->d_enbr_ptr, ctx->d_enbr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);

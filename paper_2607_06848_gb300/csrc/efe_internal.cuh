@@ -137,6 +137,21 @@ struct efe_ctx {
     void *d_Ax = nullptr;                     // extra A stages, bf16 [k-step][MT][2048]
     long long cx_steps = 0;
     int cx_max_slots = 0;                     // largest atom-slot count of a cell
+    // E Y_c from the padding rows of the cell products (rows ne .. MT*128 of the
+    // last M-tile hold, per atom slot, the E coefficients of the owned nodes)
+    bool epad = false;
+    int *d_atom_pair_off = nullptr;           // natoms + 1
+    int *d_atom_pairs = nullptr;              // per atom: its (cell, atom) pairs (indices into d_cell_atoms)
+    int ca_pairs = 0;                         // number of (cell, atom) support pairs
+    // the support entries with a nonzero projector row, per atom (sorted by node)
+    std::vector<long long> psup_off;          // natoms + 1
+    long long *d_psup_off = nullptr;
+    int *d_psup_node = nullptr;
+    float *d_psup_coef = nullptr;             // 4 per entry
+    int2 *d_pchunk_order = nullptr;
+    int pchunk_nch = 0;
+    // per atom, the atoms whose blocks of H^E_ee or P^E are not all zero (per potential)
+    int *d_enbr_ptr = nullptr, *d_enbr = nullptr;
 };
 
 // error helpers
@@ -176,5 +191,5 @@ efe_status efe_cells_shared(efe_ctx *ctx, const double *K, const double *X, doub
 efe_status efe_xprime_fp64(efe_ctx *ctx, const double *X, double *Xp, int N);
 void efe_sym_eig(int n, const std::vector<double> &A, std::vector<double> &w, std::vector<double> &V);
 efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, void *Ycells, int ldy, int *d_err,
-                        int out_bf16 = 0, const void *YW = nullptr, int nCB = 0);
+                        int out_bf16 = 0, const void *YW = nullptr, int nCB = 0, float *Epart = nullptr);
 int efe_tc_columns(const efe_ctx *ctx, int N, int ldb);

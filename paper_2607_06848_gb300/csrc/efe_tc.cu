@@ -78,6 +78,8 @@ struct TcParams {
     const __nv_bfloat16 *YW;            // [atom][nCB][8 rows][8 columns]: Y_e (rows 0-3), W (rows 4-7)
     int nCB;                            // 8-column blocks per atom in YW
     int x_slot_bytes;                   // shared memory of the extra B slot
+    float *Epart;                       // E Y_c per (cell-atom pair, f) from the padding rows (nullptr: none)
+    const int *ca_ptr;                  // ncells + 1: the cell-atom pairs of each cell
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -429,6 +431,27 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                     }
                     __syncwarp();
                 }
+                // the padding rows of the last tile carry E Y_c partials (row ne + 4 slot + f)
+                if (P.Epart && mt == P.MT - 1 && rbase + 32 > P.ne) {
+                    const int q0 = P.ca_ptr[cell];
+                    const int nrow = 4 * (P.ca_ptr[cell + 1] - q0);
+                    const int r = rbase + lane - P.ne;                 // this lane's padding row
+                    float *dst = P.Epart + ((size_t)q0 * 4 + (r > 0 ? r : 0)) * P.ldy + col0;
+                    for (int c0 = 0; c0 < P.Npad; c0 += 16) {
+                        uint32_t v[16];
+                        tmem_ld16_nw(tbase + (uint32_t)c0, v);
+                        tmem_wait_ld();
+                        reg_after_wait(v);
+                        if (r >= 0 && r < nrow) {
+#pragma unroll
+                            for (int i = 0; i < 16; i += 4)
+                                if (col0 + c0 + i < P.ldy)
+                                    *reinterpret_cast<float4 *>(dst + c0 + i) =
+                                        make_float4(__uint_as_float(v[i]), __uint_as_float(v[i + 1]),
+                                                    __uint_as_float(v[i + 2]), __uint_as_float(v[i + 3]));
+                        }
+                    }
+                }
                 fence_before();
                 mbar_arrive(&acc_empty[mt]);
             }
@@ -508,6 +531,66 @@ __global__ void k_tile_coupling(MeshDev m, int MT, const int *__restrict__ cx_of
             }
         }
         Ax[((size_t)(x0 + j) * MT + mt) * 2048 + e] = __float2bfloat16_rn(v);
+    }
+}
+
+// The padding rows of each cell's last M-tile (rows ne .. MT*128): row
+// ne + 4 s + f holds E_f of the cell's s-th support atom (the cell-atom list:
+// the atoms whose support cells include the cell), as a row of the cell matrix
+// over the operand's K ordering (node (z*(p+1) + y)*xpad + x), so the cell
+// products also return the cell's share of E Y_c.  Each (node, atom) entry
+// goes to exactly one cell: of the cells that contain the node and are
+// support cells of the atom, the one with the largest index.  Zero elsewhere.
+__global__ void k_tile_epad(MeshDev m, int MT, int xpad, int ksteps, const int *__restrict__ ca_ptr,
+                            const int *__restrict__ ca_atoms, const long long *__restrict__ node_ptr,
+                            const int *__restrict__ nm_atom, const float *__restrict__ nmE,
+                            __nv_bfloat16 *__restrict__ He16) {
+    const int c = blockIdx.x;
+    const int q0 = ca_ptr[c], nslot = ca_ptr[c + 1] - q0;
+    const int cx = c % m.nx, cy = (c / m.nx) % m.ny, cz = c / (m.nx * m.ny);
+    const int mt = MT - 1, r0 = m.ne - mt * 128;         // first padding row within the tile
+    const int nrow = 128 - r0;
+    const long long total = (long long)ksteps * nrow * 16;
+    for (long long i = threadIdx.x; i < total; i += blockDim.x) {
+        const int kk = (int)(i % 16);
+        const int rr = (int)((i / 16) % nrow);
+        const int s = (int)(i / (16LL * nrow));
+        const int Rt = r0 + rr;                           // row within the tile
+        const int rg = Rt / 8, ri = Rt % 8, kg = kk / 8, ki = kk % 8;
+        const int r = Rt + mt * 128 - m.ne, slot = r / 4, f = r % 4;
+        float v = 0.f;
+        if (slot < nslot) {
+            const int atom = ca_atoms[q0 + slot];
+            const int K = s * 16 + kk;
+            const int x = K % xpad, y = (K / xpad) % m.np1, z = K / (xpad * m.np1);
+            const int ix = cx * m.p + x, iy = cy * m.p + y, iz = cz * m.p + z;
+            if (x < m.np1 && z < m.np1 && ix >= 1 && iy >= 1 && iz >= 1 && ix <= m.Gx - 2 && iy <= m.Gy - 2 &&
+                iz <= m.Gz - 2) {
+                // the largest-index support cell of `atom` containing the node
+                int best = -1;
+                for (int dz = 0; dz < 2; ++dz)
+                    for (int dy = 0; dy < 2; ++dy)
+                        for (int dx = 0; dx < 2; ++dx) {
+                            const int ex = ix / m.p - dx, ey = iy / m.p - dy, ez = iz / m.p - dz;
+                            if (ex < 0 || ey < 0 || ez < 0 || ex >= m.nx || ey >= m.ny || ez >= m.nz) continue;
+                            if (ix - ex * m.p > m.p || iy - ey * m.p > m.p || iz - ez * m.p > m.p) continue;
+                            const int e = (ez * m.ny + ey) * m.nx + ex;
+                            if (e <= best) continue;
+                            for (int q = ca_ptr[e]; q < ca_ptr[e + 1]; ++q)
+                                if (ca_atoms[q] == atom) { best = e; break; }
+                        }
+                if (best == c) {
+                    const long long n = ((long long)iz * m.Gy + iy) * m.Gx + ix;
+                    for (long long q = node_ptr[n]; q < node_ptr[n + 1]; ++q)
+                        if ((nm_atom[q] & kNmAtomMask) == atom) {
+                            v = nmE[4 * q + f];
+                            break;
+                        }
+                }
+            }
+        }
+        const size_t e = (((size_t)c * ksteps + s) * MT + mt) * 2048 + (size_t)(rg * 2 + kg) * 64 + ri * 8 + ki;
+        He16[e] = __float2bfloat16_rn(v);
     }
 }
 
@@ -609,6 +692,30 @@ static efe_status tc_coupling_structure(efe_ctx *ctx, int MT) {
         maxs = std::max(maxs, (int)list.size());
     }
     if (atoms.empty()) atoms.assign(2, ctx->natoms);
+    // E Y_c from the padding rows: a cell's rows carry the atoms whose support
+    // cells include it (the cell-atom lists); per atom, its (cell, atom) pairs
+    // in cell order, over which the partials are summed
+    std::vector<int> cptr(ncells + 1), cat;
+    EFE_CUDA(ctx, cudaMemcpy(cptr.data(), ctx->d_cell_atom_ptr, sizeof(int) * (ncells + 1), cudaMemcpyDeviceToHost));
+    cat.resize(std::max(cptr[ncells], 1));
+    if (cptr[ncells] > 0)
+        EFE_CUDA(ctx, cudaMemcpy(cat.data(), ctx->d_cell_atoms, sizeof(int) * cptr[ncells], cudaMemcpyDeviceToHost));
+    int maxca = 0;
+    for (int c = 0; c < ncells; ++c) maxca = std::max(maxca, cptr[c + 1] - cptr[c]);
+    std::vector<int> aoff(ctx->natoms + 2, 0), apairs;
+    for (int q = 0; q < cptr[ncells]; ++q) aoff[cat[q] + 2]++;
+    for (int I = 0; I < ctx->natoms; ++I) aoff[I + 2] += aoff[I + 1];
+    apairs.resize(std::max(aoff[ctx->natoms + 1], 1));
+    for (int q = 0; q < cptr[ncells]; ++q) apairs[aoff[cat[q] + 1]++] = q;
+    aoff.pop_back();
+    ctx->ca_pairs = cptr[ncells];
+    EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_atom_pair_off, sizeof(int) * (ctx->natoms + 1)));
+    EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_atom_pairs, sizeof(int) * apairs.size()));
+    EFE_CUDA(ctx, cudaMemcpy(ctx->d_atom_pair_off, aoff.data(), sizeof(int) * (ctx->natoms + 1),
+                             cudaMemcpyHostToDevice));
+    EFE_CUDA(ctx, cudaMemcpy(ctx->d_atom_pairs, apairs.data(), sizeof(int) * apairs.size(), cudaMemcpyHostToDevice));
+    // the padding rows hold 4 E rows per cell-atom pair when they suffice
+    ctx->epad = ctx->enrich && 4 * maxca <= MT * 128 - m.ne;
     EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_cx_off, sizeof(int) * (ncells + 1)));
     EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_cx_atoms, sizeof(int) * atoms.size()));
     EFE_CUDA(ctx, cudaMemcpy(ctx->d_cx_off, off.data(), sizeof(int) * (ncells + 1), cudaMemcpyHostToDevice));
@@ -617,6 +724,46 @@ static efe_status tc_coupling_structure(efe_ctx *ctx, int MT) {
     EFE_TRY(efe_alloc(ctx, &ctx->d_Ax, sizeof(__nv_bfloat16) * (size_t)std::max(ctx->cx_steps, 1LL) * MT * 2048));
     ctx->cx_max_slots = maxs;
     ctx->cx_built = true;
+    return EFE_OK;
+}
+
+// Per atom I, the atoms J whose 4x4 blocks of H^E_ee (I, J) or of P^E
+// ((I, J) or (J, I)) hold a nonzero, read from the assembled FP64 blocks of
+// the current potential (overlapping supports; I itself included).
+static efe_status tc_block_pattern(efe_ctx *ctx) {
+    const int na = ctx->natoms, ne = ctx->n_enr;
+    std::vector<double> he, pe;
+    EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->enrich) {
+        he.resize((size_t)ne * ne);
+        EFE_CUDA(ctx, cudaMemcpy(he.data(), ctx->d_HEee, sizeof(double) * he.size(), cudaMemcpyDeviceToHost));
+        if (ctx->nonlocal && ctx->d_PE) {
+            pe.resize((size_t)ctx->n_proj * ne);
+            EFE_CUDA(ctx, cudaMemcpy(pe.data(), ctx->d_PE, sizeof(double) * pe.size(), cudaMemcpyDeviceToHost));
+        }
+    }
+    std::vector<int> ptr(na + 1, 0), nb;
+    for (int I = 0; I < na; ++I) {
+        for (int J = 0; J < na; ++J) {
+            bool nz = I == J;
+            for (int a = 0; a < 4 && !nz; ++a)
+                for (int b = 0; b < 4 && !nz; ++b) {
+                    if (!he.empty() && he[(size_t)(4 * I + a) * ne + 4 * J + b] != 0.0) nz = true;
+                    if (!pe.empty() && (pe[(size_t)(4 * I + a) * ne + 4 * J + b] != 0.0 ||
+                                        pe[(size_t)(4 * J + a) * ne + 4 * I + b] != 0.0))
+                        nz = true;
+                }
+            if (nz) nb.push_back(J);
+        }
+        ptr[I + 1] = (int)nb.size();
+    }
+    if (nb.empty()) nb.push_back(0);
+    if (!ctx->d_enbr_ptr) EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_enbr_ptr, sizeof(int) * (na + 1)));
+    if (ctx->d_enbr) cudaFree(ctx->d_enbr);
+    ctx->d_enbr = nullptr;
+    EFE_TRY(efe_alloc(ctx, (void **)&ctx->d_enbr, sizeof(int) * nb.size()));
+    EFE_CUDA(ctx, cudaMemcpy(ctx->d_enbr_ptr, ptr.data(), sizeof(int) * (na + 1), cudaMemcpyHostToDevice));
+    EFE_CUDA(ctx, cudaMemcpy(ctx->d_enbr, nb.data(), sizeof(int) * nb.size(), cudaMemcpyHostToDevice));
     return EFE_OK;
 }
 
@@ -646,6 +793,14 @@ efe_status efe_tc_prepare(efe_ctx *ctx) {
             ctx->d_nm_P32, ctx->enrich ? 1 : 0, ctx->nonlocal ? 1 : 0, reinterpret_cast<__nv_bfloat16 *>(ctx->d_Ax));
         ctx->launches++;
         EFE_TRY(efe_check_launch(ctx, "k_tile_coupling"));
+        EFE_TRY(tc_block_pattern(ctx));
+        if (ctx->epad) {
+            k_tile_epad<<<(unsigned)ncells, 256, 0, ctx->stream>>>(
+                m, MT, xpad, ksteps, ctx->d_cell_atom_ptr, ctx->d_cell_atoms, ctx->d_node_ptr, ctx->d_nm_atom,
+                ctx->d_nm_E32, reinterpret_cast<__nv_bfloat16 *>(ctx->d_He16));
+            ctx->launches++;
+            EFE_TRY(efe_check_launch(ctx, "k_tile_epad"));
+        }
     }
     ctx->he16_valid = true;
     return EFE_OK;
@@ -663,7 +818,7 @@ int efe_tc_columns(const efe_ctx *ctx, int N, int ldb) {
 // bf16, nCB = efe_tc_columns / 8, the last atom block zero) the owned FE rows
 // of each cell also receive E^T Y_e + P_c^T W.
 efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, void *Ycells, int ldy, int *d_err,
-                        int out_bf16, const void *YW, int nCB) {
+                        int out_bf16, const void *YW, int nCB, float *Epart) {
     const MeshDev &m = ctx->m;
     if (!ctx->he16_valid) EFE_TRY(efe_tc_prepare(ctx));
     PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode(ctx);
@@ -712,6 +867,8 @@ efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, void 
     P.YW = reinterpret_cast<const __nv_bfloat16 *>(YW);
     P.nCB = nCB;
     P.x_slot_bytes = sh.x_slot_bytes;
+    P.Epart = (cpl && ctx->epad) ? Epart : nullptr;
+    P.ca_ptr = ctx->d_cell_atom_ptr;
     if (cpl && sh.nchunks * P.ncb > nCB) {
         ctx->err = "tensor-core cell product: coupling table narrower than the column chunks";
         return EFE_ERR_ARG;
