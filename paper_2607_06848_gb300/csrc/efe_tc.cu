@@ -21,14 +21,19 @@
 //   D = accumulator, M-tile mt at TMEM columns [mt*Npad, (mt+1)*Npad).
 // The MMAs run k-step-major (all M-tiles of a k-step, then the next k-step),
 // so each plane pair is released as soon as its k-steps are done and the
-// freed shared memory deepens the A ring.  One cell's FP32 accumulators for
-// all columns would fill the SM's tensor memory, so that the next cell's MMAs
-// would wait for the epilogue's drain; instead the columns are split into
-// chunks of at most 256 / MT and two blocks run on each SM (up to 256 TMEM
-// columns and ~111 KB of shared memory each): while one block drains its
-// cell, the other's MMAs and loads proceed.  Blocks with the same blockIdx.x
-// walk the same cells (one column chunk each, blockIdx.y), so a cell's H_e
-// tiles come from DRAM once and from L2 for the other chunks.
+// freed shared memory deepens the A ring.  An A stage holds several k-steps
+// (one bulk copy and one barrier round trip per stage: the round trip, not the
+// data, bounds a stage of a single k-step).  Each tcgen05.mma costs about the
+// same issue time whatever its N, so all columns go into one instruction
+// (N up to 512 / MT) and the accumulators fill most of the SM's tensor memory;
+// when two buffers fit (small N) the epilogue of one cell overlaps the MMAs of
+// the next, otherwise the MMAs wait for it, and twelve epilogue warps (three
+// per TMEM lane quadrant) keep that drain short.  Columns beyond one
+// instruction's N go to further chunks, one per block of a thread-block
+// cluster; the cluster's blocks walk the same cells, and its first block
+// loads each A stage (H_e tiles, coupling tiles) once and multicasts it to
+// all of them, whose MMAs each release the stage (a multicast commit to the
+// empty barriers of every block).
 // Coupling (the bf16 filter): the FE rows of H^E Y also hold E^T Y_e + P_c^T W
 // (the FE-enrichment block of H^E and the projector rows).  Each FE node is
 // owned by exactly one cell (the one in which its local indices lie in
@@ -42,8 +47,8 @@
 // Per-cell results go to Ycells[cell][row][ldy] (FP32 or bf16); a gather
 // kernel sums the up-to-8 contributions of each node, so no colouring or
 // atomics are needed and every cell of the mesh runs in one persistent launch.
-// The epilogue stages each warp's 32 rows through shared memory (XOR-swizzled
-// 16-byte units) and writes whole 128-byte row segments.
+// The epilogue writes each thread's row (TMEM lane) in 16-column groups of whole
+// 32-byte sectors.
 #include "efe_internal.cuh"
 
 #include <cuda.h>
@@ -55,12 +60,12 @@
 
 namespace {
 
-constexpr int TC_THREADS = 256;      // w0 TMA producer, w1 MMA issuer, w2 TMEM owner, w4-7 epilogue
+constexpr int EPI_WARPS = 12;        // epilogue: three warps per TMEM lane quadrant, splitting the columns
+constexpr int TC_THREADS = 128 + 32 * EPI_WARPS;   // w0 TMA producer, w1 MMA issuer, w2 TMEM owner, w4.. epilogue
 constexpr int MAX_A_STAGES = 24;     // A ring depth limit (one stage = one k-step of all M-tiles)
 constexpr int B_SLOTS = 2;           // plane-pair ring
-constexpr int STAGE_BYTES = 2048;    // epilogue staging per warp: 32 rows x 64 B
-constexpr int SMEM_LIMIT = 113664;   // dynamic shared memory per block: two blocks per SM (2 x 111 KB)
-constexpr int TMEM_COLS = 256;       // tensor-memory columns per block (two blocks share the SM's 512)
+constexpr int SMEM_LIMIT = 232448;   // dynamic shared memory per block (227 KB, one block per SM)
+constexpr int TMEM_COLS = 512;       // tensor memory per block: one or two accumulator buffers
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz before a wait gives up
 
 struct TcParams {
@@ -69,6 +74,7 @@ struct TcParams {
     int kpg;                            // k-steps per plane pair: 2 plane_rows / 16
     int ngroups;                        // plane pairs per cell: ceil((p+1) / 2)
     int a_stages;                       // A ring depth
+    int ks;                             // k-steps per A stage (one bulk copy, one barrier pair)
     int slot_bytes;                     // one B slot: ncb x 2 plane_rows x 16 B
     int out_bf16;                       // per-cell results stored as bf16 (else FP32)
     // coupling as extra k-steps (cx_off == nullptr: none)
@@ -76,6 +82,8 @@ struct TcParams {
     const int *cx_atoms;                // 2 atom slots per extra k-step (natoms: the zero block)
     const __nv_bfloat16 *Ax;            // extra A stages [k-step][MT][2048]
     const __nv_bfloat16 *YW;            // [atom][nCB][8 rows][8 columns]: Y_e (rows 0-3), W (rows 4-7)
+    int ncl;                            // blocks per cluster = column chunks (blockIdx.y)
+    int nbuf;                           // accumulator buffers in tensor memory (1 or 2)
     int nCB;                            // 8-column blocks per atom in YW
     int x_slot_bytes;                   // shared memory of the extra B slot
     float *Epart;                       // E Y_c per (cell-atom pair, f) from the padding rows (nullptr: none)
@@ -129,6 +137,20 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                  : "memory");
 }
 
+// the same, delivered to the same shared-memory offset in every block of the
+// cluster in `mask`, signalling the barrier at that offset in each of them
+__device__ __forceinline__ void bulk_load_mc(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                             uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // shared-memory matrix descriptor, no swizzle (layout type 0), version 1
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = 0;
@@ -150,6 +172,14 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
+}
+// commit that arrives on the barrier at this offset in every block of `mask`
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
 }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -174,43 +204,76 @@ __device__ __forceinline__ void reg_after_wait(uint32_t r[16]) {
                    "+r"(r[15]));
 }
 
-// 16-byte unit u (0..3) of staged row `row` (rows of 64 B; units XOR-swizzled
-// by bits 1-2 of the row, so that any 8 consecutive rows -- a quarter-warp
-// access -- hit 8 different 16-byte bank groups)
-__device__ __forceinline__ void stage_store(uint32_t base, int row, int u, uint32_t x, uint32_t y, uint32_t z,
-                                            uint32_t w) {
-    const uint32_t a = base + (uint32_t)(row * 64 + ((u ^ ((row >> 1) & 3)) * 16));
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+// Columns col .. col+15 of one output row from 16 FP32 accumulators: bf16 (32
+// bytes) or FP32 (64 bytes); 256-bit stores when `wide` (aligned), else 16-byte
+// stores; nothing at or past ldy (ldy is a multiple of 8 for bf16, of 4 for FP32).
+__device__ __forceinline__ void store16(unsigned char *row, int col, int ldy, int bf16, bool wide,
+                                        const uint32_t v[16]) {
+    if (bf16) {
+        uint32_t w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            __nv_bfloat162 b2 = __floats2bfloat162_rn(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+            w[i] = *reinterpret_cast<uint32_t *>(&b2);
+        }
+        unsigned char *p = row + (size_t)col * 2;
+        if (wide && col + 16 <= ldy) {
+            asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]), "r"(w[1]),
+                         "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                         : "memory");
+        } else {
+            if (col + 8 <= ldy) *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+            if (col + 16 <= ldy) *reinterpret_cast<uint4 *>(p + 16) = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+    } else {
+        unsigned char *p = row + (size_t)col * 4;
+        if (wide && col + 16 <= ldy) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p + 32 * h),
+                             "r"(v[8 * h]), "r"(v[8 * h + 1]), "r"(v[8 * h + 2]), "r"(v[8 * h + 3]), "r"(v[8 * h + 4]),
+                             "r"(v[8 * h + 5]), "r"(v[8 * h + 6]), "r"(v[8 * h + 7])
+                             : "memory");
+        } else {
+#pragma unroll
+            for (int h = 0; h < 4; ++h)
+                if (col + 4 * h + 4 <= ldy)
+                    *reinterpret_cast<uint4 *>(p + 16 * h) = make_uint4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+        }
+    }
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 2)
+__global__ void __launch_bounds__(TC_THREADS, 1)
     k_cell_mma(const __grid_constant__ CUtensorMap xmap, const __nv_bfloat16 *__restrict__ He16, void *Ycells,
                TcParams P, int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // every TMA destination below is a multiple of 128 B from this base
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    const int stage_bytes = P.MT * 4096;
+    const int stage_bytes = P.ks * P.MT * 4096;      // one A stage: ks k-steps of all M-tiles
     unsigned char *sA = smem;
     unsigned char *sB = smem + (size_t)P.a_stages * stage_bytes;
     unsigned char *sX = sB + (size_t)B_SLOTS * P.slot_bytes;
-    unsigned char *sStage = sX + P.x_slot_bytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sStage + 4 * STAGE_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sX + P.x_slot_bytes);
     uint64_t *full_a = bars, *empty_a = bars + MAX_A_STAGES;
     uint64_t *full_b = bars + 2 * MAX_A_STAGES, *empty_b = full_b + B_SLOTS;
-    uint64_t *acc_full = empty_b + B_SLOTS, *acc_empty = acc_full + 4;
-    uint64_t *full_x = acc_empty + 4, *empty_x = full_x + 1;
+    uint64_t *acc_full = empty_b + B_SLOTS, *acc_empty = acc_full + 8;   // [buffer][M-tile]
+    uint64_t *full_x = acc_empty + 8, *empty_x = full_x + 1;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(empty_x + 1);
     const uint32_t xblk = (uint32_t)P.ncb * 128;      // one atom's 8 rows x Npad columns in sX
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int pair_stride = 2 * P.plane_rows * 16;   // bytes between column blocks in a slot
-    const int col0 = blockIdx.y * P.Npad;             // this block's column chunk
+    const int col0 = blockIdx.y * P.Npad;             // this block's column chunk (its rank in the cluster)
+    const bool leader = blockIdx.y == 0;               // loads (and multicasts) the A stages
+    const uint16_t cmask = (uint16_t)((1u << P.ncl) - 1u);
+    const uint32_t acc_cols = (uint32_t)(P.MT * P.Npad);   // one accumulator buffer
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < P.a_stages; ++i) { mbar_init(&full_a[i], 1); mbar_init(&empty_a[i], 1); }
+        // an A stage is released by the MMAs of every block of the cluster
+        for (int i = 0; i < P.a_stages; ++i) { mbar_init(&full_a[i], 1); mbar_init(&empty_a[i], P.ncl); }
         for (int i = 0; i < B_SLOTS; ++i) { mbar_init(&full_b[i], 1); mbar_init(&empty_b[i], 1); }
-        for (int t = 0; t < 4; ++t) { mbar_init(&acc_full[t], 1); mbar_init(&acc_empty[t], 128); }
+        for (int t = 0; t < 8; ++t) { mbar_init(&acc_full[t], 1); mbar_init(&acc_empty[t], 32 * EPI_WARPS); }
         mbar_init(full_x, 1);
         mbar_init(empty_x, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -228,47 +291,56 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     }
     __syncthreads();
     fence_after();
+    // every block's barriers exist before any multicast or remote arrive reaches them
+    cluster_sync_all();
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
         // ---------------- producer ----------------
+        // A stages of up to KS k-steps (one bulk copy each, multicast by the
+        // leader); before a stage, the plane pairs its k-steps read
         int sa = 0, sb = 0;
         uint32_t pha = 0, phb = 0;
         bool ok = true;
         uint32_t aused = 0, apar = 0;      // per A slot: issued at least once, parity of its last phase
         uint32_t bused = 0, bpar = 0;      // the same per B slot
         uint32_t phx = 0, xused = 0, xpar = 0;
+        auto load_a = [&](const __nv_bfloat16 *src, int cnt) -> bool {
+            if (!mbar_wait(&empty_a[sa], pha ^ 1)) return false;
+            const uint32_t bytes = (uint32_t)(cnt * P.MT * 4096);
+            mbar_expect_tx(&full_a[sa], bytes);
+            if (P.ncl == 1) bulk_load(sA + (size_t)sa * stage_bytes, src, bytes, &full_a[sa]);
+            else if (leader) bulk_load_mc(sA + (size_t)sa * stage_bytes, src, bytes, &full_a[sa], cmask);
+            aused |= 1u << sa;
+            apar = (apar & ~(1u << sa)) | (pha << sa);
+            if (++sa == P.a_stages) { sa = 0; pha ^= 1; }
+            return true;
+        };
         for (int cell = blockIdx.x; cell < P.ncells && ok; cell += gridDim.x) {
             const int cx = cell % P.nx, cy = (cell / P.nx) % P.ny, cz = cell / (P.nx * P.ny);
             const __nv_bfloat16 *Ac = He16 + (size_t)cell * P.ksteps * P.MT * 2048;
-            int s = 0;
-            for (int g = 0; g < P.ngroups && ok; ++g) {
-                // plane pair g -> B slot sb
-                if (!mbar_wait(&empty_b[sb], phb ^ 1)) { ok = false; break; }
-                const int np = min(2, P.np1 - 2 * g);
-                mbar_expect_tx(&full_b[sb], (uint32_t)(np * P.plane_rows * 16 * P.ncb));
-                unsigned char *slot = sB + (size_t)sb * P.slot_bytes;
-                for (int zz = 0; zz < np; ++zz)
-                    for (int cb = 0; cb < P.ncb; ++cb)
-                        tma_load_4d(slot + (size_t)cb * pair_stride + (size_t)zz * P.plane_rows * 16, &xmap,
-                                    col0 + 8 * cb, cx * P.p, cy * P.p, cz * P.p + 2 * g + zz,
-                                    &full_b[sb]);   // {cols, x, y, z}
-                bused |= 1u << sb;
-                bpar = (bpar & ~(1u << sb)) | (phb << sb);
-                if (++sb == B_SLOTS) { sb = 0; phb ^= 1; }
-                // the A stages of this pair's k-steps
-                const int s_end = min(P.ksteps, (g + 1) * P.kpg);
-                for (; s < s_end; ++s) {
-                    if (!mbar_wait(&empty_a[sa], pha ^ 1)) { ok = false; break; }
-                    mbar_expect_tx(&full_a[sa], (uint32_t)stage_bytes);
-                    bulk_load(sA + (size_t)sa * stage_bytes, Ac + (size_t)s * P.MT * 2048, (uint32_t)stage_bytes,
-                              &full_a[sa]);
-                    aused |= 1u << sa;
-                    apar = (apar & ~(1u << sa)) | (pha << sa);
-                    if (++sa == P.a_stages) { sa = 0; pha ^= 1; }
+            int gnext = 0;
+            for (int s = 0; s < P.ksteps && ok; s += P.ks) {
+                const int cnt = min(P.ks, P.ksteps - s);
+                // plane pairs read by k-steps < s + cnt
+                while (ok && gnext < P.ngroups && gnext * P.kpg < s + cnt) {
+                    const int g = gnext++;
+                    if (!mbar_wait(&empty_b[sb], phb ^ 1)) { ok = false; break; }
+                    const int np = min(2, P.np1 - 2 * g);
+                    mbar_expect_tx(&full_b[sb], (uint32_t)(np * P.plane_rows * 16 * P.ncb));
+                    unsigned char *slot = sB + (size_t)sb * P.slot_bytes;
+                    for (int zz = 0; zz < np; ++zz)
+                        for (int cb = 0; cb < P.ncb; ++cb)
+                            tma_load_4d(slot + (size_t)cb * pair_stride + (size_t)zz * P.plane_rows * 16, &xmap,
+                                        col0 + 8 * cb, cx * P.p, cy * P.p, cz * P.p + 2 * g + zz,
+                                        &full_b[sb]);   // {cols, x, y, z}
+                    bused |= 1u << sb;
+                    bpar = (bpar & ~(1u << sb)) | (phb << sb);
+                    if (++sb == B_SLOTS) { sb = 0; phb ^= 1; }
                 }
+                if (!ok || !load_a(Ac + (size_t)s * P.MT * 2048, cnt)) { ok = false; break; }
             }
-            // the coupling: Y_e / W rows of the cell's atoms, then the extra A stages
+            // the coupling: Y_e / W rows of the cell's atoms, then its extra A stages
             const int x0 = P.cx_off ? P.cx_off[cell] : 0;
             const int nxs = P.cx_off ? P.cx_off[cell + 1] - x0 : 0;
             if (ok && nxs > 0) {
@@ -281,20 +353,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                 xused = 1;
                 xpar = phx;
                 phx ^= 1;
-                for (int j = 0; j < nxs; ++j) {
-                    if (!mbar_wait(&empty_a[sa], pha ^ 1)) { ok = false; break; }
-                    mbar_expect_tx(&full_a[sa], (uint32_t)stage_bytes);
-                    bulk_load(sA + (size_t)sa * stage_bytes, P.Ax + (size_t)(x0 + j) * P.MT * 2048,
-                              (uint32_t)stage_bytes, &full_a[sa]);
-                    aused |= 1u << sa;
-                    apar = (apar & ~(1u << sa)) | (pha << sa);
-                    if (++sa == P.a_stages) { sa = 0; pha ^= 1; }
-                }
+                for (int j = 0; j < nxs && ok; j += P.ks)
+                    if (!load_a(P.Ax + (size_t)(x0 + j) * P.MT * 2048, min(P.ks, nxs - j))) ok = false;
             }
         }
         if (!ok) atomicExch(err, 1);
         if (xused) mbar_wait(full_x, xpar);
-        // drain: every copy this thread issued has landed before the block exits
+        // drain: every copy this thread issued (or expects) has landed before the block exits
         for (int i = 0; i < B_SLOTS; ++i)
             if (bused & (1u << i)) mbar_wait(&full_b[i], (bpar >> i) & 1u);
         for (int i = 0; i < P.a_stages; ++i)
@@ -308,31 +373,44 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         int it = 0;
         bool ok = true;
         const uint32_t sB_addr = smem_u32(sB), sA_addr = smem_u32(sA), sX_addr = smem_u32(sX);
+        // descriptors differ only in the 14-bit start-address field (shared
+        // addresses < 256 KB): a base descriptor plus (byte offset >> 4)
+        const uint64_t adesc0 = smem_desc(sA_addr, 128, 256);
+        const uint64_t bdesc0 = smem_desc(sB_addr, 128, (uint32_t)pair_stride);
         for (int cell = blockIdx.x; cell < P.ncells && ok; cell += gridDim.x, ++it) {
-            // every M-tile accumulates over the whole cell: all of them must be drained
+            // accumulator buffer of this cell: every M-tile of it must be drained
+            const int buf = it % P.nbuf, use = it / P.nbuf;
+            const uint32_t dacc = tmem + (uint32_t)buf * acc_cols;
             for (int mt = 0; mt < P.MT && ok; ++mt)
-                if (!mbar_wait(&acc_empty[mt], (it & 1) ^ 1)) ok = false;
+                if (!mbar_wait(&acc_empty[4 * buf + mt], (use & 1) ^ 1)) ok = false;
             if (!ok) break;
             fence_after();
-            for (int s = 0; s < P.ksteps; ++s) {
-                const int g = s / P.kpg, j = s - g * P.kpg;
-                if (j == 0) {
-                    if (!mbar_wait(&full_b[sb], phb)) { ok = false; break; }
-                    fence_after();
-                }
+            int j = 0;                                        // k-step within the current plane pair
+            for (int s0 = 0; s0 < P.ksteps && ok; s0 += P.ks) {
+                const int cnt = min(P.ks, P.ksteps - s0);
                 if (!mbar_wait(&full_a[sa], pha)) { ok = false; break; }
                 fence_after();
-                const uint64_t bd = smem_desc(sB_addr + sb * P.slot_bytes + j * 256, 128, (uint32_t)pair_stride);
-                for (int mt = 0; mt < P.MT; ++mt) {
-                    const uint64_t ad = smem_desc(sA_addr + sa * stage_bytes + mt * 4096, 128, 256);
-                    mma_bf16(tmem + (uint32_t)(mt * P.Npad), ad, bd, idesc, s > 0 ? 1u : 0u);
+                uint64_t ad = adesc0 + (uint64_t)(((uint32_t)sa * (uint32_t)stage_bytes) >> 4);
+                for (int t = 0; t < cnt; ++t, ad += (uint64_t)(P.MT * 4096 >> 4)) {
+                    const int s = s0 + t;
+                    if (j == 0) {
+                        if (!mbar_wait(&full_b[sb], phb)) { ok = false; break; }
+                        fence_after();
+                    }
+                    const uint64_t bd = bdesc0 + (uint64_t)(((uint32_t)sb * (uint32_t)P.slot_bytes + j * 256) >> 4);
+                    const uint32_t acc = s > 0 ? 1u : 0u;
+                    for (int mt = 0; mt < P.MT; ++mt)
+                        mma_bf16(dacc + (uint32_t)(mt * P.Npad), ad + (uint64_t)(mt * 256), bd, idesc, acc);
+                    if (++j == P.kpg || s == P.ksteps - 1) {
+                        mma_commit(&empty_b[sb]);
+                        if (++sb == B_SLOTS) { sb = 0; phb ^= 1; }
+                        j = 0;
+                    }
                 }
-                mma_commit(&empty_a[sa]);
+                if (!ok) break;
+                if (P.ncl == 1) mma_commit(&empty_a[sa]);
+                else mma_commit_mc(&empty_a[sa], cmask);
                 if (++sa == P.a_stages) { sa = 0; pha ^= 1; }
-                if (j == P.kpg - 1 || s == P.ksteps - 1) {
-                    mma_commit(&empty_b[sb]);
-                    if (++sb == B_SLOTS) { sb = 0; phb ^= 1; }
-                }
             }
             if (!ok) break;
             const int x0 = P.cx_off ? P.cx_off[cell] : 0;
@@ -340,23 +418,27 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             if (nxs > 0) {
                 if (!mbar_wait(full_x, phx)) { ok = false; break; }
                 fence_after();
-                for (int j = 0; j < nxs; ++j) {
+                for (int j0 = 0; j0 < nxs && ok; j0 += P.ks) {
+                    const int cnt = min(P.ks, nxs - j0);
                     if (!mbar_wait(&full_a[sa], pha)) { ok = false; break; }
                     fence_after();
-                    // two atoms (16 K rows): K groups xblk apart, 8-column blocks 128 B apart
-                    const uint64_t bd = smem_desc(sX_addr + (uint32_t)(2 * j) * xblk, xblk, 128);
-                    for (int mt = 0; mt < P.MT; ++mt) {
-                        const uint64_t ad = smem_desc(sA_addr + sa * stage_bytes + mt * 4096, 128, 256);
-                        mma_bf16(tmem + (uint32_t)(mt * P.Npad), ad, bd, idesc, 1u);
+                    for (int t = 0; t < cnt; ++t) {
+                        // two atoms (16 K rows): K groups xblk apart, 8-column blocks 128 B apart
+                        const uint64_t bd = smem_desc(sX_addr + (uint32_t)(2 * (j0 + t)) * xblk, xblk, 128);
+                        const uint32_t abase = sA_addr + sa * stage_bytes + t * P.MT * 4096;
+                        for (int mt = 0; mt < P.MT; ++mt)
+                            mma_bf16(dacc + (uint32_t)(mt * P.Npad), smem_desc(abase + mt * 4096, 128, 256), bd,
+                                     idesc, 1u);
                     }
-                    mma_commit(&empty_a[sa]);
+                    if (P.ncl == 1) mma_commit(&empty_a[sa]);
+                    else mma_commit_mc(&empty_a[sa], cmask);
                     if (++sa == P.a_stages) { sa = 0; pha ^= 1; }
                 }
                 if (!ok) break;
                 mma_commit(empty_x);
                 phx ^= 1;
             }
-            for (int mt = 0; mt < P.MT; ++mt) mma_commit(&acc_full[mt]);
+            for (int mt = 0; mt < P.MT; ++mt) mma_commit(&acc_full[4 * buf + mt]);
         }
         if (!ok) atomicExch(err, 2);
     } else if (warp >= 4) {
@@ -364,75 +446,47 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         // TMEM -> registers (thread = row) -> shared memory (row of 64 B, its
         // 16-byte units XOR-swizzled by the row) -> global (4 lanes per row
         // segment: whole 32-byte sectors, 8 rows per warp store)
-        const int q = warp & 3;
-        unsigned char *stg = sStage + q * STAGE_BYTES;
-        const uint32_t stg_addr = smem_u32(stg);
-        const int ew = P.out_bf16 ? 2 : 4;              // bytes per stored element
-        const int cw = 64 / ew;                         // columns per staged chunk
-        const int upu = 16 / ew;                        // columns per 16-byte unit
+        const int q = warp & 3, ew = (warp - 4) >> 2;   // lane quadrant; which third of the column chunks
+        const int eb = P.out_bf16 ? 2 : 4;              // bytes per stored element
+        // 32-byte stores need 32-byte aligned rows and chunk starts
+        const bool wide = ((size_t)P.ldy * eb) % 32 == 0 && (col0 * eb) % 32 == 0 &&
+                          (reinterpret_cast<uintptr_t>(Ycells) & 31) == 0;
         int it = 0;
         bool ok = true;
         for (int cell = blockIdx.x; cell < P.ncells && ok; cell += gridDim.x, ++it) {
+            const int buf = it % P.nbuf, use = it / P.nbuf;
             for (int mt = 0; mt < P.MT; ++mt) {
                 // warp-uniform decision: the TMEM loads below are .sync.aligned
-                const bool got = mbar_wait(&acc_full[mt], it & 1);
+                const bool got = mbar_wait(&acc_full[4 * buf + mt], use & 1);
                 if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
                 fence_after();
                 const int rbase = mt * 128 + q * 32;
-                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * P.Npad);
-                unsigned char *ybase = reinterpret_cast<unsigned char *>(Ycells) +
-                                       (((size_t)cell * P.ne + rbase) * P.ldy + col0) * ew;
-                for (int c0 = 0; rbase < P.ne && c0 < P.Npad; c0 += cw) {
-                    const int nl = min(cw, P.Npad - c0) / 16;  // x16 loads, warp-uniform
-                    const int nu = nl * 16 / upu;                // 16-byte units per row
-                    uint32_t r[2][16];
+                const uint32_t tbase =
+                    tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * acc_cols + (uint32_t)(mt * P.Npad);
+                // this lane's output row (store16 takes the global column)
+                unsigned char *ybase =
+                    reinterpret_cast<unsigned char *>(Ycells) + ((size_t)cell * P.ne + rbase) * P.ldy * eb;
+                // 64-column chunks, one per warp of the quadrant in turn; four TMEM
+                // loads, one wait, then each thread stores its row's 16-column
+                // groups (32 or 64 bytes: whole sectors, 256-bit stores when aligned)
+                const bool row_ok = rbase + lane < P.ne;
+                unsigned char *yrow = ybase + (size_t)lane * P.ldy * eb;
+                for (int c0 = ew * 64; rbase < P.ne && c0 < P.Npad; c0 += (EPI_WARPS / 4) * 64) {
+                    const int nl = min(64, P.Npad - c0) / 16;  // warp-uniform
+                    uint32_t r[4][16];
 #pragma unroll
-                    for (int g = 0; g < 2; ++g)
+                    for (int g = 0; g < 4; ++g)
                         if (g < nl) tmem_ld16_nw(tbase + (uint32_t)(c0 + 16 * g), r[g]);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int g = 0; g < 2; ++g) {
+                    for (int g = 0; g < 4; ++g) {
                         if (g >= nl) continue;
                         reg_after_wait(r[g]);
-                        if (P.out_bf16) {
-                            // one x16 load = two 16-byte units of 8 bf16
-#pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                uint32_t w[4];
-#pragma unroll
-                                for (int i = 0; i < 4; ++i) {
-                                    __nv_bfloat162 bb = __floats2bfloat162_rn(__uint_as_float(r[g][8 * h + 2 * i]),
-                                                                              __uint_as_float(r[g][8 * h + 2 * i + 1]));
-                                    w[i] = *reinterpret_cast<uint32_t *>(&bb);
-                                }
-                                stage_store(stg_addr, lane, 2 * g + h, w[0], w[1], w[2], w[3]);
-                            }
-                        } else {
-                            // one x16 load = four 16-byte units of 4 floats
-#pragma unroll
-                            for (int h = 0; h < 4; ++h)
-                                stage_store(stg_addr, lane, 4 * g + h, r[g][4 * h], r[g][4 * h + 1], r[g][4 * h + 2],
-                                            r[g][4 * h + 3]);
-                        }
+                        if (row_ok) store16(yrow, col0 + c0 + 16 * g, P.ldy, P.out_bf16, wide, r[g]);
                     }
-                    __syncwarp();
-                    for (int idx = lane; idx < 32 * nu; idx += 32) {
-                        const int row = idx / nu, u = idx - row * nu;
-                        const int col = c0 + u * upu;
-                        if (rbase + row < P.ne && col0 + col < P.ldy) {
-                            uint4 v;
-                            const uint32_t a = stg_addr + (uint32_t)(row * 64 + ((u ^ ((row >> 1) & 3)) * 16));
-                            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
-                                         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                                         : "r"(a)
-                                         : "memory");
-                            *reinterpret_cast<uint4 *>(ybase + ((size_t)row * P.ldy + col) * ew) = v;
-                        }
-                    }
-                    __syncwarp();
                 }
                 // the padding rows of the last tile carry E Y_c partials (row ne + 4 slot + f)
-                if (P.Epart && mt == P.MT - 1 && rbase + 32 > P.ne) {
+                if (P.Epart && ew == 0 && mt == P.MT - 1 && rbase + 32 > P.ne) {
                     const int q0 = P.ca_ptr[cell];
                     const int nrow = 4 * (P.ca_ptr[cell + 1] - q0);
                     const int r = rbase + lane - P.ne;                 // this lane's padding row
@@ -453,7 +507,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                     }
                 }
                 fence_before();
-                mbar_arrive(&acc_empty[mt]);
+                mbar_arrive(&acc_empty[4 * buf + mt]);
             }
         }
         if (!ok) atomicExch(err, 3);
@@ -463,6 +517,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TMEM_COLS));
     }
+    // no block leaves while another may still multicast into it or arrive on its barriers
+    cluster_sync_all();
 }
 
 // Pre-tile H_e (FP32, ne x ne per cell) into bf16 MMA blocks:
@@ -614,17 +670,16 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode(efe_ctx *ctx) {
 
 // Geometry of the tensor-core cell product for this mesh and N columns.
 struct TcShape {
-    int xpad, Kpad, ksteps, MT, Npad, nchunks, plane_rows, kpg, ngroups, a_stages, slot_bytes, x_slot_bytes;
+    int xpad, Kpad, ksteps, MT, Npad, nchunks, plane_rows, kpg, ngroups, a_stages, ks, slot_bytes, x_slot_bytes;
     size_t smem;
 };
 
-constexpr size_t TC_FIXED = (2 * MAX_A_STAGES + 2 * B_SLOTS + 10) * 8 + 64 + 1024;   // barriers, TMEM slot, alignment
+constexpr size_t TC_FIXED = (2 * MAX_A_STAGES + 2 * B_SLOTS + 18) * 8 + 64 + 1024;   // barriers, TMEM slot, alignment
 
 // shared memory: A ring + two B slots + the coupling slot + epilogue staging +
 // barriers (+ alignment slack) within 227 KB
 static size_t tc_smem(const TcShape &s) {
-    return (size_t)s.a_stages * s.MT * 4096 + (size_t)B_SLOTS * s.slot_bytes + s.x_slot_bytes + 4 * STAGE_BYTES +
-           TC_FIXED;
+    return (size_t)s.a_stages * s.ks * s.MT * 4096 + (size_t)B_SLOTS * s.slot_bytes + s.x_slot_bytes + TC_FIXED;
 }
 
 // x_slots: atom slots of the coupling per cell (0: no coupling)
@@ -639,7 +694,7 @@ static TcShape tc_shape(const efe_ctx *ctx, int N, int ldb, int x_slots = 0) {
     s.kpg = 2 * s.plane_rows / 16;
     s.ngroups = (np1 + 1) / 2;
     const int stage = s.MT * 4096;
-    const size_t fixed = TC_FIXED + 4 * STAGE_BYTES;
+    const size_t fixed = TC_FIXED;
     int maxN = std::min(256, (TMEM_COLS / s.MT) / 16 * 16);
     // keep at least 4 A stages
     while (maxN > 16 && fixed + 4 * (size_t)stage + (size_t)B_SLOTS * (maxN / 8) * 2 * s.plane_rows * 16 +
@@ -653,7 +708,15 @@ static TcShape tc_shape(const efe_ctx *ctx, int N, int ldb, int x_slots = 0) {
     s.x_slot_bytes = x_slots * (s.Npad / 8) * 128;
     const size_t used = fixed + (size_t)B_SLOTS * s.slot_bytes + s.x_slot_bytes;
     const size_t left = used < (size_t)SMEM_LIMIT ? (size_t)SMEM_LIMIT - used : 0;
-    s.a_stages = (int)std::min<size_t>(MAX_A_STAGES, left / stage);
+    // A stages of ks k-steps: each stage costs one producer/MMA barrier round
+    // trip, so as many k-steps per stage as still leave three stages in flight
+    s.ks = 1;
+    for (int ks = 4; ks >= 1; --ks)
+        if (left / ((size_t)ks * stage) >= 3 || ks == 1) {
+            s.ks = ks;
+            break;
+        }
+    s.a_stages = (int)std::min<size_t>(MAX_A_STAGES, left / ((size_t)s.ks * stage));
     s.smem = tc_smem(s);
     return s;
 }
@@ -859,6 +922,7 @@ efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, void 
     P.kpg = sh.kpg;
     P.ngroups = sh.ngroups;
     P.a_stages = sh.a_stages;
+    P.ks = sh.ks;
     P.slot_bytes = sh.slot_bytes;
     P.out_bf16 = out_bf16;
     P.cx_off = cpl ? ctx->d_cx_off : nullptr;
@@ -873,17 +937,39 @@ efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, void 
         ctx->err = "tensor-core cell product: coupling table narrower than the column chunks";
         return EFE_ERR_ARG;
     }
-    if (sh.a_stages < 4 || sh.smem > (size_t)SMEM_LIMIT || sh.MT * sh.Npad > TMEM_COLS) {
+    P.ncl = sh.nchunks;
+    P.nbuf = 2 * sh.MT * sh.Npad <= TMEM_COLS ? 2 : 1;
+    if (sh.a_stages < 2 || sh.smem > (size_t)SMEM_LIMIT || sh.MT * sh.Npad > TMEM_COLS || sh.nchunks > 8) {
         ctx->err = "tensor-core cell product: shared- or tensor-memory plan does not fit";
         return EFE_ERR_ARG;
     }
-    const size_t shm = sh.smem;
+    // more than half of an SM's shared memory: one block per SM, so that no two
+    // blocks (of one cluster, or not) compete for the SM's 512 TMEM columns
+    const size_t shm = std::max(sh.smem, (size_t)120 * 1024);
     EFE_CUDA(ctx, cudaFuncSetAttribute(k_cell_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    // two blocks per SM; blocks (x, y) for all y walk the same cells (column chunk y)
+    // one block per SM; a cluster of nchunks blocks (x, 0..nchunks-1) walks the
+    // same cells, one column chunk each; as many clusters as fit at once
     const int sms = nsm > 0 ? nsm : 148;
-    const int gx = std::max(1, std::min(ncells, (2 * sms) / sh.nchunks));
-    k_cell_mma<<<dim3(gx, sh.nchunks), TC_THREADS, shm, ctx->stream>>>(
-        map, reinterpret_cast<const __nv_bfloat16 *>(ctx->d_He16), Ycells, P, d_err);
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = (unsigned)sh.nchunks;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = shm;
+    cfg.stream = ctx->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int gx = std::max(1, sms / sh.nchunks);
+    cfg.gridDim = dim3((unsigned)gx, (unsigned)sh.nchunks);
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_cell_mma, &cfg) == cudaSuccess && nclusters > 0)
+        gx = std::min(gx, nclusters);
+    gx = std::max(1, std::min(gx, ncells));
+    cfg.gridDim = dim3((unsigned)gx, (unsigned)sh.nchunks);
+    EFE_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_cell_mma, map, reinterpret_cast<const __nv_bfloat16 *>(ctx->d_He16),
+                                     Ycells, P, d_err));
     ctx->launches++;
     ctx->cell_launches++;
     EFE_TRY(efe_check_launch(ctx, "k_cell_mma"));
