@@ -195,12 +195,14 @@ __global__ void k_support_reduce(const long long *sup_off, const int *sup_node, 
 }
 
 // Sum the chunk partials: outA[4I+f][j] (rows 0-3) and outB[4I+f][j] (rows 4-7).
-__global__ void k_support_sum(int natoms, int nch, int N, const double *part, double *outA, double *outB) {
+// nr = 8, or 4 when only rows 0-3 were formed.
+__global__ void k_support_sum(int natoms, int nch, int N, const double *part, double *outA, double *outB,
+                              int nr = 8) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= (long long)natoms * 8 * N) return;
+    if (idx >= (long long)natoms * nr * N) return;
     int j = (int)(idx % N);
-    int r = (int)((idx / N) % 8);
-    int I = (int)(idx / (8LL * N));
+    int r = (int)((idx / N) % nr);
+    int I = (int)(idx / ((long long)nr * N));
     double s = 0.0;
     for (int ch = 0; ch < nch; ++ch) s += part[((long long)(I * nch + ch) * 8 + r) * N + j];
     if (r < 4) { if (outA) outA[(long long)(4 * I + r) * N + j] = s; }
@@ -648,6 +650,84 @@ __global__ void __launch_bounds__(256, 4) k_support_reduce3(const long long *sup
     for (int i = threadIdx.x; i < nr * 256; i += blockDim.x) {
         const int rr = i / 256, jj = i % 256;
         if (jj < N) o[(long long)rr * N + jj] = acc[rr][jj];
+    }
+}
+
+// P_c Y_c over the compacted projector support lists, bf16 Y (the mixed
+// filter's P-only reduction).  One block per (atom, chunk of kPChunk
+// entries), from the order table; the chunk's node indices and P_c rows are
+// staged in shared memory first, so the loop carries no dependent index
+// load.  Thread t takes 8-column group t % ngr (16-byte loads) at position
+// lane t / ngr and keeps 8 rows in flight; the position lanes are then
+// summed in a fixed order (deterministic), rows 0-3 of the chunk's partials.
+constexpr int kPChunk = 1024;
+__global__ void __launch_bounds__(256, 3) k_psup_reduce(const long long *__restrict__ sup_off,
+                                                       const int *__restrict__ sup_node,
+                                                       const float4 *__restrict__ coef,
+                                                       const __nv_bfloat16 *__restrict__ Y, int N, int ldb, int nch,
+                                                       const int2 *__restrict__ order, double *__restrict__ part) {
+    __shared__ int s_node[kPChunk];
+    __shared__ float4 s_coef[kPChunk];
+    const int I = order[blockIdx.x].x, ch = order[blockIdx.x].y;
+    const long long beg = sup_off[I] + (long long)ch * kPChunk;
+    const int cnt = (int)max(0LL, min(sup_off[I + 1] - beg, (long long)kPChunk));
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        s_node[i] = sup_node[beg + i];
+        s_coef[i] = coef[beg + i];
+    }
+    __syncthreads();
+    const int ngr = ldb / 8, npl = blockDim.x / ngr;      // ngr <= 32 (N <= 256)
+    const int g = threadIdx.x % ngr, pl = threadIdx.x / ngr;
+    float acc[4][8];
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[f][c] = 0.f;
+    if (pl < npl) {
+        const __nv_bfloat16 *Yg = Y + 8 * g;
+        for (int i0 = pl; i0 < cnt; i0 += 8 * npl) {
+            uint4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * npl;
+                v[u] = i < cnt ? __ldg(reinterpret_cast<const uint4 *>(Yg + (size_t)s_node[i] * ldb))
+                               : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * npl;
+                if (i >= cnt) break;
+                const float4 q = s_coef[i];
+                const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v[u]);
+#pragma unroll
+                for (int c2 = 0; c2 < 4; ++c2) {
+                    const float2 y = __bfloat1622float2(h[c2]);
+                    acc[0][2 * c2] += q.x * y.x; acc[0][2 * c2 + 1] += q.x * y.y;
+                    acc[1][2 * c2] += q.y * y.x; acc[1][2 * c2 + 1] += q.y * y.y;
+                    acc[2][2 * c2] += q.z * y.x; acc[2][2 * c2 + 1] += q.z * y.y;
+                    acc[3][2 * c2] += q.w * y.x; acc[3][2 * c2 + 1] += q.w * y.y;
+                }
+            }
+        }
+    }
+    // two halves (f = 0, 1 then 2, 3): [npl][2][ldb] floats = 16 npl ngr <= 4096 fit in s_coef
+    float *red = reinterpret_cast<float *>(s_coef);
+    double *o = part + ((long long)I * nch + ch) * 8 * N;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+        __syncthreads();                                  // s_coef (or the previous half) is free
+        if (pl < npl)
+#pragma unroll
+            for (int f = 0; f < 2; ++f)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) red[((size_t)pl * 2 + f) * ldb + 8 * g + c] = acc[2 * h2 + f][c];
+        __syncthreads();
+        for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+            const int f = t / N, j = t - f * N;
+            float sum = 0.f;
+            for (int l = 0; l < npl; ++l) sum += red[((size_t)l * 2 + f) * ldb + j];
+            o[(long long)(2 * h2 + f) * N + j] = sum;
+        }
     }
 }
 
@@ -1540,7 +1620,13 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     if (cpl) {
         EFE_TRY(hx_scratch(ctx, N, s));
         if (epad) {
-            if (ctx->nonlocal) EFE_TRY(p_support_lists(ctx, s.chunk, &pnch));
+            if (ctx->nonlocal) {
+                EFE_TRY(p_support_lists(ctx, kPChunk, &pnch));
+                if (pnch > s.nch) {   // the partials are sized for the full support lists
+                    ctx->err = "projector support chunks exceed the partial-sum buffer";
+                    return EFE_ERR_ARG;
+                }
+            }
         } else {
             EFE_TRY(chunk_order(ctx, s.chunk, s.nch));
         }
@@ -1581,13 +1667,12 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
                 // P_c Y_c over the projector entries (W is needed by these cell products);
                 // E Y_c comes out of their padding rows
                 if (ctx->nonlocal) {
-                    k_support_reduce3<__nv_bfloat16><<<(unsigned)(pnch * std::max(ctx->natoms, 1)), 256, 0,
-                                                       ctx->stream>>>(
-                        ctx->d_psup_off, ctx->d_psup_node, ctx->d_psup_coef, nullptr, Ycur, nullptr, N, ldb, s.chunk,
-                        pnch, ctx->d_pchunk_order, s.part);
-                    const long long n8 = (long long)ctx->natoms * 8 * N;
-                    k_support_sum<<<nblk(n8, 256), 256, 0, ctx->stream>>>(ctx->natoms, pnch, N, s.part, s.Wc,
-                                                                          nullptr);
+                    k_psup_reduce<<<(unsigned)(pnch * std::max(ctx->natoms, 1)), 256, 0, ctx->stream>>>(
+                        ctx->d_psup_off, ctx->d_psup_node, reinterpret_cast<const float4 *>(ctx->d_psup_coef), Ycur,
+                        N, ldb, pnch, ctx->d_pchunk_order, s.part);
+                    const long long n4 = (long long)ctx->natoms * 4 * N;
+                    k_support_sum<<<nblk(n4, 256), 256, 0, ctx->stream>>>(ctx->natoms, pnch, N, s.part, s.Wc,
+                                                                          nullptr, 4);
                     ctx->launches += 2;
                 }
             } else {
