@@ -186,7 +186,7 @@ def algorithmic_bytes_bf16(w, d, N, m):
 
 def roofline_bf16(w, d, N, m, ms_cell_launch, ms_rec_launch, ms_filter, pk, pk_kind):
     """HBM rooflines of the bf16 filter from live CUDA-event times: the whole
-    filter pass, and its two heaviest kernels (k_gather_rec_b: the FE-node
+    filter pass, and its two heaviest kernels (k_gather_rec_c: the FE-node
     recurrence with the gather of the cell products; k_cell_mma: the tcgen05
     cell products), with the algorithmic bytes of algorithmic_bytes_bf16 (the
     recurrence's four arrays go to the node kernel, the H_e stream to the cell
@@ -198,8 +198,8 @@ def roofline_bf16(w, d, N, m, ms_cell_launch, ms_rec_launch, ms_filter, pk, pk_k
     rec_b, he_b, total_b = algorithmic_bytes_bf16(w, d, N, m)
     out = []
     for name, bytes_, ms, traffic_file, key, per in (
-            ("k_gather_rec_b (FE-node recurrence: gather of cell products, coupling, Eq. residualapprox)",
-             rec_b, ms_rec_launch, "k_gather_rec_b_traffic.txt", "traffic_over_algorithmic", rec_b),
+            ("k_gather_rec_c (FE-node recurrence: gather of cell products, coupling, Eq. residualapprox)",
+             rec_b, ms_rec_launch, "k_gather_rec_c_traffic.txt", "traffic_over_algorithmic", rec_b),
             ("k_cell_mma (tcgen05 cell products, one launch per H apply)", he_b, ms_cell_launch,
              "k_cell_mma_traffic.txt", "bytes_per_cell", d["n_cells"])):
         achieved = bytes_ / (ms / 1e3) / 1e9 if ms and ms > 0 else None

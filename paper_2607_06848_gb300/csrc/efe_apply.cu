@@ -555,6 +555,124 @@ __global__ void __launch_bounds__(256, 4)
     }
 }
 
+// The bf16 node recurrence with 8-column groups (the filter's node pass for
+// bf16 cell rows; the same arithmetic as k_gather_rec_b).  A warp takes a run
+// of kRun nodes along x; it first lists, per node of the run, the rows of its
+// up to 8 cells (z, y, x order; -1 where the node has no such cell, -2 for a
+// Dirichlet node) and (M^cc_n)^-1 in shared memory, then walks the run's
+// 16-byte column groups as one flat list, so the per-group work is the loads,
+// the sum over the cells (in the listed order) and the recurrence, two columns
+// per packed FP32 instruction.
+__device__ __forceinline__ void bf8_to_f2(const uint4 v, float2 f[4]) {
+    f[0] = make_float2(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u));
+    f[1] = make_float2(__uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
+    f[2] = make_float2(__uint_as_float(v.z << 16), __uint_as_float(v.z & 0xffff0000u));
+    f[3] = make_float2(__uint_as_float(v.w << 16), __uint_as_float(v.w & 0xffff0000u));
+}
+__device__ __forceinline__ uint32_t f2_to_bf2(const float2 v) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__global__ void __launch_bounds__(256, 4)
+    k_gather_rec_c(MeshDev m, int nruns_x, int ldb, const __nv_bfloat16 *__restrict__ Yc,
+                   const double *__restrict__ minv, const __nv_bfloat16 *__restrict__ Y1,
+                   const __nv_bfloat16 *__restrict__ Y0, const __nv_bfloat16 *__restrict__ G,
+                   const float *__restrict__ ck, float a, float c, float b, __nv_bfloat16 *__restrict__ Yn) {
+    __shared__ int s_row[8][kRun][8];
+    __shared__ float s_mi[8][kRun];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + w;
+    const long long nrows = (long long)m.Gy * m.Gz;
+    if (wid >= nrows * nruns_x) return;        // warp-uniform; no block-wide barrier below
+    const int xr = (int)(wid % nruns_x);
+    const long long yz = wid / nruns_x;
+    const int iy = (int)(yz % m.Gy), iz = (int)(yz / m.Gy);
+    const int x0 = xr * kRun;
+    const int nrun = min(kRun, m.Gx - x0);
+    const bool yz_in = iy > 0 && iz > 0 && iy < m.Gy - 1 && iz < m.Gz - 1;
+    const long long n0 = yz * m.Gx + x0;
+    {
+        const AxisCells ay = axis_cells(iy, m.p, m.ny), az = axis_cells(iz, m.p, m.nz);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = lane + 32 * h, k = e >> 3, u = e & 7;
+            const int ix = x0 + k;
+            int row = -1;
+            if (k < nrun) {
+                if (!(yz_in && ix > 0 && ix < m.Gx - 1)) {
+                    row = -2;
+                } else {
+                    const int sx = u & 1, sy = (u >> 1) & 1, sz = u >> 2;
+                    const AxisCells ax = axis_cells(ix, m.p, m.nx);
+                    if (sx <= ax.two && sy <= ay.two && sz <= az.two) {
+                        const int cx = ax.k0 + sx, cy = ay.k0 + sy, cz = az.k0 + sz;
+                        const int lx = sx ? 0 : ax.a0, ly = sy ? 0 : ay.a0, lz = sz ? 0 : az.a0;
+                        row = ((cz * m.ny + cy) * m.nx + cx) * m.ne + (lz * m.np1 + ly) * m.np1 + lx;
+                    }
+                }
+            }
+            s_row[w][k][u] = row;
+            if (u == 0 && k < nrun) s_mi[w][k] = (float)minv[n0 + k];
+        }
+    }
+    __syncwarp();
+    const int ncg = ldb / 8;
+    const int total = nrun * ncg;
+    int k = 0, cg = lane;
+    while (cg >= ncg) { cg -= ncg; ++k; }
+    const float2 a2 = make_float2(a, a), mc2 = make_float2(-c, -c), mb2 = make_float2(-b, -b);
+    for (int item = lane; item < total; item += 32) {
+        const long long n = n0 + k;
+        const int j = 8 * cg;
+        const size_t off = (size_t)n * ldb + j;
+        const int4 r0 = *reinterpret_cast<const int4 *>(&s_row[w][k][0]);
+        const int4 r1 = *reinterpret_cast<const int4 *>(&s_row[w][k][4]);
+        if (r0.x == -2) {
+            *reinterpret_cast<uint4 *>(Yn + off) = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+            const int rows[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            uint4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = rows[u] >= 0 ? __ldg(reinterpret_cast<const uint4 *>(Yc + (size_t)rows[u] * ldb + j))
+                                    : make_uint4(0u, 0u, 0u, 0u);
+            const uint4 y1 = __ldg(reinterpret_cast<const uint4 *>(Y1 + off));
+            const uint4 y0 = Y0 ? __ldg(reinterpret_cast<const uint4 *>(Y0 + off)) : make_uint4(0u, 0u, 0u, 0u);
+            const uint4 gg = __ldg(reinterpret_cast<const uint4 *>(G + off));
+            const float4 k0 = *reinterpret_cast<const float4 *>(ck + j), k1 = *reinterpret_cast<const float4 *>(ck + j + 4);
+            float2 acc[4], f[4];
+            bf8_to_f2(v[0], acc);
+#pragma unroll
+            for (int u = 1; u < 8; ++u) {
+                bf8_to_f2(v[u], f);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] = __fadd2_rn(acc[q], f[q]);
+            }
+            float2 f1[4], f0[4], fg[4];
+            bf8_to_f2(y1, f1);
+            bf8_to_f2(y0, f0);
+            bf8_to_f2(gg, fg);
+            const float2 kk[4] = {make_float2(k0.x, k0.y), make_float2(k0.z, k0.w), make_float2(k1.x, k1.y),
+                                  make_float2(k1.z, k1.w)};
+            const float mi = s_mi[w][k];
+            const float2 mi2 = make_float2(mi, mi);
+            uint4 o;
+            uint32_t *op = &o.x;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                // a (mi HY - c Y1) - b Y0 + (a ck) Ghat
+                const float2 t = __ffma2_rn(mi2, acc[q], __fmul2_rn(mc2, f1[q]));
+                const float2 r = __ffma2_rn(a2, t, __fmul2_rn(mb2, f0[q]));
+                op[q] = f2_to_bf2(__ffma2_rn(__fmul2_rn(a2, kk[q]), fg[q], r));
+            }
+            *reinterpret_cast<uint4 *>(Yn + off) = o;
+        }
+        cg += 32;
+        while (cg >= ncg) { cg -= ncg; ++k; }
+    }
+}
+
 // The coupling table of the cell products, YW[I][cb][r][c] (bf16, MN-major
 // 8 x 8 core matrices): rows r < 4 are Y_e rows 4I + r, rows r >= 4 are W rows
 // 4I + r - 4, column j = 8 cb + c; zero past N and for the extra block I = natoms.
@@ -1545,6 +1663,10 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
         ctx->err = "mesh too large for 32-bit node indices";
         return EFE_ERR_ARG;
     }
+    if ((long long)mh.nx * mh.ny * mh.nz * mh.ne > 2147483647LL) {
+        ctx->err = "mesh too large for 32-bit cell-row indices";
+        return EFE_ERR_ARG;
+    }
     if (N > 256) {
         ctx->err = "the tensor-core filter takes at most 256 columns per call";
         return EFE_ERR_ARG;
@@ -1726,16 +1848,16 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
         auto *rev = rec_event_pair(ctx);
         if (rev) cudaEventRecord(rev->first, ctx->stream);
         if (cells16)
-            k_gather_rec_b<__nv_bfloat16><<<rb_run, 256, 0, ctx->stream>>>(
-                mh, nruns_x, ldb, (const __nv_bfloat16 *)Ycells, ctx->d_minv, Ycur, Yprev, Gb,
-                fck + (size_t)(k - 1) * ldb, ak, cf, bk, Yb[inext]);
+            k_gather_rec_c<<<rb_run, 256, 0, ctx->stream>>>(mh, nruns_x, ldb, (const __nv_bfloat16 *)Ycells,
+                                                            ctx->d_minv, Ycur, Yprev, Gb, fck + (size_t)(k - 1) * ldb,
+                                                            ak, cf, bk, Yb[inext]);
         else
             k_gather_rec_b<float><<<rb_run, 256, 0, ctx->stream>>>(
                 mh, nruns_x, ldb, (const float *)Ycells, ctx->d_minv, Ycur, Yprev, Gb, fck + (size_t)(k - 1) * ldb,
                 ak, cf, bk, Yb[inext]);
         if (rev) cudaEventRecord(rev->second, ctx->stream);
         ctx->launches++;
-        EFE_TRY(efe_check_launch(ctx, "k_gather_rec_b"));
+        EFE_TRY(efe_check_launch(ctx, "node recurrence"));
         if (ne_) {
             k_enr_rec_v<<<nblk((long long)ne_ * ldb, 256), 256, 0, ctx->stream>>>(
                 ne_, N, ldb, s.Yraw, nullptr, Zcur, Zprev, Ge, fck + (size_t)(k - 1) * ldb, ak, cf, bk, Ze[inext]);

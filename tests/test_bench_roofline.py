@@ -63,8 +63,8 @@ def test_traffic_comes_from_the_ncu_summaries():
     N, m = w["nstates"], w["cheb_degree"]
     out = bench.roofline_bf16(w, d, N, m, 1.0, 1.0, 29.0, {"hbm_gbs": 1.0}, "test")
     by = {r["kernel"].split()[0]: r for r in out}
-    for name, f, key, per in (("k_gather_rec_b", "k_gather_rec_b_traffic.txt", "traffic_over_algorithmic",
-                               by["k_gather_rec_b"]["algorithmic_bytes"]),
+    for name, f, key, per in (("k_gather_rec_c", "k_gather_rec_c_traffic.txt", "traffic_over_algorithmic",
+                               by["k_gather_rec_c"]["algorithmic_bytes"]),
                               ("k_cell_mma", "k_cell_mma_traffic.txt", "bytes_per_cell", d["n_cells"])):
         v = bench._traffic_per_unit(f, key)
         if v is None:
