@@ -1,6 +1,7 @@
 // H^E, M^E, (M~^E)^-1 products, the residual Chebyshev filter, Rayleigh-Ritz,
 // Lanczos bounds and the C ABI entry points (paper Sec. II.B, III.A, III.B).
 #include "efe_internal.cuh"
+#include "efe_convert.cuh"
 
 #include <cuda_bf16.h>
 
@@ -869,7 +870,7 @@ __global__ void __launch_bounds__(256) k_filter_start_b(long long nn, long long 
     const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (r >= rows) return;
     const bool fe = r < nn;
-    const double mc = fe ? mcc[r] : 0.0, mi = fe ? minv[r] : 0.0;
+    const double mi = fe ? minv[r] : 0.0;
     const double *hv = HV + r * N, *vv = V + r * N;
     const double *mv = fe ? nullptr : MVe + (r - nn) * N;
     for (int j0 = 4 * (threadIdx.x & 31); j0 < ldb; j0 += 128) {
@@ -879,13 +880,16 @@ __global__ void __launch_bounds__(256) k_filter_start_b(long long nn, long long 
             const int j = j0 + i;
             g[i] = v[i] = m4[i] = 0.f;
             if (j < N) {
-                const double mvj = fe ? mc * vv[j] : mv[j];
-                const double gd = hv[j] - mvj * lv[j];
                 if (fe) {
-                    g[i] = (float)(mi * gd);
-                    if (Y0b && mi != 0.0) v[i] = (float)vv[j];
+                    // (M^cc)^-1 (HV - M^cc V lv) = (M^cc)^-1 HV - lv V: two FP64 operations,
+                    // the narrowing by integer operations (zero at the Dirichlet nodes)
+                    if (mi != 0.0) {
+                        g[i] = f64_to_f32_rn(fma(-lv[j], vv[j], mi * hv[j]));
+                        if (Y0b) v[i] = f64_to_f32_rn(vv[j]);
+                    }
                 } else {
-                    g[i] = (float)gd;
+                    const double mvj = mv[j];
+                    g[i] = (float)(hv[j] - mvj * lv[j]);
                     m4[i] = (float)mvj;
                 }
             }
