@@ -50,6 +50,7 @@
 // The epilogue writes each thread's row (TMEM lane) in 16-column groups of whole
 // 32-byte sectors.
 #include "efe_internal.cuh"
+#include <cstring>
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -67,6 +68,8 @@ constexpr int B_SLOTS = 2;           // plane-pair ring
 constexpr int SMEM_LIMIT = 232448;   // dynamic shared memory per block (227 KB, one block per SM)
 constexpr int TMEM_COLS = 512;       // tensor memory per block: one or two accumulator buffers
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz before a wait gives up
+constexpr int EPI_SLOT = 1024;       // epilogue staging: one 32-row x 16-column bf16 box (32-byte rows)
+constexpr int EPI_STAGE = EPI_WARPS * 2 * EPI_SLOT;   // two slots per epilogue warp
 
 struct TcParams {
     int ncells, nx, ny, p, np1, ne, xpad, Kpad, ksteps, MT, Npad, ncb, ldy;   // column chunk: blockIdx.y
@@ -88,6 +91,7 @@ struct TcParams {
     int x_slot_bytes;                   // shared memory of the extra B slot
     float *Epart;                       // E Y_c per (cell-atom pair, f) from the padding rows (nullptr: none)
     const int *ca_ptr;                  // ncells + 1: the cell-atom pairs of each cell
+    int tma_out;                        // bf16 rows leave by TMA tensor stores (ymap valid)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -204,6 +208,23 @@ __device__ __forceinline__ void reg_after_wait(uint32_t r[16]) {
                    "+r"(r[15]));
 }
 
+// shared -> global through the tensor map (bf16 output rows): box {16 columns,
+// 32 rows, 1 cell} at (x, y, z); rows past n_e and columns past ldy lie outside
+// the map and are not written.  Completion is tracked per thread in bulk groups.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, uint32_t src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z), "r"(src)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_le1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ uint32_t pack_bf16(uint32_t lo, uint32_t hi) {
+    __nv_bfloat162 b2 = __floats2bfloat162_rn(__uint_as_float(lo), __uint_as_float(hi));
+    return *reinterpret_cast<uint32_t *>(&b2);
+}
+
 // Columns col .. col+15 of one output row from 16 FP32 accumulators: bf16 (32
 // bytes) or FP32 (64 bytes); 256-bit stores when `wide` (aligned), else 16-byte
 // stores; nothing at or past ldy (ldy is a multiple of 8 for bf16, of 4 for FP32).
@@ -244,15 +265,16 @@ __device__ __forceinline__ void store16(unsigned char *row, int col, int ldy, in
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_cell_mma(const __grid_constant__ CUtensorMap xmap, const __nv_bfloat16 *__restrict__ He16, void *Ycells,
-               TcParams P, int *err) {
+    k_cell_mma(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap ymap,
+               const __nv_bfloat16 *__restrict__ He16, void *Ycells, TcParams P, int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // every TMA destination below is a multiple of 128 B from this base
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const int stage_bytes = P.ks * P.MT * 4096;      // one A stage: ks k-steps of all M-tiles
-    unsigned char *sA = smem;
-    unsigned char *sB = smem + (size_t)P.a_stages * stage_bytes;
+    unsigned char *sE = smem;                          // epilogue staging (bf16 output boxes)
+    unsigned char *sA = smem + EPI_STAGE;
+    unsigned char *sB = sA + (size_t)P.a_stages * stage_bytes;
     unsigned char *sX = sB + (size_t)B_SLOTS * P.slot_bytes;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sX + P.x_slot_bytes);
     uint64_t *full_a = bars, *empty_a = bars + MAX_A_STAGES;
@@ -443,14 +465,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (!ok) atomicExch(err, 2);
     } else if (warp >= 4) {
         // ---------------- epilogue ----------------
-        // TMEM -> registers (thread = row) -> shared memory (row of 64 B, its
-        // 16-byte units XOR-swizzled by the row) -> global (4 lanes per row
-        // segment: whole 32-byte sectors, 8 rows per warp store)
+        // TMEM -> registers (thread = row), 64-column chunks, one per warp of
+        // the lane quadrant in turn.  bf16 output: the chunk is packed in
+        // registers, the accumulator is released, and the rows leave through
+        // shared memory by TMA tensor stores (32 rows x 16 columns per box, two
+        // staging slots per warp), so the MMAs of the next cell do not wait for
+        // the global stores.  FP32 output: direct stores, then the release.
         const int q = warp & 3, ew = (warp - 4) >> 2;   // lane quadrant; which third of the column chunks
         const int eb = P.out_bf16 ? 2 : 4;              // bytes per stored element
         // 32-byte stores need 32-byte aligned rows and chunk starts
         const bool wide = ((size_t)P.ldy * eb) % 32 == 0 && (col0 * eb) % 32 == 0 &&
                           (reinterpret_cast<uintptr_t>(Ycells) & 31) == 0;
+        const uint32_t stg = smem_u32(sE + (size_t)(warp - 4) * 2 * EPI_SLOT);
+        const bool tma_out = P.tma_out != 0;
+        int nst = 0;                                    // boxes this warp has stored (lane 0 issues)
         int it = 0;
         bool ok = true;
         for (int cell = blockIdx.x; cell < P.ncells && ok; cell += gridDim.x, ++it) {
@@ -463,30 +491,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int rbase = mt * 128 + q * 32;
                 const uint32_t tbase =
                     tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * acc_cols + (uint32_t)(mt * P.Npad);
-                // this lane's output row (store16 takes the global column)
-                unsigned char *ybase =
-                    reinterpret_cast<unsigned char *>(Ycells) + ((size_t)cell * P.ne + rbase) * P.ldy * eb;
-                // 64-column chunks, one per warp of the quadrant in turn; four TMEM
-                // loads, one wait, then each thread stores its row's 16-column
-                // groups (32 or 64 bytes: whole sectors, 256-bit stores when aligned)
-                const bool row_ok = rbase + lane < P.ne;
-                unsigned char *yrow = ybase + (size_t)lane * P.ldy * eb;
-                for (int c0 = ew * 64; rbase < P.ne && c0 < P.Npad; c0 += (EPI_WARPS / 4) * 64) {
-                    const int nl = min(64, P.Npad - c0) / 16;  // warp-uniform
-                    uint32_t r[4][16];
-#pragma unroll
-                    for (int g = 0; g < 4; ++g)
-                        if (g < nl) tmem_ld16_nw(tbase + (uint32_t)(c0 + 16 * g), r[g]);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        if (g >= nl) continue;
-                        reg_after_wait(r[g]);
-                        if (row_ok) store16(yrow, col0 + c0 + 16 * g, P.ldy, P.out_bf16, wide, r[g]);
-                    }
-                }
                 // the padding rows of the last tile carry E Y_c partials (row ne + 4 slot + f)
-                if (P.Epart && ew == 0 && mt == P.MT - 1 && rbase + 32 > P.ne) {
+                auto epart = [&]() {
+                    if (!(P.Epart && ew == 0 && mt == P.MT - 1 && rbase + 32 > P.ne)) return;
                     const int q0 = P.ca_ptr[cell];
                     const int nrow = 4 * (P.ca_ptr[cell + 1] - q0);
                     const int r = rbase + lane - P.ne;                 // this lane's padding row
@@ -505,11 +512,74 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                                     __uint_as_float(v[i + 2]), __uint_as_float(v[i + 3]));
                         }
                     }
+                };
+                if (tma_out) {
+                    // bf16: 16-column groups -> staging slot -> TMA tensor store (asynchronous,
+                    // so the release below does not wait for the global writes)
+                    for (int c0 = ew * 64; rbase < P.ne && c0 < P.Npad; c0 += (EPI_WARPS / 4) * 64) {
+                        const int nl = min(64, P.Npad - c0) / 16;  // warp-uniform
+#pragma unroll
+                        for (int g0 = 0; g0 < 4; g0 += 2) {
+                            if (g0 >= nl) break;
+                            uint32_t r[2][16];
+#pragma unroll
+                            for (int gg = 0; gg < 2; ++gg)
+                                if (g0 + gg < nl) tmem_ld16_nw(tbase + (uint32_t)(c0 + 16 * (g0 + gg)), r[gg]);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int gg = 0; gg < 2; ++gg) {
+                                if (g0 + gg >= nl) continue;
+                                reg_after_wait(r[gg]);
+                                uint32_t pk[8];
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(r[gg][2 * i], r[gg][2 * i + 1]);
+                                // 32-byte rows (lane = row), 16-byte halves swapped on rows 4-7 mod 8
+                                const uint32_t slot = stg + (uint32_t)(nst & 1) * EPI_SLOT;
+                                if (lane == 0 && nst >= 2) bulk_wait_read_le1();   // this slot's last store has read it
+                                __syncwarp();
+                                const uint32_t sw = (uint32_t)((lane >> 2) & 1);
+#pragma unroll
+                                for (int h = 0; h < 2; ++h)
+                                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
+                                                     slot + (uint32_t)lane * 32u + ((uint32_t)h ^ sw) * 16u),
+                                                 "r"(pk[4 * h]), "r"(pk[4 * h + 1]), "r"(pk[4 * h + 2]),
+                                                 "r"(pk[4 * h + 3]));
+                                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                                __syncwarp();
+                                if (lane == 0) tma_store_3d(&ymap, slot, col0 + c0 + 16 * (g0 + gg), rbase, cell);
+                                ++nst;
+                            }
+                        }
+                    }
+                    epart();
+                    fence_before();
+                    mbar_arrive(&acc_empty[4 * buf + mt]);
+                } else {
+                    // 64-column chunks stored directly, then the release
+                    const bool row_ok = rbase + lane < P.ne;
+                    unsigned char *yrow = reinterpret_cast<unsigned char *>(Ycells) +
+                                          ((size_t)cell * P.ne + rbase + lane) * P.ldy * eb;
+                    for (int c0 = ew * 64; rbase < P.ne && c0 < P.Npad; c0 += (EPI_WARPS / 4) * 64) {
+                        const int nl = min(64, P.Npad - c0) / 16;  // warp-uniform
+                        uint32_t r[4][16];
+#pragma unroll
+                        for (int g = 0; g < 4; ++g)
+                            if (g < nl) tmem_ld16_nw(tbase + (uint32_t)(c0 + 16 * g), r[g]);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) {
+                            if (g >= nl) continue;
+                            reg_after_wait(r[g]);
+                            if (row_ok) store16(yrow, col0 + c0 + 16 * g, P.ldy, P.out_bf16, wide, r[g]);
+                        }
+                    }
+                    epart();
+                    fence_before();
+                    mbar_arrive(&acc_empty[4 * buf + mt]);
                 }
-                fence_before();
-                mbar_arrive(&acc_empty[4 * buf + mt]);
             }
         }
+        if (lane == 0 && nst > 0) bulk_wait_all();   // every store has landed before the block exits
         if (!ok) atomicExch(err, 3);
     }
     __syncthreads();
@@ -679,7 +749,8 @@ constexpr size_t TC_FIXED = (2 * MAX_A_STAGES + 2 * B_SLOTS + 18) * 8 + 64 + 102
 // shared memory: A ring + two B slots + the coupling slot + epilogue staging +
 // barriers (+ alignment slack) within 227 KB
 static size_t tc_smem(const TcShape &s) {
-    return (size_t)s.a_stages * s.ks * s.MT * 4096 + (size_t)B_SLOTS * s.slot_bytes + s.x_slot_bytes + TC_FIXED;
+    return (size_t)EPI_STAGE + (size_t)s.a_stages * s.ks * s.MT * 4096 + (size_t)B_SLOTS * s.slot_bytes +
+           s.x_slot_bytes + TC_FIXED;
 }
 
 // x_slots: atom slots of the coupling per cell (0: no coupling)
@@ -694,7 +765,7 @@ static TcShape tc_shape(const efe_ctx *ctx, int N, int ldb, int x_slots = 0) {
     s.kpg = 2 * s.plane_rows / 16;
     s.ngroups = (np1 + 1) / 2;
     const int stage = s.MT * 4096;
-    const size_t fixed = TC_FIXED;
+    const size_t fixed = TC_FIXED + EPI_STAGE;
     int maxN = std::min(256, (TMEM_COLS / s.MT) / 16 * 16);
     // keep at least 4 A stages
     while (maxN > 16 && fixed + 4 * (size_t)stage + (size_t)B_SLOTS * (maxN / 8) * 2 * s.plane_rows * 16 +
@@ -900,10 +971,31 @@ efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, void 
         ctx->err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")";
         return EFE_ERR_CUDA;
     }
+    const int ncells = m.nx * m.ny * m.nz;
+    // bf16 output rows: Ycells as {ldy columns, n_e rows, cells}, stored by
+    // 16 x 32 boxes (32-byte swizzle); rows past n_e fall outside the map
+    // (TMA stores only where every box lies inside the rows' columns and the row
+    // pitch is a whole number of 32-byte swizzle spans; otherwise direct stores)
+    alignas(64) CUtensorMap ymap;
+    std::memset(&ymap, 0, sizeof(ymap));
+    const bool tma_out = out_bf16 && ldy % 16 == 0 && sh.nchunks * sh.Npad <= ldy &&
+                         (reinterpret_cast<uintptr_t>(Ycells) & 15) == 0;
+    if (tma_out) {
+        cuuint64_t ydim[3] = {(cuuint64_t)ldy, (cuuint64_t)m.ne, (cuuint64_t)ncells};
+        cuuint64_t ystr[2] = {(cuuint64_t)ldy * 2, (cuuint64_t)ldy * 2 * m.ne};
+        cuuint32_t ybox[3] = {16, 32, 1};
+        cuuint32_t yes[3] = {1, 1, 1};
+        cr = encode(&ymap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Ycells, ydim, ystr, ybox, yes,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) {
+            ctx->err = "cuTensorMapEncodeTiled failed for the output rows (" + std::to_string((int)cr) + ")";
+            return EFE_ERR_CUDA;
+        }
+    }
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int ncells = m.nx * m.ny * m.nz;
     TcParams P{};
     P.ncells = ncells;
     P.nx = m.nx;
@@ -933,6 +1025,7 @@ efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, void 
     P.x_slot_bytes = sh.x_slot_bytes;
     P.Epart = (cpl && ctx->epad) ? Epart : nullptr;
     P.ca_ptr = ctx->d_cell_atom_ptr;
+    P.tma_out = tma_out ? 1 : 0;
     if (cpl && sh.nchunks * P.ncb > nCB) {
         ctx->err = "tensor-core cell product: coupling table narrower than the column chunks";
         return EFE_ERR_ARG;
@@ -968,7 +1061,7 @@ efe_status efe_tc_cells(efe_ctx *ctx, const void *Xp_bf16, int ldb, int N, void 
         gx = std::min(gx, nclusters);
     gx = std::max(1, std::min(gx, ncells));
     cfg.gridDim = dim3((unsigned)gx, (unsigned)sh.nchunks);
-    EFE_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_cell_mma, map, reinterpret_cast<const __nv_bfloat16 *>(ctx->d_He16),
+    EFE_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_cell_mma, map, ymap, reinterpret_cast<const __nv_bfloat16 *>(ctx->d_He16),
                                      Ycells, P, d_err));
     ctx->launches++;
     ctx->cell_launches++;

@@ -304,13 +304,16 @@ def test_filter_degree2_block_form_apply(name, N):
     assert rel < 1e-2, rel
 
 
-def test_filter_pass_bf16_two_chunks_p6():
-    # 200 vectors (two column chunks of the cell products) on the degree-6 mesh
-    # with a nearly redundant enrichment: Ritz vectors from the FP64 GPU
-    # solver (itself checked against the oracle), then one bf16 pass against
-    # the oracle's FP64 pass; error bounded by u * max residual
+@pytest.mark.parametrize("N", [200, 160, 48])
+def test_filter_pass_bf16_p6(N):
+    # on the degree-6 mesh with a nearly redundant enrichment: 200 vectors (two
+    # column chunks of the cell products, rows stored directly), 160 and 48
+    # (one chunk whose rows fill whole 32-byte spans: TMA tensor stores of the
+    # cell rows).  Ritz vectors from the FP64 GPU solver (itself checked
+    # against the oracle), then one bf16 pass against the oracle's FP64 pass;
+    # error bounded by u * max residual
     o, g = TP._systems("p6_enriched")
-    N, m = 200, 12
+    m = 12
     X = torch.tensor(TP._rand(o, N, 911), device="cuda")
     u0 = torch.tensor(TP._rand(o, 1, 912), device="cuda")
     HX = torch.empty_like(X)
