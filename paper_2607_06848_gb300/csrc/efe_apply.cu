@@ -867,10 +867,21 @@ __global__ void __launch_bounds__(256) k_filter_start_b(long long nn, long long 
                                                         __nv_bfloat16 *__restrict__ Y1b,
                                                         __nv_bfloat16 *__restrict__ Y0b, float *__restrict__ Ge,
                                                         float *__restrict__ Z1e, float *__restrict__ Z0e) {
+    // lv split once per block (N <= 256 on this path)
+    __shared__ float2 s_lv[256];
+    for (int j = threadIdx.x; j < N && j < 256; j += blockDim.x) {
+        float h, l;
+        f64_split(lv[j], h, l);
+        s_lv[j] = make_float2(h, l);
+    }
+    __syncthreads();
     const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (r >= rows) return;
     const bool fe = r < nn;
     const double mi = fe ? minv[r] : 0.0;
+    float mih, mil;
+    f64_split(mi, mih, mil);
+    const bool mi_nz = mi != 0.0;
     const double *hv = HV + r * N, *vv = V + r * N;
     const double *mv = fe ? nullptr : MVe + (r - nn) * N;
     for (int j0 = 4 * (threadIdx.x & 31); j0 < ldb; j0 += 128) {
@@ -881,11 +892,16 @@ __global__ void __launch_bounds__(256) k_filter_start_b(long long nn, long long 
             g[i] = v[i] = m4[i] = 0.f;
             if (j < N) {
                 if (fe) {
-                    // (M^cc)^-1 (HV - M^cc V lv) = (M^cc)^-1 HV - lv V: two FP64 operations,
-                    // the narrowing by integer operations (zero at the Dirichlet nodes)
-                    if (mi != 0.0) {
-                        g[i] = f64_to_f32_rn(fma(-lv[j], vv[j], mi * hv[j]));
-                        if (Y0b) v[i] = f64_to_f32_rn(vv[j]);
+                    // (M^cc)^-1 (HV - M^cc V lv) = (M^cc)^-1 HV - lv V in double-single
+                    // arithmetic on the FP32 pipe (operands split by integer operations;
+                    // zero at the Dirichlet nodes)
+                    if (mi_nz) {
+                        float hh, hl, vh, vl;
+                        f64_split(hv[j], hh, hl);
+                        f64_split(vv[j], vh, vl);
+                        const float2 l2 = s_lv[j];
+                        g[i] = ds_mul_sub(mih, mil, hh, hl, l2.x, l2.y, vh, vl);
+                        if (Y0b) v[i] = vh;
                     }
                 } else {
                     const double mvj = mv[j];

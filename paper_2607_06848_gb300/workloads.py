@@ -75,6 +75,16 @@ def cluster64(seed=0):
     return cluster(64, 40.0, 24, 6, 154, 30, seed=seed, name="cluster64")
 
 
+def cluster64_species(seed=0):
+    """cluster64 with one element's projector strengths on every atom (the paper's
+    clusters are of one element); its SCF converges, while random strengths per atom
+    make a disordered system whose density sloshes between the atoms."""
+    w = cluster64(seed)
+    w["hproj"] = species_strengths(64)
+    w["name"] = "cluster64_species"
+    return w
+
+
 def cluster512(seed=0):
     return cluster(512, 80.0, 40, 5, 1230, 30, seed=seed, name="cluster512")
 

@@ -1,7 +1,9 @@
-// Checks the integer-operation conversion of efe_convert.cuh against the
-// hardware conversion over hashed bit patterns: every binary64 exponent
+// Checks the integer-operation conversion and split of efe_convert.cuh
+// against the hardware conversion and FP64 over hashed bit patterns, and the
+// double-single product difference against FP64: every binary64 exponent
 // range that maps onto binary32 normals, subnormals, overflow and zero,
 // exact ties, and NaN / inf.  Prints the mismatch counts; exit status 0.
+#include <cmath>
 #include <cstdio>
 #include "efe_convert.cuh"
 
@@ -37,16 +39,42 @@ __global__ void k_check(long long n, unsigned long long *bad) {
         } else if (__float_as_uint(got) != __float_as_uint(ref)) {
             atomicAdd(&bad[0], 1ull);
         }
+        // the split: hi is the hardware's rounding, and hi + lo reproduces x to 2^-45
+        // relative where hi and lo are binary32 normals
+        if (x == x) {
+            float hi, lo;
+            f64_split(x, hi, lo);
+            const bool in = fabs(x) >= 0x1p-100 && fabs(x) < 0x1p120;
+            if (__float_as_uint(hi) != __float_as_uint(ref) ||
+                (in && !(fabs(x - ((double)hi + (double)lo)) < 0x1p-45 * fabs(x))))
+                atomicAdd(&bad[1], 1ull);
+        }
+        // the double-single difference a b - c d against FP64, on operands of one scale
+        // with cancellation down to 2^-20 of the products
+        {
+            const double a = 1.0 + (double)(h & 0xffffff) * 0x1p-24, bq = 0.5 + (double)((h >> 24) & 0xffffff) * 0x1p-25;
+            const double c = 1.0 + (double)((h >> 48) & 0xffff) * 0x1p-16;
+            const double d = (a * bq / c) * (1.0 + ldexp((double)((h >> 8) & 0xffff) - 32768.0, -35));
+            float ah, al, bh, bl, ch, cl, dh, dl;
+            f64_split(a, ah, al);
+            f64_split(bq, bh, bl);
+            f64_split(c, ch, cl);
+            f64_split(d, dh, dl);
+            const float got2 = ds_mul_sub(ah, al, bh, bl, ch, cl, dh, dl);
+            const double exact = fma(a, bq, -c * d);   // cancels to <= 2^-20 |a b|: FP64 error ~2^-53 |a b|
+            const double tol = ldexp(fabs((double)got2), -23) + 0x1p-43 * (fabs(a * bq) + fabs(c * d));
+            if (fabs((double)got2 - exact) > tol) atomicAdd(&bad[2], 1ull);
+        }
     }
 }
 
 int main() {
     const long long n = 1LL << 28;
-    unsigned long long *bad = nullptr, hb[1] = {0};
+    unsigned long long *bad = nullptr, hb[3] = {0, 0, 0};
     if (cudaMalloc(&bad, sizeof(hb)) != cudaSuccess) return 2;
     cudaMemset(bad, 0, sizeof(hb));
     k_check<<<4096, 256>>>(n, bad);
     if (cudaMemcpy(hb, bad, sizeof(hb), cudaMemcpyDeviceToHost) != cudaSuccess) return 3;
-    printf("checked %lld f64_to_f32_rn %llu\n", n, hb[0]);
+    printf("checked %lld f64_to_f32_rn %llu f64_split %llu ds_mul_sub %llu\n", n, hb[0], hb[1], hb[2]);
     return 0;
 }

@@ -1,8 +1,11 @@
-"""The integer-operation FP64 -> FP32 conversion used by the filter's start
-pass (efe_convert.cuh), against the hardware conversion over 2^28 hashed bit
-patterns: round to nearest even with exact ties, binary32 subnormals and
-overflow, zero, inf and NaN.  Compiled and run as a standalone CUDA
-program."""
+"""The integer-operation FP64 -> FP32 conversion and split and the
+double-single product difference used by the filter's start pass
+(efe_convert.cuh), over 2^28 hashed bit patterns: the conversion against the
+hardware's (round to nearest even with exact ties, binary32 subnormals and
+overflow, zero, inf and NaN), the split (hi the hardware's rounding at every
+pattern, hi + lo within 2^-45 of x where both are binary32 normals), and
+a b - c d against FP64 at cancellations down to 2^-20.  Compiled and run as
+a standalone CUDA program."""
 import os
 import re
 import shutil
@@ -24,7 +27,7 @@ def test_conversions_match_the_hardware(tmp_path):
     subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-I" + CSRC,
                     os.path.join(HERE, "cuda", "convert_check.cu"), "-o", exe], check=True)
     out = subprocess.run([exe], check=True, capture_output=True, text=True, timeout=120).stdout
-    m = re.search(r"checked (\d+) f64_to_f32_rn (\d+)", out)
+    m = re.search(r"checked (\d+) f64_to_f32_rn (\d+) f64_split (\d+) ds_mul_sub (\d+)", out)
     assert m, out
     assert int(m.group(1)) == 1 << 28
-    assert int(m.group(2)) == 0, out
+    assert (int(m.group(2)), int(m.group(3)), int(m.group(4))) == (0, 0, 0), out
