@@ -285,6 +285,38 @@ def scf_time_to_solution(torch, dev):
     return out
 
 
+def scf_cluster64(torch, dev):
+    """SCF time-to-solution at the benchmark's own size (24^3 cells p = 6, 154 states,
+    degree 30) on the 64-atom cluster with one element's projector strengths: mixed
+    (every filter pass in bf16) from seeded vectors, then FP64 continued from the mixed
+    fixed point (its vectors and density), whose energy the mixed one is compared with.
+    Phase times: potential, eigensolver, density, energy, mixing (ms)."""
+    from paper_2607_06848_gb300 import EFE, workloads as W, EFE_FP64, EFE_BF16
+    w = W.cluster64_species()
+    g = EFE(w["h"], w["ncell"], w["p"], w["atoms"], w["Z"], enrich=dict(alpha=ALPHA, r_end=R_END, t=T_ENR),
+            psp=dict(rc=1.0, r_trunc=6.0, h=w["hproj"], rloc=0.8))
+    rows = g.dims["n_rows"]
+    X = torch.tensor(W.random_block(rows, w["nstates"], 1), device=dev)
+    u0 = torch.tensor(W.random_block(rows, 1, 2), device=dev)
+    rho = torch.empty(g.dims["n_quad"], dtype=torch.float64, device=dev)
+    rec = {}
+    for name, prec, it in (("mixed_bf16", EFE_BF16, 100), ("fp64_continued", EFE_FP64, 10)):
+        start = rho.clone() if name == "fp64_continued" else None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = g.efe_scf(X, u0, rho0_q=start, rho_out=rho, cheb_degree=w["cheb_degree"], precision=prec,
+                      max_iter=it, profile=1)
+        torch.cuda.synchronize()
+        rec[name] = {"seconds": time.perf_counter() - t0, "iters": r["iters"], "converged": r["converged"],
+                     "E_Ha": r["E"], "ms_phase": [round(x, 1) for x in r["ms_phase"]]}
+    rec["dE_mixed_vs_fp64_Ha_per_atom"] = abs(rec["mixed_bf16"]["E_Ha"] - rec["fp64_continued"]["E_Ha"]) / 64
+    d = g.dims
+    rec["workload"] = "64 atoms (one element), 24^3 cells p=6 (%d FE DOF + %d enriched), %d states, degree %d" % (
+        d["n_fe_dof"], d["n_enr"], w["nstates"], w["cheb_degree"])
+    g.close()
+    return rec
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -429,6 +461,8 @@ def run_ours(args):
     }
     if not args.no_scf:
         line["scf"] = scf_time_to_solution(torch, dev)
+        if args.scf_c1:
+            line["scf"]["cluster64_species"] = scf_cluster64(torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         val, dt, desc, cores = cpu_sample(steps=6, warmup=0)
         line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
@@ -451,6 +485,8 @@ def main():
     ap.add_argument("--workload", default="cluster64")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-scf", action="store_true")
+    ap.add_argument("--scf-c1", action="store_true",
+                    help="add the SCF at the benchmark's own size (64 atoms, ~7 minutes)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
