@@ -200,6 +200,16 @@ efe_status efe_filter(efe_ctx *ctx, const double *V, const double *HV, const dou
  * implementation.  EFE_ERR_ARG for other values. */
 efe_status efe_set_cell_storage(efe_ctx *ctx, efe_precision prec);
 
+/* How the Poisson solves (efe_poisson and those inside efe_scf) iterate:
+ * EFE_FP64 -- conjugate gradients in FP64; EFE_FP32 -- iterative refinement:
+ * the residual and the solution in FP64, the correction equations by FP32
+ * conjugate gradients (each to 1e-4 of its right-hand side), then an FP64
+ * check; the stopping test is the FP64 residual either way, so both meet the
+ * same tolerance.  Default (until this is called): EFE_FP32 on meshes of
+ * 2^20 nodes or more (where the FP64 operator dominates), else EFE_FP64.  Not
+ * a part of the paper's method.  EFE_ERR_ARG for other values. */
+efe_status efe_set_poisson_precision(efe_ctx *ctx, efe_precision prec);
+
 /* Rayleigh-Ritz with the exact M^E (Eq. projectedKSEig), in place:
  * X <- X D, HX <- H^E X D with D^T (X^T M X) D = I, ascending eigenvalues.
  * X, HX: device rows x N (HX is computed here); eig, resid: host N doubles
@@ -277,7 +287,8 @@ efe_status efe_density(efe_ctx *ctx, const double *X, int N, const double *occ, 
 efe_status efe_xc(efe_ctx *ctx, const double *rho_q, double *vxc_q, double *exc_q);
 
 /* FE solution of -1/(4 pi) Lap phi = f with phi = 0 on the box (Eq. poisson),
- * Jacobi-preconditioned conjugate gradients to ||r|| < tol ||F||.
+ * Jacobi-preconditioned conjugate gradients to ||r|| < tol ||F|| (the FP64
+ * residual; see efe_set_poisson_precision for how the iterations run).
  * f_q: device n_quad; phi_nodes: device n_nodes (out); phi_q: device n_quad
  * (out, may be NULL); iters, rel_res: host (may be NULL). */
 efe_status efe_poisson(efe_ctx *ctx, const double *f_q, double *phi_nodes, double *phi_q,

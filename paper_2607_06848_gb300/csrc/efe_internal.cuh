@@ -130,6 +130,7 @@ struct efe_ctx {
     size_t hostio_bytes = 0;
     long long cell_launches = 0;
     bool cells_bf16 = true;                   // mixed filter: per-cell products stored in bf16 (else FP32)
+    int poisson_mixed = -1;                   // Poisson CG: 1 FP32 refinement stage, 0 FP64 only, -1 by mesh size
     // coupling as extra k-steps of the tensor-core cell products (efe_tc.cu)
     bool cx_built = false;
     int *d_cx_off = nullptr;                  // n_cells + 1: first extra k-step of each cell

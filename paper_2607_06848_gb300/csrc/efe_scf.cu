@@ -299,14 +299,20 @@ constexpr int NRED = 512;
 // c = (h/2) / (4 pi).  Applied as w1 = M_z u, w2 = S_z u; t1 = M_y w1,
 // t2 = S_y w1 + M_y w2; y = S_x t1 + M_x t2: 7 (p+1)^4 FMAs per cell instead
 // of (p+1)^6 for the dense matrix.  One CTA per cell of one colour.
-struct Lap1D {
-    double S[(EFE_MAXP + 1) * (EFE_MAXP + 1)], M[(EFE_MAXP + 1) * (EFE_MAXP + 1)];
-    double c;
+template <typename T>
+struct Lap1 {
+    T S[(EFE_MAXP + 1) * (EFE_MAXP + 1)], M[(EFE_MAXP + 1) * (EFE_MAXP + 1)];
+    T c;
 };
+using Lap1D = Lap1<double>;
 
+// T = double: the operator of the FP64 CG; T = float: of the inner FP32 CG of
+// the mixed-precision solve (the correction equation; its residual is formed
+// in FP64 by the double instance)
 constexpr int kLapMax = (EFE_MAXP + 1) * (EFE_MAXP + 1) * (EFE_MAXP + 1);
-__global__ void __launch_bounds__(256) k_lap_colour(MeshDev m, Lap1D L, int colour, const double *X, double *Y) {
-    __shared__ double u[kLapMax], w1[kLapMax], w2[kLapMax], w3[kLapMax];
+template <typename T>
+__global__ void __launch_bounds__(256) k_lap_colour(MeshDev m, Lap1<T> L, int colour, const T *X, T *Y) {
+    __shared__ T u[kLapMax], w1[kLapMax], w2[kLapMax], w3[kLapMax];
     const int np1 = m.np1, ne = m.ne;
     const int ox = colour & 1, oy = (colour >> 1) & 1, oz = (colour >> 2) & 1;
     const int hx = (m.nx - ox + 1) / 2, hy = (m.ny - oy + 1) / 2;
@@ -319,9 +325,9 @@ __global__ void __launch_bounds__(256) k_lap_colour(MeshDev m, Lap1D L, int colo
     __syncthreads();
     for (int l = threadIdx.x; l < ne; l += blockDim.x) {         // along z: w1 = M u, w2 = S u
         const int axy = l % (np1 * np1), az = l / (np1 * np1);
-        double a = 0.0, s = 0.0;
+        T a = 0, s = 0;
         for (int k = 0; k < np1; ++k) {
-            const double v = u[k * np1 * np1 + axy];
+            const T v = u[k * np1 * np1 + axy];
             a += L.M[az * np1 + k] * v;
             s += L.S[az * np1 + k] * v;
         }
@@ -331,7 +337,7 @@ __global__ void __launch_bounds__(256) k_lap_colour(MeshDev m, Lap1D L, int colo
     __syncthreads();
     for (int l = threadIdx.x; l < ne; l += blockDim.x) {         // along y: u = M w1, w3 = S w1 + M w2
         const int ax = l % np1, ay = (l / np1) % np1, az = l / (np1 * np1);
-        double a = 0.0, s = 0.0;
+        T a = 0, s = 0;
         for (int k = 0; k < np1; ++k) {
             const int src = (az * np1 + k) * np1 + ax;
             a += L.M[ay * np1 + k] * w1[src];
@@ -345,7 +351,7 @@ __global__ void __launch_bounds__(256) k_lap_colour(MeshDev m, Lap1D L, int colo
         const int ax = l % np1, ay = (l / np1) % np1, az = l / (np1 * np1);
         const int ix = cx * m.p + ax, iy = cy * m.p + ay, iz = cz * m.p + az;
         if (!interior_node(m, ix, iy, iz)) continue;
-        double s = 0.0;
+        T s = 0;
         for (int k = 0; k < np1; ++k) {
             const int src = (az * np1 + ay) * np1 + k;
             s += L.S[ax * np1 + k] * u[src] + L.M[ax * np1 + k] * w3[src];
@@ -446,6 +452,77 @@ __global__ void k_cg_p(long long n, const double *sc, const double *z, double *p
 }
 
 __global__ void k_set_scalar(double *sc, int k, double v) { sc[k] = v; }
+
+// --- the FP32 inner CG of the mixed-precision solve --------------------------
+// Vectors in FP32, each thread's partial sums in FP32 (a few tens of terms),
+// the block and grid sums and the CG scalars in FP64.
+__device__ __forceinline__ void block_parts2(double s1, double s2, double *part, int nparts) {
+    __shared__ double red[2][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = s1;
+        red[1][threadIdx.x >> 5] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t1 += red[0][w];
+            t2 += red[1][w];
+        }
+        part[blockIdx.x] = t1;
+        if (nparts > 1) part[NRED + blockIdx.x] = t2;
+    }
+}
+__global__ void k_dotp_f(long long n, const float *a, const float *b, double *part) {
+    float s = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s = fmaf(a[i], b[i], s);
+    block_parts2((double)s, 0.0, part, 1);
+}
+// d += alpha p; r -= alpha Ap; z = D^-1 r; partials of r.r and r.z
+__global__ void k_cg_update_f(long long n, const double *sc, float *d, float *r, const float *p, const float *Ap,
+                              const float *dinv, float *z, double *part) {
+    const float a = (float)sc[CG_ALPHA];
+    float s1 = 0.f, s2 = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float ri = r[i];
+        if (a != 0.f) {
+            d[i] = fmaf(a, p[i], d[i]);
+            ri = fmaf(-a, Ap[i], ri);
+            r[i] = ri;
+        }
+        const float zi = dinv[i] * ri;
+        z[i] = zi;
+        s1 = fmaf(ri, ri, s1);
+        s2 = fmaf(ri, zi, s2);
+    }
+    block_parts2((double)s1, (double)s2, part, 2);
+}
+__global__ void k_cg_p_f(long long n, const double *sc, const float *z, float *p) {
+    const float b = (float)sc[CG_BETA];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = fmaf(b, p[i], z[i]);
+}
+__global__ void k_narrow(long long n, const double *x, float *y) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (float)x[i];
+}
+// phi += d (the correction), and d = 0 for the next inner solve
+__global__ void k_add_correction(long long n, double *phi, float *d) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) {
+        phi[i] += (double)d[i];
+        d[i] = 0.f;
+    }
+}
+__global__ void k_add_mass_f(long long n, float s, const float *mcc, const float *X, float *Y) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) Y[i] = fmaf(s * mcc[i], X[i], Y[i]);
+}
 
 // --- Anderson mixing: history rings of rho_in (x) and residuals R = rho_out - rho_in
 constexpr int kMixMax = 8;                                           // dR vectors at most
@@ -563,6 +640,12 @@ struct ScfState {
     double *cg_F = nullptr, *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_Ap = nullptr;
     double *cg_sc = nullptr, *cg_part = nullptr;
     Lap1D lap{};                    // 1-D factors of the Poisson operator
+    Lap1<float> lapf{};             // the same in FP32 (inner solves)
+    // FP32 work vectors of the mixed-precision solve, the FP32 mass, and the
+    // FP32 Jacobi factors with the shift they were made for (-1: none yet)
+    float *f_r = nullptr, *f_z = nullptr, *f_p = nullptr, *f_Ap = nullptr, *f_d = nullptr, *f_dinv = nullptr,
+          *f_mcc = nullptr;
+    double f_dinv_k2 = -1.0;
 };
 
 static ScfState &scf_state(efe_ctx *ctx) {
@@ -575,7 +658,7 @@ void efe_scf_free(efe_ctx *ctx) {
     ScfState *S = static_cast<ScfState *>(ctx->scf);
     void *ptrs[] = {S->d_b, S->d_avals, S->d_cell_pair_ptr, S->d_cell_pair_idx, S->d_pair_atom, S->d_Kpois,
                     S->d_dinv, S->d_dinv_shift, S->d_part, S->d_Z, S->cg_F, S->cg_r, S->cg_z, S->cg_p, S->cg_Ap, S->cg_sc,
-                    S->cg_part};
+                    S->cg_part, S->f_r, S->f_z, S->f_p, S->f_Ap, S->f_d, S->f_dinv, S->f_mcc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete S;
@@ -618,6 +701,11 @@ static efe_status scf_prepare(efe_ctx *ctx) {
                 S.lap.M[a * np1 + b] = mv;
             }
         S.lap.c = 0.5 * m.h / (4.0 * kPi);
+        for (int i = 0; i < np1 * np1; ++i) {
+            S.lapf.S[i] = (float)S.lap.S[i];
+            S.lapf.M[i] = (float)S.lap.M[i];
+        }
+        S.lapf.c = (float)S.lap.c;
     }
     // Poisson cell matrix (1/4pi) K_e = (1/2pi) (1/2 K_e) and its assembled diagonal
     const int ne = m.ne;
@@ -715,12 +803,114 @@ static efe_status lap_apply(efe_ctx *ctx, const double *X, double *Y, double shi
     return efe_check_launch(ctx, "k_lap_colour");
 }
 
+// the FP32 operator: Y = (1/4 pi) K X + shift M^cc X
+static efe_status lap_apply_f(efe_ctx *ctx, const float *X, float *Y, float shift) {
+    ScfState &S = scf_state(ctx);
+    const MeshDev &m = ctx->m;
+    EFE_CUDA(ctx, cudaMemsetAsync(Y, 0, sizeof(float) * ctx->n_nodes, ctx->stream));
+    for (int colour = 0; colour < 8; ++colour) {
+        const int ox = colour & 1, oy = (colour >> 1) & 1, oz = (colour >> 2) & 1;
+        const int ncol = ((m.nx - ox + 1) / 2) * ((m.ny - oy + 1) / 2) * ((m.nz - oz + 1) / 2);
+        if (ncol) k_lap_colour<float><<<ncol, 256, 0, ctx->stream>>>(m, S.lapf, colour, X, Y);
+    }
+    if (shift != 0.f)
+        k_add_mass_f<<<nb(ctx->n_nodes, 256), 256, 0, ctx->stream>>>(ctx->n_nodes, shift, S.f_mcc, X, Y);
+    return efe_check_launch(ctx, "k_lap_colour<float>");
+}
+
+constexpr int kCgBlock = 16;            // CG iterations between host reads of the convergence flag
+constexpr double kInnerEta = 1e-4;      // an inner FP32 solve reduces its residual by this factor
+constexpr int kMaxOuter = 30;
+
+// Mixed-precision stage of the solve (iterative refinement): the residual
+// r = F - A phi in FP64; the correction equation A d = r by Jacobi CG in FP32
+// (vectors and per-thread sums in FP32, CG scalars in FP64) to kInnerEta of
+// |r|; phi += d in FP64; repeat until |r| < thr.  The FP32 operator does the
+// bulk of the iterations on this part's FP32 pipe; the stopping test is on the
+// FP64 residual, so the result meets the same tolerance as the FP64 CG.  The
+// FP64 residual of the final phi is left in S.cg_r.
+static efe_status poisson_mixed(efe_ctx *ctx, ScfState &S, const double *F, double *phi, bool warm, double shift,
+                                const double *dinv, double k2, double thr, int max_it, int *iters) {
+    const long long n = ctx->n_nodes;
+    if (!S.f_r) {
+        for (float **pp : {&S.f_r, &S.f_z, &S.f_p, &S.f_Ap, &S.f_d, &S.f_dinv, &S.f_mcc})
+            EFE_TRY(efe_alloc(ctx, (void **)pp, sizeof(float) * n));
+        k_narrow<<<nb(n, 256), 256, 0, ctx->stream>>>(n, ctx->d_mcc, S.f_mcc);
+    }
+    if (S.f_dinv_k2 != k2) {
+        k_narrow<<<nb(n, 256), 256, 0, ctx->stream>>>(n, dinv, S.f_dinv);
+        S.f_dinv_k2 = k2;
+    }
+    double *r = S.cg_r, *Ap = S.cg_Ap, *sc = S.cg_sc;
+    if (warm) {
+        EFE_TRY(lap_apply(ctx, phi, Ap, shift));
+        k_axpy_n<<<nb(n, 256), 256, 0, ctx->stream>>>(n, 1.0, F, -1.0, Ap, r);
+    } else {
+        EFE_CUDA(ctx, cudaMemsetAsync(phi, 0, sizeof(double) * n, ctx->stream));
+        EFE_CUDA(ctx, cudaMemcpyAsync(r, F, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    EFE_CUDA(ctx, cudaMemsetAsync(S.f_d, 0, sizeof(float) * n, ctx->stream));
+    int total = 0;
+    double hs[CG_NSC];
+    double rn_prev = 0.0;
+    for (int outer = 0; outer < kMaxOuter && total < max_it; ++outer) {
+        double rn2;
+        EFE_TRY(dot(ctx, n, r, r, rn2));
+        const double rn = std::sqrt(rn2);
+        if (!(rn >= thr)) break;                      // converged (or not finite: the FP64 CG reports it)
+        if (outer > 0 && !(rn < 0.5 * rn_prev)) break;   // FP32 no longer gains: the FP64 CG takes over
+        rn_prev = rn;
+        k_narrow<<<nb(n, 256), 256, 0, ctx->stream>>>(n, r, S.f_r);
+        k_set_scalar<<<1, 1, 0, ctx->stream>>>(sc, CG_THR, std::max(kInnerEta * rn, 0.5 * thr));
+        k_set_scalar<<<1, 1, 0, ctx->stream>>>(sc, CG_ALPHA, 0.0);
+        k_cg_update_f<<<NRED, 256, 0, ctx->stream>>>(n, sc, S.f_d, S.f_r, S.f_p, S.f_Ap, S.f_dinv, S.f_z, S.cg_part);
+        k_cg_beta<<<1, 32, 0, ctx->stream>>>(S.cg_part, sc, 1);
+        EFE_CUDA(ctx, cudaMemcpyAsync(S.f_p, S.f_z, sizeof(float) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        EFE_TRY(efe_check_launch(ctx, "poisson inner start"));
+        EFE_CUDA(ctx, cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+        EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        bool done = hs[CG_DONE] != 0.0;
+        int issued = 0;
+        const int cap = max_it - total;
+        while (!done && issued < cap) {
+            const int blk = std::min(kCgBlock, cap - issued);
+            for (int k = 0; k < blk; ++k) {
+                EFE_TRY(lap_apply_f(ctx, S.f_p, S.f_Ap, (float)shift));
+                k_dotp_f<<<NRED, 256, 0, ctx->stream>>>(n, S.f_p, S.f_Ap, S.cg_part);
+                k_cg_alpha<<<1, 32, 0, ctx->stream>>>(S.cg_part, sc);
+                k_cg_update_f<<<NRED, 256, 0, ctx->stream>>>(n, sc, S.f_d, S.f_r, S.f_p, S.f_Ap, S.f_dinv, S.f_z,
+                                                             S.cg_part);
+                k_cg_beta<<<1, 32, 0, ctx->stream>>>(S.cg_part, sc, 0);
+                k_cg_p_f<<<nb(n, 256), 256, 0, ctx->stream>>>(n, sc, S.f_z, S.f_p);
+            }
+            EFE_TRY(efe_check_launch(ctx, "poisson inner iterations"));
+            issued += blk;
+            EFE_CUDA(ctx, cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+            EFE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            done = hs[CG_DONE] != 0.0;
+        }
+        const int inner = (int)hs[CG_IT];
+        total += inner;
+        // phi += d; the FP64 residual of the new phi
+        k_add_correction<<<nb(n, 256), 256, 0, ctx->stream>>>(n, phi, S.f_d);
+        EFE_TRY(lap_apply(ctx, phi, Ap, shift));
+        k_axpy_n<<<nb(n, 256), 256, 0, ctx->stream>>>(n, 1.0, F, -1.0, Ap, r);
+        EFE_TRY(efe_check_launch(ctx, "poisson refinement"));
+        if (inner == 0) break;                        // no progress in FP32: the FP64 CG takes over
+    }
+    *iters = total;
+    return EFE_OK;
+}
+
 // FE solution of -1/(4 pi) Lap phi + k2/(4 pi) phi = f (k2 = 0: Poisson), phi = 0
 // on the box, with the lumped mass for the k2 term: Jacobi-preconditioned CG to
-// ||r|| < tol ||F||.  warm: start from the phi passed in (else from 0).
-// The scalars stay on the device; the host reads the convergence flag once
-// every kCgBlock iterations, and iterations after convergence change nothing.
-constexpr int kCgBlock = 16;
+// ||r|| < tol ||F||.  warm: start from the phi passed in (else from 0).  With
+// the mixed setting (efe_set_poisson_precision; by default on meshes of 2^20
+// nodes or more) a refinement stage (poisson_mixed) brings the FP64 residual
+// below the tolerance first; the FP64 CG then starts from its phi, checks the
+// residual and iterates only if the stage stopped short.  The scalars stay on the
+// device; the host reads the convergence flag once every kCgBlock iterations,
+// and iterations after convergence change nothing.
 static efe_status poisson(efe_ctx *ctx, const double *fq, double *phi, double *phi_q, double tol, int max_it,
                           int *iters, double *rel_res, bool warm = false, double k2 = 0.0) {
     ScfState &S = scf_state(ctx);
@@ -758,8 +948,13 @@ static efe_status poisson(efe_ctx *ctx, const double *fq, double *phi, double *p
     double bnorm2;
     EFE_TRY(dot(ctx, n, F, F, bnorm2));
     const double bnorm = std::sqrt(bnorm2);
-    int it = 0;
+    int it = 0, it_mixed = 0;
     double rr = 0.0;
+    const bool mixed = ctx->poisson_mixed > 0 || (ctx->poisson_mixed < 0 && n >= (1LL << 20));
+    if (mixed && bnorm > 0.0) {
+        EFE_TRY(poisson_mixed(ctx, S, F, phi, warm, shift, dinv, k2, tol * bnorm, max_it, &it_mixed));
+        warm = true;
+    }
     if (!(bnorm > 0.0)) {
         EFE_CUDA(ctx, cudaMemsetAsync(phi, 0, sizeof(double) * n, ctx->stream));
     } else {
@@ -805,7 +1000,7 @@ static efe_status poisson(efe_ctx *ctx, const double *fq, double *phi, double *p
         rr = hs[CG_RR];
     }
     if (phi_q) EFE_TRY(cell_values(ctx, phi, nullptr, 1, nullptr, 1, phi_q));
-    if (iters) *iters = it;
+    if (iters) *iters = it + it_mixed;
     if (rel_res) *rel_res = bnorm > 0 ? rr / bnorm : 0.0;
     return EFE_OK;
 }
@@ -814,6 +1009,16 @@ static efe_status poisson(efe_ctx *ctx, const double *fq, double *phi, double *p
 // C ABI
 // ===========================================================================
 extern "C" {
+
+efe_status efe_set_poisson_precision(efe_ctx *ctx, efe_precision prec) {
+    if (!ctx) return EFE_ERR_ARG;
+    if (prec != EFE_FP64 && prec != EFE_FP32) {
+        ctx->err = "efe_set_poisson_precision: EFE_FP64 or EFE_FP32";
+        return EFE_ERR_ARG;
+    }
+    ctx->poisson_mixed = prec == EFE_FP32 ? 1 : 0;
+    return EFE_OK;
+}
 
 efe_status efe_smeared_charge(efe_ctx *ctx, double *b_q) {
     if (!ctx || !b_q) return EFE_ERR_ARG;

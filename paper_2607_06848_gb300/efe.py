@@ -91,6 +91,7 @@ SIGNATURES = {
     "efe_lanczos": [_P, _P, _I, _D],
     "efe_filter": [_P, _P, _P, _P, _I, _I, _D, _I, _P],
     "efe_set_cell_storage": [_P, _I],
+    "efe_set_poisson_precision": [_P, _I],
     "efe_rayleigh_ritz": [_P, _P, _P, _I, _D, _D],
     "efe_chfsi": [_P, _P, _P, _I, _I, _D, _P, _I, ctypes.c_double, _I, _I, _D, _D, ctypes.POINTER(_I)],
     "efe_filter_host": [_P, _D, _D, _D, _I, _I, _D, _I, _D],
@@ -244,6 +245,9 @@ class EFE:
 
     def efe_set_cell_storage(self, prec):
         self._check(self.lib.efe_set_cell_storage(self.ctx, int(prec)))
+
+    def efe_set_poisson_precision(self, prec):
+        self._check(self.lib.efe_set_poisson_precision(self.ctx, int(prec)))
 
     def efe_filter(self, V, HV, lam, m, bounds, Vout, prec=EFE_FP64):
         b = (ctypes.c_double * 3)(*[float(x) for x in bounds])

@@ -114,6 +114,30 @@ def test_poisson_matches_oracle():
     assert _rel(phq.cpu().numpy(), m.interpolate(po[:, None])[:, 0]) < 1e-10
 
 
+def test_poisson_refinement_matches_oracle():
+    # the FP32 refinement stage forced on the small mesh (by default it runs on
+    # meshes of 2^20 nodes or more): the same FP64 tolerance, the same solution
+    from paper_2607_06848_gb300 import EFE_FP32, EFE_FP64
+    o, g, w = _dimer()
+    m = o.mesh
+    pts = m.all_quad_points()
+    f = OS.initial_density(m, w["atoms"], w["Z"]) + OS.gaussian_charge(pts, w["atoms"], w["Z"], 0.8)
+    fd = torch.tensor(f, device="cuda")
+    po, _ = OS.poisson_solve(m, f, tol=1e-12)
+    out = {}
+    for prec in (EFE_FP32, EFE_FP64):
+        g.efe_set_poisson_precision(prec)
+        phi = torch.empty(g.dims["n_nodes"], dtype=torch.float64, device="cuda")
+        its, rr = g.efe_poisson(fd, phi, None, tol=1e-12)
+        assert rr < 1e-12 and its > 10
+        assert _rel(phi.cpu().numpy(), po) < 1e-10
+        out[prec] = phi.cpu().numpy()
+    assert _rel(out[EFE_FP32], out[EFE_FP64]) < 1e-10
+    from paper_2607_06848_gb300.efe import EFEError
+    with pytest.raises(EFEError):
+        g.efe_set_poisson_precision(2)
+
+
 def test_density_matches_oracle():
     o, g, w = _dimer()
     X = W.random_block(o.nn + o.n_enr, 8, 5)
