@@ -212,17 +212,19 @@ __global__ void k_support_sum(int natoms, int nch, int N, const double *part, do
 
 // E Y_c per atom from the padding-row partials of the cell products:
 // Rh[4I + f][j] = sum over the atom's (cell, atom) pairs q of Epart[4q + f][j].
-// Block = (atom, f, 32 columns); 8 lanes per column take every 8th pair,
-// then a fixed-order sum over the lanes (deterministic).
+// Block = (atom, f, 32 columns); 8 lanes per column take every 8th pair
+// (FP32 sums), then a fixed-order FP64 sum over the lanes (deterministic).
 __global__ void __launch_bounds__(256) k_epart_sum(int N, int ld, const int *pair_off, const int *pairs,
                                                    const float *Epart, double *Rh) {
     __shared__ double red[8][32];
     const int I = blockIdx.z, f = blockIdx.y, j = blockIdx.x * 32 + (threadIdx.x & 31), pl = threadIdx.x >> 5;
-    double acc = 0.0;
+    // each lane's share in FP32 (the partials are FP32; FP64 adds and widenings
+    // per element would run on the narrow FP64 pipe), the 8 lanes in FP64
+    float acc = 0.f;
     if (j < N)
         for (int q = pair_off[I] + pl; q < pair_off[I + 1]; q += 8)
-            acc += (double)Epart[((size_t)pairs[q] * 4 + f) * ld + j];
-    red[pl][threadIdx.x & 31] = acc;
+            acc += Epart[((size_t)pairs[q] * 4 + f) * ld + j];
+    red[pl][threadIdx.x & 31] = (double)acc;
     __syncthreads();
     if (pl == 0 && j < N) {
         const int t = threadIdx.x & 31;
@@ -797,11 +799,11 @@ __global__ void __launch_bounds__(256, 3) k_psup_reduce(const long long *__restr
     __syncthreads();
     const int ngr = ldb / 8, npl = blockDim.x / ngr;      // ngr <= 32 (N <= 256)
     const int g = threadIdx.x % ngr, pl = threadIdx.x / ngr;
-    float acc[4][8];
+    float2 acc[4][4];
 #pragma unroll
     for (int f = 0; f < 4; ++f)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[f][c] = 0.f;
+        for (int c = 0; c < 4; ++c) acc[f][c] = make_float2(0.f, 0.f);
     if (pl < npl) {
         const __nv_bfloat16 *Yg = Y + 8 * g;
         for (int i0 = pl; i0 < cnt; i0 += 8 * npl) {
@@ -817,14 +819,16 @@ __global__ void __launch_bounds__(256, 3) k_psup_reduce(const long long *__restr
                 const int i = i0 + u * npl;
                 if (i >= cnt) break;
                 const float4 q = s_coef[i];
-                const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v[u]);
+                float2 y[4];
+                bf8_to_f2(v[u], y);
+                const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y), qz = make_float2(q.z, q.z),
+                             qw = make_float2(q.w, q.w);
 #pragma unroll
-                for (int c2 = 0; c2 < 4; ++c2) {
-                    const float2 y = __bfloat1622float2(h[c2]);
-                    acc[0][2 * c2] += q.x * y.x; acc[0][2 * c2 + 1] += q.x * y.y;
-                    acc[1][2 * c2] += q.y * y.x; acc[1][2 * c2 + 1] += q.y * y.y;
-                    acc[2][2 * c2] += q.z * y.x; acc[2][2 * c2 + 1] += q.z * y.y;
-                    acc[3][2 * c2] += q.w * y.x; acc[3][2 * c2 + 1] += q.w * y.y;
+                for (int c2 = 0; c2 < 4; ++c2) {          // two columns per packed FMA
+                    acc[0][c2] = __ffma2_rn(qx, y[c2], acc[0][c2]);
+                    acc[1][c2] = __ffma2_rn(qy, y[c2], acc[1][c2]);
+                    acc[2][c2] = __ffma2_rn(qz, y[c2], acc[2][c2]);
+                    acc[3][c2] = __ffma2_rn(qw, y[c2], acc[3][c2]);
                 }
             }
         }
@@ -839,7 +843,10 @@ __global__ void __launch_bounds__(256, 3) k_psup_reduce(const long long *__restr
 #pragma unroll
             for (int f = 0; f < 2; ++f)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) red[((size_t)pl * 2 + f) * ldb + 8 * g + c] = acc[2 * h2 + f][c];
+                for (int c = 0; c < 4; ++c) {
+                    red[((size_t)pl * 2 + f) * ldb + 8 * g + 2 * c] = acc[2 * h2 + f][c].x;
+                    red[((size_t)pl * 2 + f) * ldb + 8 * g + 2 * c + 1] = acc[2 * h2 + f][c].y;
+                }
         __syncthreads();
         for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
             const int f = t / N, j = t - f * N;
