@@ -278,22 +278,30 @@ __global__ void k_proj_w_sp(int n_proj, int n_enr, const double *Wc, const doubl
         }
     W[idx] = D[p] * s;
 }
-template <typename T>
-__global__ void k_enr_raw_sp(int n_enr, const double *Rhac, const double *Haa, const double *Pa, const double *W,
-                             const T *Xe, int ld, int N, const int *nb_ptr, const int *nb, double *Ye) {
+
+// The enriched rows of the bf16 filter over the nonzero atom blocks,
+// Ye = Rhac + H^E_ee Xe + P^E^T W, in FP32 arithmetic (those rows are FP32):
+// FP32 copies of H^E_ee and P^E, W as FP32 rows of stride ldw; Rhac read and
+// Ye written in FP64 (one conversion each).
+__global__ void k_enr_raw_f(int n_enr, const double *Rhac, const float *Haa, const float *Pa, const float *W, int ldw,
+                            const float *Xe, int ld, int N, const int *nb_ptr, const int *nb, double *Ye) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= (long long)n_enr * N) return;
     const int k = (int)(idx / N), j = (int)(idx % N), I = k / 4;
-    double s = Rhac[idx];
+    float s = (float)Rhac[idx];
     for (int q = nb_ptr[I]; q < nb_ptr[I + 1]; ++q) {
         const int k0 = 4 * nb[q];
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
-            s += Haa[(long long)k * n_enr + k0 + g] * (double)Xe[(long long)(k0 + g) * ld + j];
-            if (Pa) s += Pa[(long long)(k0 + g) * n_enr + k] * W[(long long)(k0 + g) * N + j];
+            s = fmaf(Haa[(long long)k * n_enr + k0 + g], Xe[(long long)(k0 + g) * ld + j], s);
+            if (Pa) s = fmaf(Pa[(long long)(k0 + g) * n_enr + k], W[(long long)(k0 + g) * ldw + j], s);
         }
     }
-    Ye[idx] = s;
+    Ye[idx] = (double)s;
+}
+__global__ void k_d2f(long long n, const double *x, float *y) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (float)x[i];
 }
 
 // Y_c[n] += sum_entries (Hca X_e + Pc W)
@@ -1736,6 +1744,8 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
                   sizeof(float) * ckf.size() +
                   2 * 4 * nb + sizeof(float) * (5 * neb + npb + nep) + 2 * (neb + npb + nyw) +
                   (cells16 ? 2 : 4) * ycells;
+    const size_t nhe = (size_t)std::max(ne_, 1) * std::max(ne_, 1), npe = (size_t)std::max(ctx->n_proj, 1) * std::max(ne_, 1);
+    need += sizeof(float) * (nhe + npe) + 64;
     EFE_TRY(efe_workspace(ctx, need));
     Carver cv{(char *)ctx->d_ws, ctx->ws_bytes};
     double *MV = cv.take<double>((size_t)std::max(ne_, 1) * N), *dck = cv.take<double>((size_t)(m + 1) * N);
@@ -1754,6 +1764,7 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     __nv_bfloat16 *YW = cv.take<__nv_bfloat16>(nyw);
     float *Epart = cv.take<float>(nep);
     void *Ycells = cells16 ? (void *)cv.take<__nv_bfloat16>(ycells) : (void *)cv.take<float>(ycells);
+    float *HEee32 = cv.take<float>(nhe), *PE32 = cv.take<float>(npe);   // FP32 copies for the enriched rows
     EFE_CUDA(ctx, cudaMemcpyAsync(dck, ck.data(), sizeof(double) * ck.size(), cudaMemcpyHostToDevice, ctx->stream));
     EFE_CUDA(ctx, cudaMemcpyAsync(fck, ckf.data(), sizeof(float) * ckf.size(), cudaMemcpyHostToDevice, ctx->stream));
     if (standard)
@@ -1764,6 +1775,12 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     EFE_CUDA(ctx, cudaMemsetAsync(W32, 0, sizeof(float) * npb, ctx->stream));
     EFE_CUDA(ctx, cudaMemsetAsync(Ye16, 0, 2 * neb, ctx->stream));
     EFE_CUDA(ctx, cudaMemsetAsync(W16, 0, 2 * npb, ctx->stream));
+    if (cpl && ctx->enrich) {
+        k_d2f<<<nblk((long long)nhe, 256), 256, 0, ctx->stream>>>((long long)ne_ * ne_, ctx->d_HEee, HEee32);
+        if (ctx->nonlocal && ctx->d_PE)
+            k_d2f<<<nblk((long long)npe, 256), 256, 0, ctx->stream>>>((long long)ctx->n_proj * ne_, ctx->d_PE, PE32);
+        ctx->launches += 2;
+    }
     HxScratch s{};
     int pnch = 0;
     if (cpl) {
@@ -1866,9 +1883,9 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
                     N, ldb, ctx->d_atom_pair_off, ctx->d_atom_pairs, Epart, s.Rh);
                 ctx->launches++;
             }
-            k_enr_raw_sp<float><<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(
-                ne_, s.Rh, ctx->d_HEee, ctx->nonlocal ? ctx->d_PE : nullptr, s.W, Ye, ldb, N, ctx->d_enbr_ptr,
-                ctx->d_enbr, s.Yraw);
+            k_enr_raw_f<<<nblk((long long)ne_ * N, 256), 256, 0, ctx->stream>>>(
+                ne_, s.Rh, HEee32, (ctx->nonlocal && ctx->d_PE) ? PE32 : nullptr, W32, ldb, Ye, ldb, N,
+                ctx->d_enbr_ptr, ctx->d_enbr, s.Yraw);
             ctx->launches++;
             EFE_TRY(efe_check_launch(ctx, "enriched rows"));
         }
