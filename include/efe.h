@@ -189,7 +189,10 @@ efe_status efe_lanczos(efe_ctx *ctx, const double *u0, int k, double out[3]);
  * the recurrence are carried as Y_k = M~^-1 Z_k (and G as M~^-1 G) in bf16
  * storage -- Y_k is the operand of the next cell products -- with FP32
  * arithmetic; the storage rounding scales with the residual like that of the
- * operands.  The enriched rows keep Z_k in FP32. */
+ * operands.  The enriched rows keep Z_k in FP32.  EFE_BF16 takes up to 256
+ * columns per pass; wider blocks are filtered in balanced column blocks
+ * (gathered, filtered, scattered back; the filter of each column is
+ * independent of the others). */
 efe_status efe_filter(efe_ctx *ctx, const double *V, const double *HV, const double *lam,
                       int N, int m, const double bounds[3], efe_precision prec, double *Vout);
 

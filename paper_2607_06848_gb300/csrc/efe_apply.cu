@@ -1937,11 +1937,72 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     return EFE_OK;
 }
 
+// columns c0 .. c0 + nc - 1 of a rows x N block <-> a rows x nc block
+__global__ void k_cols_gather(long long rows, int N, int c0, int nc, const double *X, double *Xb) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= rows * nc) return;
+    const long long r = idx / nc;
+    Xb[idx] = X[r * N + c0 + (int)(idx - r * nc)];
+}
+__global__ void k_cols_scatter(long long rows, int N, int c0, int nc, const double *Xb, double *X) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= rows * nc) return;
+    const long long r = idx / nc;
+    X[r * N + c0 + (int)(idx - r * nc)] = Xb[idx];
+}
+
+// The mixed filter takes at most 256 columns per pass (one or two column
+// chunks of the cell products); wider blocks go through it in balanced column
+// blocks (each column's filter is independent of the others): gathered into
+// a contiguous block, filtered, scattered back.
+constexpr int kTcMaxCols = 256;
+static efe_status filter_tensor_blocked(efe_ctx *ctx, const double *V, const double *HV, const double *lam, int N,
+                                        int m, const double bounds[3], double *Vout, bool standard) {
+    if (N <= kTcMaxCols) return filter_tensor(ctx, V, HV, lam, N, m, bounds, Vout, standard);
+    const long long rows = ctx->n_rows;
+    const int nblk_c = (N + kTcMaxCols - 1) / kTcMaxCols, nb0 = (N + nblk_c - 1) / nblk_c;
+    double *buf = nullptr;
+    EFE_TRY(efe_alloc(ctx, (void **)&buf, sizeof(double) * (size_t)rows * nb0 * 3));
+    double *Vb = buf, *HVb = buf + (size_t)rows * nb0, *Ob = buf + 2 * (size_t)rows * nb0;
+    efe_status st = EFE_OK;
+    double ms = 0.0, ms_cell = 0.0, ms_rec = 0.0;
+    long long launches = 0, cell_launches = 0, rec_launches = 0;
+    for (int c0 = 0; c0 < N && st == EFE_OK; c0 += nb0) {
+        const int nc = std::min(nb0, N - c0);
+        const unsigned g = (unsigned)nblk(rows * nc, 256);
+        k_cols_gather<<<g, 256, 0, ctx->stream>>>(rows, N, c0, nc, V, Vb);
+        k_cols_gather<<<g, 256, 0, ctx->stream>>>(rows, N, c0, nc, HV, HVb);
+        ctx->launches += 2;
+        st = filter_tensor(ctx, Vb, HVb, lam ? lam + c0 : nullptr, nc, m, bounds, Ob, standard);
+        if (st != EFE_OK) break;
+        ms += ctx->stats.ms_filter;
+        ms_cell += ctx->stats.ms_cell;
+        ms_rec += ctx->stats.ms_rec;
+        launches += ctx->stats.launches;
+        cell_launches += ctx->stats.cell_launches;
+        rec_launches += ctx->stats.rec_launches;
+        k_cols_scatter<<<g, 256, 0, ctx->stream>>>(rows, N, c0, nc, Ob, Vout);
+        ctx->launches++;
+        st = efe_check_launch(ctx, "column blocks");
+    }
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(buf);
+    if (st == EFE_OK) {
+        ctx->stats.ms_filter = ms;
+        ctx->stats.ms_cell = ms_cell;
+        ctx->stats.ms_rec = ms_rec;
+        ctx->stats.launches = launches + 3LL * nblk_c;
+        ctx->stats.cell_launches = cell_launches;
+        ctx->stats.rec_launches = rec_launches;
+    }
+    return st;
+}
+
 efe_status efe_filter_dispatch(efe_ctx *ctx, const double *V, const double *HV, const double *lam, int N, int m,
                                const double bounds[3], efe_precision prec, double *Vout, bool standard = false) {
     if (prec == EFE_FP64) return filter_impl<double>(ctx, V, HV, lam, N, m, bounds, Vout, standard);
     if (prec == EFE_FP32) return filter_impl<float>(ctx, V, HV, lam, N, m, bounds, Vout, standard);
-    if (prec == EFE_BF16) return filter_tensor(ctx, V, HV, lam, N, m, bounds, Vout, standard);
+    if (prec == EFE_BF16) return filter_tensor_blocked(ctx, V, HV, lam, N, m, bounds, Vout, standard);
     ctx->err = "unknown precision";
     return EFE_ERR_ARG;
 }

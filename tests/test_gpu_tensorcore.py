@@ -304,12 +304,12 @@ def test_filter_degree2_block_form_apply(name, N):
     assert rel < 1e-2, rel
 
 
-@pytest.mark.parametrize("N", [200, 160, 48])
+@pytest.mark.parametrize("N", [200, 160, 48, 300])
 def test_filter_pass_bf16_p6(N):
     # on the degree-6 mesh with a nearly redundant enrichment: 200 vectors (two
     # column chunks of the cell products, rows stored directly), 160 and 48
     # (one chunk whose rows fill whole 32-byte spans: TMA tensor stores of the
-    # cell rows).  Ritz vectors from the FP64 GPU solver (itself checked
+    # cell rows), 300 (two column blocks of 150 through the filter).  Ritz vectors from the FP64 GPU solver (itself checked
     # against the oracle), then one bf16 pass against the oracle's FP64 pass;
     # error bounded by u * max residual
     o, g = TP._systems("p6_enriched")
