@@ -44,11 +44,17 @@
 // one bulk copy per atom from a table laid out as MN-major core matrices).
 // So the coupling runs on the tensor cores, and the node kernel that sums the
 // cells is a plain streaming pass.
+// E Y_c of the enriched rows rides in the padding rows of the last M-tile
+// (rows n_e .. MT*128 of A hold the cell's E coefficients, four per
+// cell-atom pair): their accumulators go to FP32 partials per pair.
 // Per-cell results go to Ycells[cell][row][ldy] (FP32 or bf16); a gather
 // kernel sums the up-to-8 contributions of each node, so no colouring or
 // atomics are needed and every cell of the mesh runs in one persistent launch.
-// The epilogue writes each thread's row (TMEM lane) in 16-column groups of whole
-// 32-byte sectors.
+// The epilogue reads each thread's row (TMEM lane) in 16-column groups.  bf16
+// rows whose stride is a whole number of 32-byte spans are staged in shared
+// memory as 32-row x 16-column boxes (32-byte swizzle) and leave by TMA tensor
+// stores, so the accumulator is released without waiting for global stores;
+// other rows are stored directly, in whole 32-byte sectors.
 #include "efe_internal.cuh"
 #include <cstring>
 
