@@ -1777,9 +1777,11 @@ static efe_status filter_tensor(efe_ctx *ctx, const double *V, const double *HV,
     EFE_CUDA(ctx, cudaMemsetAsync(W16, 0, 2 * npb, ctx->stream));
     if (cpl && ctx->enrich) {
         k_d2f<<<nblk((long long)nhe, 256), 256, 0, ctx->stream>>>((long long)ne_ * ne_, ctx->d_HEee, HEee32);
-        if (ctx->nonlocal && ctx->d_PE)
+        ctx->launches++;
+        if (ctx->nonlocal && ctx->d_PE) {
             k_d2f<<<nblk((long long)npe, 256), 256, 0, ctx->stream>>>((long long)ctx->n_proj * ne_, ctx->d_PE, PE32);
-        ctx->launches += 2;
+            ctx->launches++;
+        }
     }
     HxScratch s{};
     int pnch = 0;
